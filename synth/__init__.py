@@ -1,0 +1,112 @@
+"""Seeded synthetic inputs for CV-QKD slice reconciliation.
+
+This module only MAKES INPUTS; it holds none of the reconciliation arithmetic
+(no quantiser, no likelihoods, no decoding).  Both the FP64 oracle and the
+CUDA library consume what it returns, so it is the one piece they share.
+
+* Quadratures (Sec. V, "Decoding Error and Time" set-up): Alice's
+  x_i ~ N(0, V_A) with V_A = 1, Bob's y_i = x_i + n_i, n_i ~ N(0, sigma_n^2),
+  sigma_n^2 = 1/SNR.  Normal draws come from numpy's Philox-4x32-10
+  counter-based generator (Salmon et al., SC'11) keyed by the seed: first the
+  `count` values of x, then the `count` noise values.  Both arrays are
+  returned as float32 (y is rounded once, after the FP64 addition).
+* Parity-check matrices: random left-regular LDPC codes (variable degree dv,
+  check degrees floor/ceil of dv*n/M), placed by a Philox-drawn socket
+  permutation, with double edges and 4-cycles broken by seeded socket swaps
+  (C helper in _codegen.c).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def _lib():
+    """Compile (once, with gcc) and load the socket-swap helper."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        src = os.path.join(_HERE, "_codegen.c")
+        so = os.path.join(_BUILD, "libsynth_codegen.so")
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            os.makedirs(_BUILD, exist_ok=True)
+            tmp = so + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", src, "-o", tmp])
+            os.replace(tmp, so)
+        lib = ctypes.CDLL(so)
+        lib.synth_break_short_cycles.restype = ctypes.c_int64
+        lib.synth_break_short_cycles.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_uint64, ctypes.c_int32]
+        _LIB = lib
+        return lib
+
+
+def build() -> None:
+    _lib()
+
+
+def philox(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def gaussian_pair(seed: int, count: int, snr: float, va: float = 1.0):
+    """(x, y) float32 arrays of length `count`: x ~ N(0, va), y = x + N(0, 1/snr)."""
+    g = philox(seed)
+    x = g.standard_normal(count) * np.sqrt(va)
+    noise = g.standard_normal(count) * np.sqrt(1.0 / snr)
+    y = x + noise
+    return x.astype(np.float32), y.astype(np.float32)
+
+
+def checks_for_rate(n: int, rate: float) -> int:
+    """Number of parity checks M = n (1 - r) of a rate-r code of length n."""
+    m = int(round(n * (1.0 - rate)))
+    if m <= 0 or m > n:
+        raise ValueError(f"rate {rate} gives {m} checks for n={n}")
+    return m
+
+
+def make_regular_code(seed: int, n: int, m_checks: int, dv: int = 3, max_passes: int = 100):
+    """Left-regular parity-check matrix in CSR form.
+
+    Returns (row_ptr int32[M+1], col_idx int32[E], residual) where E = dv*n and
+    `residual` counts the 4-cycle / double-edge detections left after the swap
+    passes (0 means girth >= 6).  Deterministic in `seed`.
+    """
+    n, M = int(n), int(m_checks)
+    E = dv * n
+    if M <= 0 or M > E:
+        raise ValueError("bad check count")
+    d_lo = E // M
+    n_hi = E - M * d_lo
+    deg = np.full(M, d_lo, dtype=np.int64)
+    deg[:n_hi] += 1
+    row_ptr = np.zeros(M + 1, dtype=np.int32)
+    np.cumsum(deg, out=row_ptr[1:])
+    sockets = np.repeat(np.arange(n, dtype=np.int32), dv)
+    perm = philox(seed).permutation(E)
+    col_idx = np.ascontiguousarray(sockets[perm], dtype=np.int32)
+    residual = _lib().synth_break_short_cycles(
+        n, M, row_ptr.ctypes.data, col_idx.ctypes.data,
+        ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), int(max_passes))
+    if residual < 0:
+        raise MemoryError("code construction")
+    return row_ptr, col_idx, int(residual)
+
+
+def degrees(row_ptr, col_idx, n):
+    """(column degrees, row degrees) of a CSR parity-check matrix."""
+    cols = np.bincount(col_idx, minlength=n)
+    rows = np.diff(row_ptr)
+    return cols, rows

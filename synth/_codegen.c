@@ -1,0 +1,127 @@
+/*
+ * Seeded construction of left-regular LDPC parity-check matrices (input data).
+ *
+ * This file builds INPUTS shared by the FP64 oracle and the CUDA library:
+ * the parity-check matrix H is data handed to both sides, never a result
+ * of the method.  It contains none of the reconciliation arithmetic.
+ *
+ * Construction (the code family the paper's experiment substitutes with
+ * random regular codes, Sec. V; block subdivision of Sec. III-A):
+ *   - n variable nodes, each of degree dv  -> dv*n sockets;
+ *   - M check nodes; the first (dv*n - M*d_lo) checks have degree d_lo+1,
+ *     the rest degree d_lo = floor(dv*n / M);
+ *   - variable sockets are placed on check sockets by a seeded permutation
+ *     (drawn by the caller and passed in), then double edges and edges on
+ *     4-cycles are broken by socket swaps with uniformly drawn partner edges
+ *     (splitmix64 stream, Steele/Lea/Flood 2014), at most `max_passes` passes.
+ * Swapping the variable ends of two edges keeps every node degree.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static uint64_t splitmix64(uint64_t *s) {
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* uniform integer in [0, bound) by rejection (no modulo bias) */
+static uint64_t draw_below(uint64_t *s, uint64_t bound) {
+    uint64_t lim = UINT64_MAX - (UINT64_MAX % bound);
+    uint64_t r;
+    do { r = splitmix64(s); } while (r >= lim);
+    return r % bound;
+}
+
+/*
+ * Mark every edge that is (a) a repeated variable inside one check or
+ * (b) the edge (c_a, v) of a 4-cycle v - c_a - u - c_b - v found from v.
+ * Returns the number of marked edges; bad[] gets 0/1 per edge.
+ * Also returns in *n_cycles the number of (v, c_a, u) detections, which
+ * counts each 4-cycle a bounded number of times (0 iff girth >= 6 and no
+ * double edge).
+ */
+static int64_t find_bad(int32_t n, int32_t M, const int32_t *rp, const int32_t *ci,
+                        int32_t *vptr, int32_t *vedge, int32_t *vfill,
+                        int64_t *stamp, int32_t *stamp_chk, uint8_t *bad, int64_t *n_cycles) {
+    int64_t E = rp[M];
+    /* variable -> edges (CSC) */
+    memset(vptr, 0, sizeof(int32_t) * (size_t)(n + 1));
+    for (int64_t e = 0; e < E; ++e) vptr[ci[e] + 1]++;
+    for (int32_t v = 0; v < n; ++v) vptr[v + 1] += vptr[v];
+    memcpy(vfill, vptr, sizeof(int32_t) * (size_t)n);
+    int32_t *chk_of_edge = (int32_t *)malloc(sizeof(int32_t) * (size_t)E);
+    for (int32_t c = 0; c < M; ++c)
+        for (int32_t e = rp[c]; e < rp[c + 1]; ++e) {
+            chk_of_edge[e] = c;
+            vedge[vfill[ci[e]]++] = e;
+        }
+    memset(bad, 0, (size_t)E);
+    int64_t nbad = 0, ncyc = 0;
+    /* double edges: a variable appearing twice in one check */
+    for (int32_t v = 0; v < n; ++v) stamp[v] = -1;
+    for (int32_t c = 0; c < M; ++c)
+        for (int32_t e = rp[c]; e < rp[c + 1]; ++e) {
+            int32_t v = ci[e];
+            if (stamp[v] == c) { if (!bad[e]) { bad[e] = 1; nbad++; } ncyc++; }
+            stamp[v] = c;
+        }
+    /* 4-cycles: for each v, walk its checks; a neighbour u reached through two
+       different checks closes a 4-cycle */
+    for (int32_t u = 0; u < n; ++u) { stamp[u] = -1; stamp_chk[u] = -1; }
+    for (int32_t v = 0; v < n; ++v) {
+        for (int32_t k = vptr[v]; k < vptr[v + 1]; ++k) {
+            int32_t ev = vedge[k];
+            int32_t c = chk_of_edge[ev];
+            for (int32_t e = rp[c]; e < rp[c + 1]; ++e) {
+                int32_t u = ci[e];
+                if (u == v) continue;
+                if (stamp[u] == v && stamp_chk[u] != c) {
+                    if (!bad[ev]) { bad[ev] = 1; nbad++; }
+                    ncyc++;
+                }
+                stamp[u] = v;
+                stamp_chk[u] = c;
+            }
+        }
+    }
+    free(chk_of_edge);
+    *n_cycles = ncyc;
+    return nbad;
+}
+
+/*
+ * ci[E] on entry: variable index of each check socket (already permuted).
+ * rp[M+1]: check row pointers (degrees fixed by the caller).
+ * Returns the residual count of 4-cycle/double-edge detections after the
+ * last pass (0 = girth >= 6), or -1 on allocation failure.
+ */
+int64_t synth_break_short_cycles(int32_t n, int32_t M, const int32_t *rp, int32_t *ci,
+                                 uint64_t seed, int32_t max_passes) {
+    int64_t E = rp[M];
+    int32_t *vptr = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+    int32_t *vedge = (int32_t *)malloc(sizeof(int32_t) * (size_t)E);
+    int32_t *vfill = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t *stamp = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t *stamp_chk = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t *bad = (uint8_t *)malloc((size_t)E);
+    if (!vptr || !vedge || !vfill || !stamp || !stamp_chk || !bad) {
+        free(vptr); free(vedge); free(vfill); free(stamp); free(stamp_chk); free(bad);
+        return -1;
+    }
+    uint64_t s = seed ^ 0xD1B54A32D192ED03ULL;
+    int64_t ncyc = 0;
+    for (int32_t pass = 0; pass <= max_passes; ++pass) {
+        int64_t nbad = find_bad(n, M, rp, ci, vptr, vedge, vfill, stamp, stamp_chk, bad, &ncyc);
+        if (nbad == 0 || pass == max_passes) break;
+        for (int64_t e = 0; e < E; ++e) {
+            if (!bad[e]) continue;
+            int64_t p = (int64_t)draw_below(&s, (uint64_t)E);
+            int32_t t = ci[e]; ci[e] = ci[p]; ci[p] = t;
+        }
+    }
+    free(vptr); free(vedge); free(vfill); free(stamp); free(stamp_chk); free(bad);
+    return ncyc;
+}

@@ -1,0 +1,45 @@
+"""Input generators: determinism, degree structure, girth, and sample statistics."""
+import numpy as np
+import pytest
+
+import synth
+
+
+@pytest.mark.parametrize("n,rate", [(4096, 0.5), (4096, 57 / 64), (4096, 1 / 16), (16384, 0.40625)])
+def test_regular_code_structure(n, rate):
+    M = synth.checks_for_rate(n, rate)
+    rp, ci, res = synth.make_regular_code(77, n, M)
+    cols, rows = synth.degrees(rp, ci, n)
+    assert np.all(cols == 3)
+    assert rows.max() - rows.min() <= 1
+    assert rows.sum() == 3 * n and len(rows) == M
+    assert res == 0
+    # no repeated variable inside a check, no 4-cycle (two checks sharing two variables)
+    sets = [frozenset(ci[rp[c]:rp[c + 1]].tolist()) for c in range(M)]
+    assert all(len(s) == rp[c + 1] - rp[c] for c, s in enumerate(sets))
+    pairs = {}
+    for c, s in enumerate(sets):
+        vs = sorted(s)
+        for i in range(len(vs)):
+            for j in range(i + 1, len(vs)):
+                key = (vs[i], vs[j])
+                assert key not in pairs, "4-cycle"
+                pairs[key] = c
+
+
+def test_code_is_deterministic():
+    a = synth.make_regular_code(5, 2048, 1024)
+    b = synth.make_regular_code(5, 2048, 1024)
+    c = synth.make_regular_code(6, 2048, 1024)
+    assert np.array_equal(a[1], b[1]) and not np.array_equal(a[1], c[1])
+
+
+def test_gaussian_pair_statistics():
+    x, y = synth.gaussian_pair(3, 1_000_000, 3.0)
+    assert x.dtype == np.float32 and y.dtype == np.float32
+    n = (y.astype(np.float64) - x)
+    assert abs(x.mean()) < 5e-3 and abs(x.var() - 1) < 5e-3
+    assert abs(n.var() - 1 / 3) < 3e-3
+    assert abs(np.corrcoef(x, n)[0, 1]) < 5e-3
+    x2, y2 = synth.gaussian_pair(3, 1000, 3.0)
+    assert np.array_equal(x2, synth.gaussian_pair(3, 1000, 3.0)[0])
