@@ -1,0 +1,221 @@
+/*
+ * qkdrec -- GPU hot path of CV-QKD slice reconciliation (B300, sm_103a).
+ *
+ * The calls follow the paper's statement of reverse slice reconciliation
+ * (Ai & Malaney, "Optimised Multithreaded CV-QKD Reconciliation for Global
+ * Quantum Networks", arXiv:2108.08418):
+ *   Bob quantises y with a constant-step quantiser M(.) into m bits per sample
+ *   (Sec. III-B step 1, LSB = l_0), forms slices S_j = bit plane j (step 2) and
+ *   sends syndromes s_j = H_j S_j (Sec. II Step 5, Sec. III-B steps 2-3);
+ *   Alice computes soft information for slice j from her quadratures x and the
+ *   already reconciled lower slices (steps 4-5) and decodes the N_d = N/N_R
+ *   sub-blocks of every slice in parallel with BP, all sub-blocks sharing one
+ *   H_j (Sec. III-A, Fig. 2; BP decoder of Sec. III-C).
+ *
+ * Conventions shared by every call
+ *   - LLR = ln P(b = 0) / P(b = 1); the hard decision is b = 1 iff LLR < 0.
+ *   - A "frame" is one sub-block of length n of one slice (N_R = n).
+ *   - Pointers marked DEVICE are CUDA device pointers owned by the caller; the
+ *     library never frees them.  Pointers marked HOST are read or written
+ *     during the call only.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is enqueued asynchronously on it; argument errors are returned
+ *     synchronously before anything is enqueued; a CUDA launch error is
+ *     returned as QKDREC_ERR_CUDA; a fault inside a kernel surfaces at the
+ *     caller's next synchronisation.
+ *   - Every call is thread-safe for distinct outputs; the only global state is
+ *     a per-thread error string (qkdrec_last_error).
+ *   - Sizes of zero are valid and enqueue nothing.
+ */
+#ifndef QKDREC_H
+#define QKDREC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QKDREC_OK = 0,
+    QKDREC_ERR_ARG = 1,          /* bad pointer, size, option or workspace too small */
+    QKDREC_ERR_CSR = 2,          /* malformed parity-check matrix */
+    QKDREC_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+    QKDREC_ERR_NOMEM = 4,        /* device or host allocation failed (code objects only) */
+    QKDREC_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    QKDREC_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+} qkdrec_status;
+
+typedef enum {
+    QKDREC_SP_FLOOD = 0,         /* sum-product, flooding schedule */
+    QKDREC_OMS_FLOOD = 1,        /* offset min-sum, flooding schedule */
+    QKDREC_OMS_LAYERED = 2       /* offset min-sum, layered schedule (greedy layers) */
+} qkdrec_algo;
+
+typedef enum {
+    QKDREC_F32 = 0,              /* FP32 messages and posteriors */
+    QKDREC_F16MSG = 1,           /* FP16 stored messages, FP32 arithmetic and posteriors */
+    QKDREC_I8SAT = 2             /* 6-bit integer min-sum: int8 messages (+-31), int16 posteriors */
+} qkdrec_prec;
+
+typedef enum {
+    QKDREC_LABEL_GRAY = 0,       /* label(k) = k xor (k >> 1)  (Sec. II Step 4) */
+    QKDREC_LABEL_BINARY = 1      /* label(k) = k */
+} qkdrec_label;
+
+/* Opaque parity-check matrix H_j, with device copies and derived schedules. */
+typedef struct qkdrec_code_s *qkdrec_code_t;
+
+/* ------------------------------------------------------------------ codes */
+
+/*
+ * Create a code from H (m_checks x n) in CSR form (the matrix Bob and Alice
+ * agree on for one slice, Sec. II Step 5; shared by all sub-blocks, Sec. III-A).
+ *   row_ptr  HOST int32 [m_checks + 1], row_ptr[0] = 0, non-decreasing.
+ *   col_idx  HOST int32 [row_ptr[m_checks]], variable indices in [0, n).
+ *   seed     provenance only (recorded, not used).
+ * The arrays are copied; the caller keeps ownership.  The call builds the
+ * variable-to-edge map and the layer partition (greedy first fit of checks in
+ * index order: check c joins the lowest layer holding none of its variables).
+ * Synchronous (allocates and copies to the current device).
+ * Errors: QKDREC_ERR_ARG (NULL out/arrays, n <= 0, m_checks <= 0),
+ *         QKDREC_ERR_CSR (bad row_ptr, index out of range, a variable twice in
+ *         one row), QKDREC_ERR_NOMEM, QKDREC_ERR_CUDA.
+ */
+qkdrec_status qkdrec_code_create(int32_t n, int32_t m_checks, const int32_t *row_ptr,
+                                 const int32_t *col_idx, uint64_t seed, qkdrec_code_t *out);
+
+/* Free a code and its device memory (synchronous).  NULL is ignored. */
+void qkdrec_code_destroy(qkdrec_code_t code);
+
+/*
+ * Sizes of a code: n, checks M, edges E, number of layers, largest check degree.
+ * Any output pointer may be NULL.  HOST outputs.
+ */
+qkdrec_status qkdrec_code_info(qkdrec_code_t code, int32_t *n, int32_t *m_checks,
+                               int64_t *edges, int32_t *n_layers, int32_t *dc_max);
+
+/* HOST int32 [M]: the layer of every check (the partition the layered decoder uses). */
+qkdrec_status qkdrec_code_layers(qkdrec_code_t code, int32_t *layer_of_check);
+
+/* ------------------------------------------------------- quantiser (Bob) */
+
+/*
+ * Constant-step quantiser and bit slicing (Sec. III-B step 1-2; 2^m bins
+ * centred on zero, text after Eq. beta).
+ *   y         DEVICE float [count]          Bob's quadratures.
+ *   m_slices  1..8; bins k = 0 .. 2^m - 1 on [lo, hi], step (hi - lo)/2^m,
+ *             interior thresholds t_k = lo + k (hi - lo)/2^m evaluated in FP64;
+ *             interval k = number of thresholds t <= y (a sample on a
+ *             threshold goes to the upper bin; the outer bins are unbounded).
+ *   label     labelling of the interval index (Gray default).
+ *   idx_out   DEVICE uint8 [count]          interval index k (may be NULL).
+ *   bits_out  DEVICE uint8 [m_slices][count] bit j of label(k), j = 0 the LSB
+ *             (may be NULL).
+ * Errors: QKDREC_ERR_ARG (count < 0, m out of range, lo >= hi, y NULL with count > 0).
+ */
+qkdrec_status qkdrec_quantise_slices(const float *y, int64_t count, int32_t m_slices,
+                                     double lo, double hi, qkdrec_label label,
+                                     uint8_t *idx_out, uint8_t *bits_out, void *stream);
+
+/* -------------------------------------------------------- slice LLR (Alice) */
+
+/*
+ * Soft information of slice j for Alice (Sec. III-B steps 4-5, multi-stage
+ * hard decoding, Sec. II footnote):
+ *   L_j(i) = ln sum_{k in K0(i)} P(k | x_i) - ln sum_{k in K1(i)} P(k | x_i),
+ *   K_b(i) = { k : bit j of label(k) = b and bits 0..j-1 of label(k) equal the
+ *             reconciled lower bits of sample i },
+ *   P(k | x) = Phi((t_{k+1} - x)/sigma_n) - Phi((t_k - x)/sigma_n), t_0 = -inf,
+ *   t_{2^m} = +inf, the thresholds of qkdrec_quantise_slices.
+ * The result is clipped to [-30, 30].  Interval probabilities near x are
+ * evaluated in FP32; intervals whose nearer edge lies more than 5 sigma_n from
+ * x (Gaussian tails) in FP64; terms below 1e-11 of their set's nearest term
+ * and sets that cannot move the clipped result are skipped.
+ *   x           DEVICE float [count]       Alice's quadratures.
+ *   lower_bits  DEVICE uint8 [j][count]    reconciled slices 0..j-1 (NULL iff j = 0).
+ *   llr_out     DEVICE float [count].
+ * Errors: QKDREC_ERR_ARG (j outside [0, m), sigma_n <= 0, lo >= hi, NULLs).
+ */
+qkdrec_status qkdrec_slice_llr(const float *x, int64_t count, int32_t m_slices, int32_t j,
+                               double lo, double hi, double sigma_n, qkdrec_label label,
+                               const uint8_t *lower_bits, float *llr_out, void *stream);
+
+/* ------------------------------------------------------------------ syndrome */
+
+/*
+ * s = H b (mod 2) for F frames (Sec. II Step 5: Bob encodes each slice into
+ * syndrome bits; the decoder's stopping test uses the same product).
+ *   bits      DEVICE uint8 [F][n]  (values 0/1; only bit 0 is used).
+ *   synd_out  DEVICE uint8 [F][M].
+ */
+qkdrec_status qkdrec_syndrome(qkdrec_code_t code, const uint8_t *bits, int32_t F,
+                              uint8_t *synd_out, void *stream);
+
+/* ------------------------------------------------------------------ decoder */
+
+typedef struct {
+    int32_t algo;          /* qkdrec_algo */
+    int32_t prec;          /* qkdrec_prec; QKDREC_I8SAT needs an OMS algorithm */
+    int32_t max_iter;      /* >= 0 */
+    float offset;          /* OMS offset beta (float modes); default 0.5 */
+    float llr_step;        /* integer mode: LSB of the 6-bit LLR grid; default 0.5 (offset = 1 LSB) */
+    int32_t early_stop;    /* 1: stop each frame at the first satisfied syndrome */
+    int32_t fallback_f32;  /* 1: frames a low-precision decode leaves unsatisfied are
+                              decoded again with FP32 messages (same algorithm) */
+} qkdrec_decode_opts;
+
+/* Defaults: SP flooding, FP32, 50 iterations, offset 0.5, step 0.5, early stop on, no fallback. */
+void qkdrec_decode_opts_default(qkdrec_decode_opts *opts);
+
+/* Bytes of DEVICE workspace qkdrec_decode_batch needs for F frames of `code`. */
+qkdrec_status qkdrec_decode_workspace_size(qkdrec_code_t code, int32_t F,
+                                           const qkdrec_decode_opts *opts, size_t *bytes);
+
+/*
+ * Syndrome-based BP decoding of F frames that share one code (Sec. III-A:
+ * N_d decoders loaded with the same matrix; Sec. III-C: BP decoder).
+ * Per frame: L = channel LLR; the syndrome of the hard decision is tested
+ * before the first iteration and after every iteration; with early_stop the
+ * frame stops at the first success.  The check rule carries the syndrome:
+ * a check with s_c = 1 flips the sign of its outgoing messages.
+ *   llr         DEVICE float [F][n]   channel LLRs (qkdrec_slice_llr).
+ *   synd        DEVICE uint8 [F][M]   Bob's syndrome bits.
+ *   bits_out    DEVICE uint8 [F][n]   last hard decision.
+ *   iters_out   DEVICE int32 [F]      iterations executed.
+ *   conv_out    DEVICE uint8 [F]      1 iff the output satisfies the syndrome.
+ *   post_out    DEVICE float [F][n]   final posterior LLRs (may be NULL); in
+ *                                     integer mode the integer posterior * llr_step.
+ *   workspace   DEVICE, >= qkdrec_decode_workspace_size bytes, 256-byte
+ *               aligned; contents need not be initialised and are clobbered.
+ * Errors: QKDREC_ERR_ARG (NULLs, F < 0, bad options, workspace too small or
+ *         misaligned), QKDREC_ERR_UNSUPPORTED (integer mode with SP),
+ *         QKDREC_ERR_CUDA.
+ */
+qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const uint8_t *synd,
+                                  int32_t F, const qkdrec_decode_opts *opts, uint8_t *bits_out,
+                                  int32_t *iters_out, uint8_t *conv_out, float *post_out,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------ host helpers */
+
+/*
+ * Conditional capacity C_j = 1 - H(B_j | X, B_0 .. B_{j-1}) in bits per sample
+ * for x ~ N(0, va), y = x + N(0, 1/snr), the quantiser on [lo, hi] with 2^m
+ * bins, by composite Simpson integration over x in [-12 sqrt(va), 12 sqrt(va)]
+ * (Sec. II Step 5: the code rate is chosen from the slice's capacity).  HOST.
+ */
+qkdrec_status qkdrec_slice_capacity(double snr, int32_t m_slices, int32_t j, double lo, double hi,
+                                    qkdrec_label label, double va, double *capacity);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *qkdrec_last_error(void);
+
+/* Library version string. */
+const char *qkdrec_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QKDREC_H */

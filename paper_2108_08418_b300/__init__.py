@@ -1,0 +1,287 @@
+"""Python binding of libqkdrec (CV-QKD slice reconciliation hot path on B300).
+
+Thin layer over the C ABI in include/qkdrec.h: every function below has the
+name of the C entry point it calls, checks and marshals its torch arguments,
+allocates outputs (and the decoder workspace) through torch, and passes
+torch's current CUDA stream.  All arithmetic of the path runs in the CUDA
+kernels of libqkdrec.so; there is no CPU fallback -- if the library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libqkdrec.so")
+
+# C enums (include/qkdrec.h)
+OK, ERR_ARG, ERR_CSR, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+SP_FLOOD, OMS_FLOOD, OMS_LAYERED = 0, 1, 2
+F32, F16MSG, I8SAT = 0, 1, 2
+LABEL_GRAY, LABEL_BINARY = 0, 1
+_LABELS = {"gray": LABEL_GRAY, "binary": LABEL_BINARY}
+_ALGOS = {"sp_flood": SP_FLOOD, "oms_flood": OMS_FLOOD, "oms_layered": OMS_LAYERED}
+_PRECS = {"f32": F32, "f16": F16MSG, "i8": I8SAT}
+
+EXPORTED = [
+    "qkdrec_code_create", "qkdrec_code_destroy", "qkdrec_code_info", "qkdrec_code_layers",
+    "qkdrec_quantise_slices", "qkdrec_slice_llr", "qkdrec_syndrome",
+    "qkdrec_decode_opts_default", "qkdrec_decode_workspace_size", "qkdrec_decode_batch",
+    "qkdrec_slice_capacity", "qkdrec_last_error", "qkdrec_version",
+]
+
+
+class QkdrecError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"qkdrec status {status}: {msg}")
+        self.status = status
+
+
+class DecodeOptsC(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("prec", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("offset", ctypes.c_float), ("llr_step", ctypes.c_float), ("early_stop", ctypes.c_int32),
+                ("fallback_f32", ctypes.c_int32)]
+
+
+_LIB = None
+
+
+def lib():
+    """Load libqkdrec.so (built by paper_2108_08418_b300.build); raises if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libqkdrec.so not built ({LIB_PATH}); run python -m paper_2108_08418_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U64, D, U = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                              ctypes.c_double, ctypes.c_int)
+    sig = {
+        "qkdrec_code_create": (U, [I32, I32, P, P, U64, P]),
+        "qkdrec_code_destroy": (None, [P]),
+        "qkdrec_code_info": (U, [P, P, P, P, P, P]),
+        "qkdrec_code_layers": (U, [P, P]),
+        "qkdrec_quantise_slices": (U, [P, I64, I32, D, D, U, P, P, P]),
+        "qkdrec_slice_llr": (U, [P, I64, I32, I32, D, D, D, U, P, P, P]),
+        "qkdrec_syndrome": (U, [P, P, I32, P, P]),
+        "qkdrec_decode_opts_default": (None, [P]),
+        "qkdrec_decode_workspace_size": (U, [P, I32, P, P]),
+        "qkdrec_decode_batch": (U, [P, P, P, I32, P, P, P, P, P, P, ctypes.c_size_t, P]),
+        "qkdrec_slice_capacity": (U, [D, I32, I32, D, D, U, D, P]),
+        "qkdrec_last_error": (ctypes.c_char_p, []),
+        "qkdrec_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(status):
+    if status != OK:
+        raise QkdrecError(status, lib().qkdrec_last_error().decode())
+
+
+def version() -> str:
+    return lib().qkdrec_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(t):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------- codes
+class Code:
+    """Parity-check matrix H (M x n) in CSR form with its device copies."""
+
+    def __init__(self, n: int, row_ptr, col_idx, seed: int = 0, device=None):
+        torch = _torch()
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        self._h = ctypes.c_void_p()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(dev):
+            _check(lib().qkdrec_code_create(int(n), rp.shape[0] - 1, rp.ctypes.data, ci.ctypes.data,
+                                            ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(self._h)))
+        self.device = dev
+        n_, m_, e_, l_, d_ = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(),
+                              ctypes.c_int32())
+        _check(lib().qkdrec_code_info(self._h, ctypes.byref(n_), ctypes.byref(m_), ctypes.byref(e_),
+                                      ctypes.byref(l_), ctypes.byref(d_)))
+        self.n, self.M, self.E, self.n_layers, self.dc_max = n_.value, m_.value, e_.value, l_.value, d_.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def layers(self) -> np.ndarray:
+        out = np.zeros(self.M, dtype=np.int32)
+        _check(lib().qkdrec_code_layers(self._h, out.ctypes.data))
+        return out
+
+    def destroy(self):
+        if self._h:
+            lib().qkdrec_code_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def qkdrec_code_create(n, row_ptr, col_idx, seed=0, device=None) -> Code:
+    return Code(n, row_ptr, col_idx, seed, device)
+
+
+# --------------------------------------------------------------- quantiser
+def qkdrec_quantise_slices(y, m_slices: int, lo: float, hi: float, label: str = "gray",
+                           want_idx: bool = True, want_bits: bool = True):
+    """Interval index uint8 [count] and bit planes uint8 [m][count] of Bob's y (float32 CUDA)."""
+    torch = _torch()
+    count = y.numel()
+    yp = _dev(y, torch.float32, "y")
+    idx = torch.empty(count, dtype=torch.uint8, device=y.device) if want_idx else None
+    bits = torch.empty((m_slices, count), dtype=torch.uint8, device=y.device) if want_bits else None
+    _check(lib().qkdrec_quantise_slices(yp, count, int(m_slices), float(lo), float(hi), _LABELS[label],
+                                        ctypes.c_void_p(idx.data_ptr()) if idx is not None else None,
+                                        ctypes.c_void_p(bits.data_ptr()) if bits is not None else None,
+                                        _stream(y)))
+    return idx, bits
+
+
+def qkdrec_slice_llr(x, m_slices: int, j: int, lo: float, hi: float, sigma_n: float, lower_bits=None,
+                     label: str = "gray", out=None):
+    """Channel LLR float32 [count] of slice j from Alice's x and reconciled lower bits uint8 [j][count]."""
+    torch = _torch()
+    count = x.numel()
+    xp = _dev(x, torch.float32, "x")
+    lb = None
+    if j > 0:
+        if lower_bits is None or lower_bits.shape[0] < j or lower_bits[0].numel() != count:
+            raise ValueError("lower_bits must be uint8 [>= j][count]")
+        lb = _dev(lower_bits, torch.uint8, "lower_bits")
+    if out is None:
+        out = torch.empty(count, dtype=torch.float32, device=x.device)
+    op = _dev(out, torch.float32, "out")
+    _check(lib().qkdrec_slice_llr(xp, count, int(m_slices), int(j), float(lo), float(hi), float(sigma_n),
+                                  _LABELS[label], lb, op, _stream(x)))
+    return out
+
+
+# ---------------------------------------------------------------- syndrome
+def qkdrec_syndrome(code: Code, bits):
+    """Syndromes uint8 [F][M] of bits uint8 [F][n]."""
+    torch = _torch()
+    bits2 = bits.reshape(-1, code.n)
+    F = bits2.shape[0]
+    bp = _dev(bits2, torch.uint8, "bits")
+    out = torch.empty((F, code.M), dtype=torch.uint8, device=bits.device)
+    _check(lib().qkdrec_syndrome(code.handle, bp, F, ctypes.c_void_p(out.data_ptr()), _stream(bits)))
+    return out
+
+
+# ----------------------------------------------------------------- decoder
+@dataclass
+class DecodeOpts:
+    algo: str = "sp_flood"        # sp_flood | oms_flood | oms_layered
+    prec: str = "f32"             # f32 | f16 | i8
+    max_iter: int = 50
+    offset: float = 0.5
+    llr_step: float = 0.5
+    early_stop: bool = True
+    fallback_f32: bool = False
+
+    def c(self) -> DecodeOptsC:
+        return DecodeOptsC(_ALGOS[self.algo], _PRECS[self.prec], int(self.max_iter), float(self.offset),
+                           float(self.llr_step), int(bool(self.early_stop)), int(bool(self.fallback_f32)))
+
+
+def qkdrec_decode_workspace_size(code: Code, F: int, opts: DecodeOpts) -> int:
+    o = opts.c()
+    b = ctypes.c_size_t()
+    _check(lib().qkdrec_decode_workspace_size(code.handle, int(F), ctypes.byref(o), ctypes.byref(b)))
+    return b.value
+
+
+def workspace_for(code: Code, F: int, opts: DecodeOpts, device):
+    torch = _torch()
+    nbytes = qkdrec_decode_workspace_size(code, F, opts)
+    # torch's caching allocator hands out 512-byte aligned blocks
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def qkdrec_decode_batch(code: Code, llr, synd, opts: DecodeOpts | None = None, want_post: bool = False,
+                        workspace=None, out=None):
+    """Decode F frames: llr float32 [F][n], synd uint8 [F][M] -> dict(bits, iters, converged, post)."""
+    torch = _torch()
+    opts = opts or DecodeOpts()
+    llr2 = llr.reshape(-1, code.n)
+    F = llr2.shape[0]
+    if synd.numel() != F * code.M:
+        raise ValueError("synd must be uint8 [F][M]")
+    lp = _dev(llr2, torch.float32, "llr")
+    sp = _dev(synd, torch.uint8, "synd")
+    dev = llr.device
+    if out is None:
+        out = dict(bits=torch.empty((F, code.n), dtype=torch.uint8, device=dev),
+                   iters=torch.empty(F, dtype=torch.int32, device=dev),
+                   converged=torch.empty(F, dtype=torch.uint8, device=dev),
+                   post=torch.empty((F, code.n), dtype=torch.float32, device=dev) if want_post else None)
+    if workspace is None:
+        workspace = workspace_for(code, F, opts, dev)
+    o = opts.c()
+    post = out.get("post")
+    _check(lib().qkdrec_decode_batch(code.handle, lp, sp, F, ctypes.byref(o),
+                                     ctypes.c_void_p(out["bits"].data_ptr()),
+                                     ctypes.c_void_p(out["iters"].data_ptr()),
+                                     ctypes.c_void_p(out["converged"].data_ptr()),
+                                     ctypes.c_void_p(post.data_ptr()) if post is not None else None,
+                                     ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(llr)))
+    return out
+
+
+# ------------------------------------------------------------ host helpers
+def qkdrec_slice_capacity(snr: float, m_slices: int, j: int, lo: float, hi: float, label: str = "gray",
+                          va: float = 1.0) -> float:
+    c = ctypes.c_double()
+    _check(lib().qkdrec_slice_capacity(float(snr), int(m_slices), int(j), float(lo), float(hi), _LABELS[label],
+                                       float(va), ctypes.byref(c)))
+    return c.value
+
+
+def quantiser_range(snr: float, va: float = 1.0):
+    """[-4 sigma_y, 4 sigma_y], sigma_y^2 = V_A + 1/SNR: the quantiser range the workloads use."""
+    sy = float(np.sqrt(va + 1.0 / snr))
+    return -4.0 * sy, 4.0 * sy
+
+
+def code_rate(capacity: float, fraction: float = 0.95, denom: int = 64) -> float:
+    """Rate rule: fraction * capacity rounded to the nearest 1/denom (ties up), at most
+    (denom-1)/denom; 0.0 means the slice is disclosed."""
+    k = int(np.floor(fraction * capacity * denom + 0.5))
+    return max(min(k, denom - 1), 0) / denom

@@ -1,0 +1,239 @@
+// Bob's quantiser / bit slicing and Alice's slice LLRs (Sec. III-B steps 1-5).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace qkd {
+
+constexpr int kMaxM = 8;
+constexpr int kMaxK = 1 << kMaxM;
+
+// ------------------------------------------------------------------ quantiser
+struct QuantParams {
+    float tf[kMaxK];        // tf[i] = smallest float >= t_{i+1} (FP64 threshold), i < K-1
+    uint8_t lab[kMaxK];     // label of interval k
+    int32_t m, K;
+};
+
+// Interval k = number of thresholds t <= y.  Because y is a float,
+// y >= t (FP64) is the same test as y >= tf (t rounded up to a float).
+// NaN compares "not below" every threshold, so it lands in the last bin.
+__global__ void quantise_kernel(const float *__restrict__ y, int64_t count, QuantParams p,
+                                uint8_t *__restrict__ idx_out, uint8_t *__restrict__ bits_out) {
+    // per-lane table lookups diverge: stage the tables in shared memory
+    __shared__ float tf[kMaxK];
+    __shared__ uint8_t lab_s[kMaxK];
+    for (int t = threadIdx.x; t < p.K; t += blockDim.x) {
+        tf[t] = p.tf[t];
+        lab_s[t] = p.lab[t];
+    }
+    __syncthreads();
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        float v = y[i];
+        int k = 0;
+        for (int s = p.K >> 1; s >= 1; s >>= 1)
+            if (!(v < tf[k + s - 1])) k += s;
+        if (idx_out) idx_out[i] = (uint8_t)k;
+        if (bits_out) {
+            int lab = lab_s[k];
+            for (int j = 0; j < p.m; ++j) bits_out[(int64_t)j * count + i] = (uint8_t)((lab >> j) & 1);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ slice LLR
+struct __align__(8) LlrParams {
+    double td[kMaxK + 1];    // the same thresholds in FP64
+    float tf[kMaxK + 1];     // t_0 .. t_K as floats (t_0 = -inf, t_K = +inf)
+    uint8_t k_of_label[kMaxK];
+    float inv_sigma;
+    double inv_sigma_d;
+    int32_t m, K, j;
+};
+
+constexpr float kTailSigma = 5.0f;   // intervals farther than this (in sigma_n) use FP64
+constexpr float kSkipNats = 25.0f;   // terms below e^-25 of the set's nearest term are dropped
+constexpr float kLn05 = -0.69314718055994531f;
+
+// log P(k|x) for an interval within kTailSigma of x: FP32 complementary error
+// functions taken on the side of x the interval lies on.
+__device__ __forceinline__ float logp_near(float a, float b) {
+    const float r2 = 0.70710678118654752f;
+    float P;
+    if (a >= 0.0f) P = 0.5f * (erfcf(a * r2) - erfcf(b * r2));
+    else if (b <= 0.0f) P = 0.5f * (erfcf(-b * r2) - erfcf(-a * r2));
+    else P = 1.0f - 0.5f * erfcf(-a * r2) - 0.5f * erfcf(b * r2);
+    return logf(P);
+}
+
+// log Q(z) for z >= 0 in FP64 through the scaled complement erfcx, so that the
+// far Gaussian tail never underflows.
+__device__ __forceinline__ double log_q(double z) {
+    const double r2 = 0.70710678118654752440;
+    if (isinf(z)) return -INFINITY;
+    double u = z * r2;
+    return log(0.5 * erfcx(u)) - u * u;
+}
+
+// log P(k|x) in FP64 for a tail interval: the interval lies entirely on one
+// side of x, at standardised near edge dn >= 0 and far edge df >= dn.
+__device__ __forceinline__ double logp_tail(double dn, double df) {
+    double ln = log_q(dn);
+    double lf = log_q(df);
+    return ln + log1p(-exp(lf - ln));
+}
+
+__device__ __forceinline__ float logp_interval(const LlrParams &p, int k, float x, double xd,
+                                               float d) {
+    if (d <= kTailSigma) {
+        float a = (p.tf[k] - x) * p.inv_sigma;
+        float b = (p.tf[k + 1] - x) * p.inv_sigma;
+        return logp_near(a, b);
+    }
+    double a = (p.td[k] - xd) * p.inv_sigma_d;
+    double b = (p.td[k + 1] - xd) * p.inv_sigma_d;
+    double r = a >= 0.0 ? logp_tail(a, b) : logp_tail(-b, -a);
+    return (float)r;
+}
+
+// standardised distance from x to interval k (0 if x lies inside)
+__device__ __forceinline__ float interval_dist(const LlrParams &p, int k, float x) {
+    float a = (p.tf[k] - x) * p.inv_sigma;
+    float b = (p.tf[k + 1] - x) * p.inv_sigma;
+    return a >= 0.0f ? a : (b <= 0.0f ? -b : 0.0f);
+}
+
+__global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
+                                 const uint8_t *__restrict__ lower, const LlrParams p_in,
+                                 float *__restrict__ out) {
+    // per-lane table lookups diverge: stage the tables in shared memory
+    __shared__ LlrParams sp;
+    {
+        const int n4 = (int)(sizeof(LlrParams) / 4);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&p_in);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+        for (int t = threadIdx.x; t < n4; t += blockDim.x) dst[t] = src[t];
+    }
+    __syncthreads();
+    const LlrParams &p = sp;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int nc = p.K >> p.j;  // candidates consistent with the lower bits
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        float x = xs[i];
+        double xd = (double)x;
+        int low = 0;
+        for (int b = 0; b < p.j; ++b) low |= (int)(lower[(int64_t)b * count + i] & 1) << b;
+        // nearest candidate of each set
+        float dmin[2] = {INFINITY, INFINITY};
+        int kmin[2] = {0, 0};
+        for (int u = 0; u < nc; ++u) {
+            int k = p.k_of_label[(u << p.j) | low];
+            float d = interval_dist(p, k, x);
+            int b = u & 1;
+            if (d < dmin[b]) { dmin[b] = d; kmin[b] = k; }
+        }
+        float lpn[2];
+        lpn[0] = logp_interval(p, kmin[0], x, xd, dmin[0]);
+        lpn[1] = logp_interval(p, kmin[1], x, xd, dmin[1]);
+        // a set whose whole mass is provably more than the clip below the other's
+        // nearest term cannot move the clipped result
+        const float lg_half_n = logf(0.5f * (float)nc);   // log |K_b|
+        float ub0 = lg_half_n + (dmin[0] > 0.0f ? kLn05 - 0.5f * dmin[0] * dmin[0] : 0.0f);
+        float ub1 = lg_half_n + (dmin[1] > 0.0f ? kLn05 - 0.5f * dmin[1] * dmin[1] : 0.0f);
+        float llr;
+        if (ub1 < lpn[0] - kLlrClip) {
+            llr = kLlrClip;
+        } else if (ub0 < lpn[1] - kLlrClip) {
+            llr = -kLlrClip;
+        } else {
+            float s[2] = {1.0f, 1.0f};
+            for (int u = 0; u < nc; ++u) {
+                int k = p.k_of_label[(u << p.j) | low];
+                int b = u & 1;
+                if (k == kmin[b]) continue;
+                float d = interval_dist(p, k, x);
+                float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
+                if (bound < lpn[b] - kSkipNats) continue;
+                s[b] += expf(logp_interval(p, k, x, xd, d) - lpn[b]);
+            }
+            llr = (lpn[0] + logf(s[0])) - (lpn[1] + logf(s[1]));
+            llr = fminf(fmaxf(llr, -kLlrClip), kLlrClip);
+        }
+        out[i] = llr;
+    }
+}
+
+static int label_of(int k, qkdrec_label lab) { return lab == QKDREC_LABEL_BINARY ? k : (k ^ (k >> 1)); }
+
+static float round_up_to_float(double t) {
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+static int grid_for(int64_t count, int block) {
+    int64_t want = ceil_div(count, block);
+    int64_t cap = (int64_t)sm_count() * 16;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace qkd
+
+using namespace qkd;
+
+extern "C" {
+
+qkdrec_status qkdrec_quantise_slices(const float *y, int64_t count, int32_t m, double lo, double hi,
+                                     qkdrec_label label, uint8_t *idx_out, uint8_t *bits_out,
+                                     void *stream) {
+    clear_error();
+    if (count < 0) QKD_FAIL(QKDREC_ERR_ARG, "count < 0");
+    if (m < 1 || m > kMaxM) QKD_FAIL(QKDREC_ERR_ARG, "m_slices=%d outside [1, %d]", m, kMaxM);
+    if (!(lo < hi)) QKD_FAIL(QKDREC_ERR_ARG, "need lo < hi");
+    if (label != QKDREC_LABEL_GRAY && label != QKDREC_LABEL_BINARY) QKD_FAIL(QKDREC_ERR_ARG, "bad label");
+    if (count == 0) return QKDREC_OK;
+    if (!y) QKD_FAIL(QKDREC_ERR_ARG, "y is NULL");
+    QuantParams p;
+    p.m = m;
+    p.K = 1 << m;
+    const double delta = (hi - lo) / p.K;
+    for (int k = 1; k < p.K; ++k) p.tf[k - 1] = round_up_to_float(lo + delta * k);
+    for (int k = 0; k < p.K; ++k) p.lab[k] = (uint8_t)label_of(k, label);
+    const int block = 256;
+    quantise_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(y, count, p, idx_out, bits_out);
+    QKD_LAUNCHED("quantise_kernel");
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_slice_llr(const float *x, int64_t count, int32_t m, int32_t j, double lo,
+                               double hi, double sigma_n, qkdrec_label label,
+                               const uint8_t *lower_bits, float *llr_out, void *stream) {
+    clear_error();
+    if (count < 0) QKD_FAIL(QKDREC_ERR_ARG, "count < 0");
+    if (m < 1 || m > kMaxM) QKD_FAIL(QKDREC_ERR_ARG, "m_slices=%d outside [1, %d]", m, kMaxM);
+    if (j < 0 || j >= m) QKD_FAIL(QKDREC_ERR_ARG, "slice j=%d outside [0, %d)", j, m);
+    if (!(lo < hi) || !(sigma_n > 0)) QKD_FAIL(QKDREC_ERR_ARG, "need lo < hi and sigma_n > 0");
+    if (label != QKDREC_LABEL_GRAY && label != QKDREC_LABEL_BINARY) QKD_FAIL(QKDREC_ERR_ARG, "bad label");
+    if (count == 0) return QKDREC_OK;
+    if (!x || !llr_out) QKD_FAIL(QKDREC_ERR_ARG, "x/llr_out NULL");
+    if (j > 0 && !lower_bits) QKD_FAIL(QKDREC_ERR_ARG, "lower_bits NULL for j=%d", j);
+    LlrParams p;
+    p.m = m;
+    p.K = 1 << m;
+    p.j = j;
+    const double delta = (hi - lo) / p.K;
+    p.td[0] = -INFINITY;
+    p.td[p.K] = INFINITY;
+    for (int k = 1; k < p.K; ++k) p.td[k] = lo + delta * k;
+    for (int k = 0; k <= p.K; ++k) p.tf[k] = (float)p.td[k];
+    for (int k = 0; k < p.K; ++k) p.k_of_label[label_of(k, label)] = (uint8_t)k;
+    p.inv_sigma = (float)(1.0 / sigma_n);
+    p.inv_sigma_d = 1.0 / sigma_n;
+    const int block = 128;
+    slice_llr_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(x, count, lower_bits, p, llr_out);
+    QKD_LAUNCHED("slice_llr_kernel");
+    return QKDREC_OK;
+}
+
+}  // extern "C"
