@@ -198,6 +198,35 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
                                   int32_t *iters_out, uint8_t *conv_out, float *post_out,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------- measurement */
+
+/* Per-kernel-class totals collected between qkdrec_profile_begin/end. */
+typedef struct {
+    char name[40];         /* kernel class, e.g. "check_flood_sp_f32" */
+    int64_t launches;      /* launches recorded */
+    double ms;             /* sum of CUDA-event durations of those launches */
+    double units;          /* work done: edge updates (check kernels), variable
+                              updates (variable kernels), samples (quantiser, LLR),
+                              check evaluations (syndrome) -- active frames only */
+    double bytes;          /* algorithmic bytes of that work (what the method must
+                              move: messages read+written, posteriors gathered, ...) */
+} qkdrec_kernel_stat;
+
+/*
+ * Start recording: every library launch made after this call (on any stream,
+ * from any thread) is bracketed by CUDA events on its stream, and its kernels
+ * add their work to device counters.  Allocates a small device buffer.
+ * Errors: QKDREC_ERR_ARG if already recording; QKDREC_ERR_CUDA.
+ */
+qkdrec_status qkdrec_profile_begin(void);
+
+/*
+ * Stop recording, synchronise the device, and write up to `capacity` kernel
+ * classes (HOST array) with their totals; *count gets the number written.
+ * Errors: QKDREC_ERR_ARG if not recording or NULL pointers; QKDREC_ERR_CUDA.
+ */
+qkdrec_status qkdrec_profile_end(qkdrec_kernel_stat *stats, int32_t capacity, int32_t *count);
+
 /* ------------------------------------------------------------ host helpers */
 
 /*

@@ -32,6 +32,7 @@ EXPORTED = [
     "qkdrec_quantise_slices", "qkdrec_slice_llr", "qkdrec_syndrome",
     "qkdrec_decode_opts_default", "qkdrec_decode_workspace_size", "qkdrec_decode_batch",
     "qkdrec_slice_capacity", "qkdrec_last_error", "qkdrec_version",
+    "qkdrec_profile_begin", "qkdrec_profile_end",
 ]
 
 
@@ -39,6 +40,11 @@ class QkdrecError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"qkdrec status {status}: {msg}")
         self.status = status
+
+
+class KernelStatC(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("units", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class DecodeOptsC(ctypes.Structure):
@@ -72,6 +78,8 @@ def lib():
         "qkdrec_decode_workspace_size": (U, [P, I32, P, P]),
         "qkdrec_decode_batch": (U, [P, P, P, I32, P, P, P, P, P, P, ctypes.c_size_t, P]),
         "qkdrec_slice_capacity": (U, [D, I32, I32, D, D, U, D, P]),
+        "qkdrec_profile_begin": (U, []),
+        "qkdrec_profile_end": (U, [P, I32, P]),
         "qkdrec_last_error": (ctypes.c_char_p, []),
         "qkdrec_version": (ctypes.c_char_p, []),
     }
@@ -285,3 +293,18 @@ def code_rate(capacity: float, fraction: float = 0.95, denom: int = 64) -> float
     (denom-1)/denom; 0.0 means the slice is disclosed."""
     k = int(np.floor(fraction * capacity * denom + 0.5))
     return max(min(k, denom - 1), 0) / denom
+
+
+# ------------------------------------------------------------- measurement
+def qkdrec_profile_begin():
+    """Start per-kernel-class event timing and work counters (see include/qkdrec.h)."""
+    _check(lib().qkdrec_profile_begin())
+
+
+def qkdrec_profile_end():
+    """Stop recording; returns {kernel class: dict(launches, ms, units, bytes)}."""
+    arr = (KernelStatC * 64)()
+    n = ctypes.c_int32()
+    _check(lib().qkdrec_profile_end(arr, 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, units=arr[i].units,
+                                       bytes=arr[i].bytes) for i in range(n.value)}

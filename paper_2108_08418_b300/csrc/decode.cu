@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "profile.cuh"
 
 namespace qkd {
 
@@ -117,6 +118,7 @@ struct DecArgs {
     int32_t early_stop;
     int32_t do_msgs;        // 0: parity test only
     float beta;             // OMS offset (float modes)
+    unsigned long long *prof;  // (units, bytes) counters of this launch's kernel class, or NULL
 };
 
 // Reduce 4-bit unsatisfied masks of the lanes that own the same frame vector,
@@ -145,12 +147,14 @@ check_flood_f(DecArgs a) {
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     const float *L = reinterpret_cast<const float *>(a.L);
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
+    unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv;
         const bool fv_ok = fv < a.FV;
         const uint32_t act = fv_ok ? active4(a.active, fv) : 0u;
         uint32_t unsat_bits = 0;
         if (act) {
+            const int nact = __popc(act & 0x01010101u);
             const int64_t c0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
             for (int it = 0; it < kChecksPerWarp; ++it) {
                 const int64_t c = c0 + it * slots + slot;
@@ -188,6 +192,7 @@ check_flood_f(DecArgs a) {
                     }
                 }
                 unsat_bits |= par;
+                units += (unsigned long long)(end - beg) * nact;
                 if (!a.do_msgs) continue;
                 for (int32_t e = beg; e < end; ++e) {
                     const int32_t v = __ldg(a.ci + e);
@@ -219,6 +224,8 @@ check_flood_f(DecArgs a) {
         if (a.early_stop || !a.do_msgs)
             publish_unsat(unsat_bits, fvw, lane, warp, fv, fv_ok, a.unsat_cur);
     }
+    // messages read + written and the posterior gathered, per active edge-frame
+    prof_add(a.prof, units, units * (a.do_msgs ? 2 * sizeof(MsgT) + 4 : 4));
 }
 
 // ----------------------------------------------------- integer check kernel
@@ -230,12 +237,14 @@ check_flood_i(DecArgs a) {
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     const int16_t *L = reinterpret_cast<const int16_t *>(a.L);
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
+    unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv;
         const bool fv_ok = fv < a.FV;
         const uint32_t act = fv_ok ? active4(a.active, fv) : 0u;
         uint32_t unsat_bits = 0;
         if (act) {
+            const int nact = __popc(act & 0x01010101u);
             const int64_t c0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
             for (int it = 0; it < kChecksPerWarp; ++it) {
                 const int64_t c = c0 + it * slots + slot;
@@ -261,6 +270,7 @@ check_flood_i(DecArgs a) {
                     }
                 }
                 unsat_bits |= par;
+                units += (unsigned long long)(end - beg) * nact;
                 if (!a.do_msgs) continue;
                 for (int32_t e = beg; e < end; ++e) {
                     const int32_t v = __ldg(a.ci + e);
@@ -284,6 +294,7 @@ check_flood_i(DecArgs a) {
         if (a.early_stop || !a.do_msgs)
             publish_unsat(unsat_bits, fvw, lane, warp, fv, fv_ok, a.unsat_cur);
     }
+    prof_add(a.prof, units, units * (a.do_msgs ? 4 : 2));
 }
 
 // ------------------------------------------------------------ variable kernels
@@ -293,6 +304,10 @@ template <int PREC>
 __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
     const int64_t total = (int64_t)a.n * a.FV;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // per updated variable-frame: its messages, its channel LLR, the new posterior
+    constexpr unsigned ms = PREC == kF32 ? 4 : (PREC == kF16 ? 2 : 1);
+    constexpr unsigned cs = PREC == kI8 ? 1 : 4, ls = PREC == kI8 ? 2 : 4;
+    unsigned long long units = 0, bytes = 0;
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
         const int64_t v = item / a.FV, fv = item - v * a.FV;
         const uint32_t act = active4(a.active, fv);
@@ -315,6 +330,9 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
         }
         if (!upd) continue;
         const int32_t vb = __ldg(a.vptr + v), ve = __ldg(a.vptr + v + 1);
+        const unsigned nu = __popc(upd);
+        units += nu;
+        bytes += (unsigned long long)nu * ((ve - vb) * ms + cs + ls);
         if (PREC != kI8) {
             float *L = reinterpret_cast<float *>(a.L);
             const float *llr = reinterpret_cast<const float *>(a.llr_i);
@@ -351,6 +369,7 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
             st_i16x4(L + item * 4, r);
         }
     }
+    prof_add(a.prof, units, bytes);
 }
 
 // ------------------------------------------------------- layout conversions
@@ -535,22 +554,28 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     a.do_msgs = 1;
     a.early_stop = o.early_stop ? 1 : 0;
     a.beta = o.offset;
+    a.prof = nullptr;
     pr.unsat[0] = reinterpret_cast<uint32_t *>(ws + l.unsat0);
     pr.unsat[1] = reinterpret_cast<uint32_t *>(ws + l.unsat1);
     pr.mask = reinterpret_cast<uint8_t *>(ws + l.mask);
     a.unsat_cur = pr.unsat[0];
     a.unsat_next = pr.unsat[1];
 
-    init_state<<<(unsigned)ceil_div(l.Fp, 256), 256, 0, st>>>(F, l.Fp, conv_prev, a.active, pr.mask,
-                                                             a.iters_i, pr.unsat[0], pr.unsat[1]);
+    {
+        prof::Scope ps(prof::kPrep, st);
+        init_state<<<(unsigned)ceil_div(l.Fp, 256), 256, 0, st>>>(F, l.Fp, conv_prev, a.active, pr.mask,
+                                                                 a.iters_i, pr.unsat[0], pr.unsat[1]);
+    }
     QKD_LAUNCHED("init_state");
     {
+        prof::Scope ps(prof::kPrep, st);
         dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
         if (prec == kI8) prep_llr<kI8><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, o.llr_step, ws + l.llr_i, ws + l.L);
         else prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, o.llr_step, ws + l.llr_i, ws + l.L);
         QKD_LAUNCHED("prep_llr");
     }
     {
+        prof::Scope ps(prof::kPrep, st);
         dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)l.W);
         prep_synd<<<grd, 256, 0, st>>>(synd, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits));
         QKD_LAUNCHED("prep_synd");
@@ -566,9 +591,13 @@ static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const 
                             const uint8_t *conv_prev, char *ws, const Layout &l, const Prepared &pr,
                             const DecArgs &a, int final_buf, uint8_t *bits_out, int32_t *iters_out,
                             uint8_t *conv_out, float *post_out, cudaStream_t st) {
-    finalize<<<(unsigned)ceil_div(F, 256), 256, 0, st>>>(F, T, conv_prev ? 1 : 0, pr.mask, a.active, a.iters_i,
-                                                         pr.unsat[final_buf], iters_out, conv_out);
+    {
+        prof::Scope ps(prof::kFinish, st);
+        finalize<<<(unsigned)ceil_div(F, 256), 256, 0, st>>>(F, T, conv_prev ? 1 : 0, pr.mask, a.active,
+                                                             a.iters_i, pr.unsat[final_buf], iters_out, conv_out);
+    }
     QKD_LAUNCHED("finalize");
+    prof::Scope ps(prof::kFinish, st);
     dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
     if (prec == kI8) write_out<kI8><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, o.llr_step, pr.mask, bits_out, post_out);
     else write_out<kF32><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, o.llr_step, pr.mask, bits_out, post_out);
@@ -598,6 +627,12 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
         a.do_msgs = do_msgs;
         a.unsat_cur = pr.unsat[t & 1];
         a.unsat_next = pr.unsat[(t + 1) & 1];
+        const int kind = !do_msgs ? (prec == kI8 ? prof::kParityI8 : prof::kParityF32)
+                         : prec == kI8 ? prof::kCheckOmsI8
+                         : o.algo == QKDREC_SP_FLOOD ? (prec == kF32 ? prof::kCheckSpF32 : prof::kCheckSpF16)
+                                                     : (prec == kF32 ? prof::kCheckOmsF32 : prof::kCheckOmsF16);
+        a.prof = prof::counters(kind);
+        prof::Scope ps(kind, st);
         if (prec == kI8) check_flood_i<true><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
         else if (o.algo == QKDREC_SP_FLOOD) {
             if (prec == kF32) check_flood_f<kSP, float><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
@@ -611,9 +646,14 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
         check(t, 1);
         QKD_LAUNCHED("check_flood");
         a.t = t;
-        if (prec == kI8) var_flood<kI8><<<vgrid, 256, 0, st>>>(a);
-        else if (prec == kF16) var_flood<kF16><<<vgrid, 256, 0, st>>>(a);
-        else var_flood<kF32><<<vgrid, 256, 0, st>>>(a);
+        {
+            const int kind = prec == kI8 ? prof::kVarI8 : (prec == kF16 ? prof::kVarF16 : prof::kVarF32);
+            a.prof = prof::counters(kind);
+            prof::Scope ps(kind, st);
+            if (prec == kI8) var_flood<kI8><<<vgrid, 256, 0, st>>>(a);
+            else if (prec == kF16) var_flood<kF16><<<vgrid, 256, 0, st>>>(a);
+            else var_flood<kF32><<<vgrid, 256, 0, st>>>(a);
+        }
         QKD_LAUNCHED("var_flood");
     }
     // stopping test on the final posteriors (parity buffer (T+1)&1 is clear)

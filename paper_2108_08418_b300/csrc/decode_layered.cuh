@@ -18,11 +18,13 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     float *L = reinterpret_cast<float *>(a.L);
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
+    unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv;
         if (fv >= a.FV) continue;
         const uint32_t act = active4(a.active, fv);
         if (!act) continue;
+        const int nact = __popc(act & 0x01010101u);
         const int64_t k0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
         for (int it = 0; it < kChecksPerWarp; ++it) {
             const int64_t k = k0 + it * slots + slot;
@@ -31,6 +33,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1);
             const uint32_t sw = __ldg(a.sbits + (int64_t)c * a.W + ((4 * fv) >> 5));
             uint32_t neg = (sw >> ((4 * fv) & 31)) & 0xfu;
+            units += (unsigned long long)(end - beg) * nact;
             float mn1[4], mn2[4];
             int32_t arg[4];
             for (int i = 0; i < 4; ++i) { mn1[i] = INFINITY; mn2[i] = INFINITY; arg[i] = -1; }
@@ -70,6 +73,8 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             }
         }
     }
+    // posterior read + written and message read + written, per active edge-frame
+    prof_add(a.prof, units, units * (2 * sizeof(MsgT) + 8));
 }
 
 // ---------------------------------------------------------- integer layered
@@ -80,11 +85,13 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     int16_t *L = reinterpret_cast<int16_t *>(a.L);
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
+    unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv;
         if (fv >= a.FV) continue;
         const uint32_t act = active4(a.active, fv);
         if (!act) continue;
+        const int nact = __popc(act & 0x01010101u);
         const int64_t k0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
         for (int it = 0; it < kChecksPerWarp; ++it) {
             const int64_t k = k0 + it * slots + slot;
@@ -93,6 +100,7 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1);
             const uint32_t sw = __ldg(a.sbits + (int64_t)c * a.W + ((4 * fv) >> 5));
             uint32_t neg = (sw >> ((4 * fv) & 31)) & 0xfu;
+            units += (unsigned long long)(end - beg) * nact;
             int mn1[4], mn2[4], arg[4];
             for (int i = 0; i < 4; ++i) { mn1[i] = 1 << 20; mn2[i] = 1 << 20; arg[i] = -1; }
             for (int32_t e = beg; e < end; ++e) {
@@ -130,6 +138,7 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             }
         }
     }
+    prof_add(a.prof, units, units * (2 * 1 + 2 * 2));
 }
 
 // Retire frames whose stopping test passed after iteration t (iters = t) and
@@ -166,12 +175,16 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *syn
         a.early_stop = 1;
         a.unsat_cur = pr.unsat[t & 1];
         a.unsat_next = pr.unsat[(t + 1) & 1];
+        const int kind = prec == kI8 ? prof::kParityI8 : prof::kParityF32;
+        a.prof = prof::counters(kind);
+        prof::Scope ps(kind, st);
         dim3 cgrid((unsigned)ceil_div(d.M, checks_per_block), gy);
         if (prec == kI8) check_flood_i<true><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
         else if (prec == kF16) check_flood_f<kOMS, __half><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
         else check_flood_f<kOMS, float><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
     };
     auto retire_at = [&](int t) {
+        prof::Scope ps(prof::kFinish, st);
         retire<<<(unsigned)ceil_div(l.Fp, 256), 256, 0, st>>>(l.Fp, t, a.active, a.iters_i, pr.unsat[t & 1],
                                                              pr.unsat[(t + 1) & 1]);
     };
@@ -181,7 +194,10 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *syn
         QKD_LAUNCHED("retire");
     }
     for (int t = 1; t <= T; ++t) {
+        const int lkind = prec == kI8 ? prof::kLayerI8 : (prec == kF16 ? prof::kLayerF16 : prof::kLayerF32);
+        a.prof = prof::counters(lkind);
         for (int32_t ly = 0; ly < d.n_layers; ++ly) {
+            prof::Scope ps(lkind, st);
             const int32_t lb = lptr[ly], ls = lptr[ly + 1] - lptr[ly];
             dim3 g((unsigned)ceil_div(ls, checks_per_block), gy);
             if (prec == kI8) layer_oms_i<<<g, kCheckWarps * 32, 0, st>>>(a, d.layer_chk, lb, ls);

@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "profile.cuh"
 
 namespace qkd {
 
@@ -19,7 +20,8 @@ struct QuantParams {
 // y >= t (FP64) is the same test as y >= tf (t rounded up to a float).
 // NaN compares "not below" every threshold, so it lands in the last bin.
 __global__ void quantise_kernel(const float *__restrict__ y, int64_t count, QuantParams p,
-                                uint8_t *__restrict__ idx_out, uint8_t *__restrict__ bits_out) {
+                                uint8_t *__restrict__ idx_out, uint8_t *__restrict__ bits_out,
+                                unsigned long long *prof) {
     // per-lane table lookups diverge: stage the tables in shared memory
     __shared__ float tf[kMaxK];
     __shared__ uint8_t lab_s[kMaxK];
@@ -29,7 +31,9 @@ __global__ void quantise_kernel(const float *__restrict__ y, int64_t count, Quan
     }
     __syncthreads();
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long units = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        ++units;
         float v = y[i];
         int k = 0;
         for (int s = p.K >> 1; s >= 1; s >>= 1)
@@ -40,6 +44,8 @@ __global__ void quantise_kernel(const float *__restrict__ y, int64_t count, Quan
             for (int j = 0; j < p.m; ++j) bits_out[(int64_t)j * count + i] = (uint8_t)((lab >> j) & 1);
         }
     }
+    // y read, index and bit planes written
+    prof_add(prof, units, units * (4 + (idx_out ? 1 : 0) + (bits_out ? p.m : 0)));
 }
 
 // ------------------------------------------------------------------ slice LLR
@@ -106,7 +112,7 @@ __device__ __forceinline__ float interval_dist(const LlrParams &p, int k, float 
 
 __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
                                  const uint8_t *__restrict__ lower, const LlrParams p_in,
-                                 float *__restrict__ out) {
+                                 float *__restrict__ out, unsigned long long *prof) {
     // per-lane table lookups diverge: stage the tables in shared memory
     __shared__ LlrParams sp;
     {
@@ -119,7 +125,9 @@ __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
     const LlrParams &p = sp;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int nc = p.K >> p.j;  // candidates consistent with the lower bits
+    unsigned long long units = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        ++units;
         float x = xs[i];
         double xd = (double)x;
         int low = 0;
@@ -162,6 +170,8 @@ __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
         }
         out[i] = llr;
     }
+    // x and the lower bits read, the LLR written
+    prof_add(prof, units, units * (8 + p.j));
 }
 
 static int label_of(int k, qkdrec_label lab) { return lab == QKDREC_LABEL_BINARY ? k : (k ^ (k >> 1)); }
@@ -201,7 +211,9 @@ qkdrec_status qkdrec_quantise_slices(const float *y, int64_t count, int32_t m, d
     for (int k = 1; k < p.K; ++k) p.tf[k - 1] = round_up_to_float(lo + delta * k);
     for (int k = 0; k < p.K; ++k) p.lab[k] = (uint8_t)label_of(k, label);
     const int block = 256;
-    quantise_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(y, count, p, idx_out, bits_out);
+    prof::Scope ps(prof::kQuantise, as_stream(stream));
+    quantise_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(y, count, p, idx_out, bits_out,
+                                                                             prof::counters(prof::kQuantise));
     QKD_LAUNCHED("quantise_kernel");
     return QKDREC_OK;
 }
@@ -231,7 +243,9 @@ qkdrec_status qkdrec_slice_llr(const float *x, int64_t count, int32_t m, int32_t
     p.inv_sigma = (float)(1.0 / sigma_n);
     p.inv_sigma_d = 1.0 / sigma_n;
     const int block = 128;
-    slice_llr_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(x, count, lower_bits, p, llr_out);
+    prof::Scope ps(prof::kSliceLlr, as_stream(stream));
+    slice_llr_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(x, count, lower_bits, p, llr_out,
+                                                                              prof::counters(prof::kSliceLlr));
     QKD_LAUNCHED("slice_llr_kernel");
     return QKDREC_OK;
 }

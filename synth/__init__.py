@@ -7,9 +7,9 @@ CUDA library consume what it returns, so it is the one piece they share.
 * Quadratures (Sec. V, "Decoding Error and Time" set-up): Alice's
   x_i ~ N(0, V_A) with V_A = 1, Bob's y_i = x_i + n_i, n_i ~ N(0, sigma_n^2),
   sigma_n^2 = 1/SNR.  Normal draws come from numpy's Philox-4x32-10
-  counter-based generator (Salmon et al., SC'11) keyed by the seed: first the
-  `count` values of x, then the `count` noise values.  Both arrays are
-  returned as float32 (y is rounded once, after the FP64 addition).
+  counter-based generator (Salmon et al., SC'11), x from key (seed, 0) and the
+  noise from key (seed, 1).  Both arrays are returned as float32 (y is rounded
+  once, after the FP64 addition).
 * Parity-check matrices: random left-regular LDPC codes (variable degree dv,
   check degrees floor/ceil of dv*n/M), placed by a Philox-drawn socket
   permutation, with double edges and 4-cycles broken by seeded socket swaps
@@ -61,10 +61,16 @@ def philox(seed: int) -> np.random.Generator:
 
 
 def gaussian_pair(seed: int, count: int, snr: float, va: float = 1.0):
-    """(x, y) float32 arrays of length `count`: x ~ N(0, va), y = x + N(0, 1/snr)."""
-    g = philox(seed)
-    x = g.standard_normal(count) * np.sqrt(va)
-    noise = g.standard_normal(count) * np.sqrt(1.0 / snr)
+    """(x, y) float32 arrays of length `count`: x ~ N(0, va), y = x + N(0, 1/snr).
+
+    x and the noise come from two Philox streams (keys (seed, 0) and (seed, 1)),
+    so the first k samples do not depend on `count`: any prefix of a long
+    block can be regenerated on its own.
+    """
+    gx = np.random.Generator(np.random.Philox(key=[int(seed), 0]))
+    gn = np.random.Generator(np.random.Philox(key=[int(seed), 1]))
+    x = gx.standard_normal(count) * np.sqrt(va)
+    noise = gn.standard_normal(count) * np.sqrt(1.0 / snr)
     y = x + noise
     return x.astype(np.float32), y.astype(np.float32)
 

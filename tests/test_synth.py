@@ -43,3 +43,9 @@ def test_gaussian_pair_statistics():
     assert abs(np.corrcoef(x, n)[0, 1]) < 5e-3
     x2, y2 = synth.gaussian_pair(3, 1000, 3.0)
     assert np.array_equal(x2, synth.gaussian_pair(3, 1000, 3.0)[0])
+
+
+def test_gaussian_pair_prefix_consistent():
+    x1, y1 = synth.gaussian_pair(9, 5000, 15.0)
+    x2, y2 = synth.gaussian_pair(9, 123, 15.0)
+    assert np.array_equal(x1[:123], x2) and np.array_equal(y1[:123], y2)
