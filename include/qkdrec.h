@@ -129,10 +129,12 @@ qkdrec_status qkdrec_quantise_slices(const float *y, int64_t count, int32_t m_sl
  *             reconciled lower bits of sample i },
  *   P(k | x) = Phi((t_{k+1} - x)/sigma_n) - Phi((t_k - x)/sigma_n), t_0 = -inf,
  *   t_{2^m} = +inf, the thresholds of qkdrec_quantise_slices.
- * The result is clipped to [-30, 30].  Interval probabilities near x are
- * evaluated in FP32; intervals whose nearer edge lies more than 5 sigma_n from
- * x (Gaussian tails) in FP64; terms below 1e-11 of their set's nearest term
- * and sets that cannot move the clipped result are skipped.
+ * The result is clipped to [-30, 30].  Interval probabilities are evaluated
+ * in FP32 in the log domain (Gaussian tails through the scaled complementary
+ * error function, so no tail underflows); when every candidate of both sets
+ * lies in the far tail (nearest term below e^-50) the two set sums are formed
+ * in FP64.  Terms below e^-25 of their set's nearest term, and a set that
+ * cannot move the clipped result, are skipped.
  *   x           DEVICE float [count]       Alice's quadratures.
  *   lower_bits  DEVICE uint8 [j][count]    reconciled slices 0..j-1 (NULL iff j = 0).
  *   llr_out     DEVICE float [count].

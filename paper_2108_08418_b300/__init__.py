@@ -34,6 +34,7 @@ EXPORTED = [
     "qkdrec_slice_capacity", "qkdrec_last_error", "qkdrec_version",
     "qkdrec_profile_begin", "qkdrec_profile_end",
 ]
+SELFTEST = ["qkdrec_selftest_phi"]
 
 
 class QkdrecError(RuntimeError):
@@ -79,6 +80,7 @@ def lib():
         "qkdrec_decode_batch": (U, [P, P, P, I32, P, P, P, P, P, P, ctypes.c_size_t, P]),
         "qkdrec_slice_capacity": (U, [D, I32, I32, D, D, U, D, P]),
         "qkdrec_profile_begin": (U, []),
+        "qkdrec_selftest_phi": (U, [P, I64, P, P]),
         "qkdrec_profile_end": (U, [P, I32, P]),
         "qkdrec_last_error": (ctypes.c_char_p, []),
         "qkdrec_version": (ctypes.c_char_p, []),
@@ -308,3 +310,13 @@ def qkdrec_profile_end():
     _check(lib().qkdrec_profile_end(arr, 64, ctypes.byref(n)))
     return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, units=arr[i].units,
                                        bytes=arr[i].bytes) for i in range(n.value)}
+
+
+# ---------------------------------------------------------------- self-test
+def qkdrec_selftest_phi(x):
+    """phi(clamp(x)) evaluated by the sum-product kernels' device function."""
+    torch = _torch()
+    xp = _dev(x, torch.float32, "x")
+    out = torch.empty_like(x)
+    _check(lib().qkdrec_selftest_phi(xp, x.numel(), ctypes.c_void_p(out.data_ptr()), _stream(x)))
+    return out

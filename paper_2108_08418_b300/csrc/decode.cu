@@ -3,18 +3,17 @@
 //
 // Data layout (frame-interleaved): every per-variable or per-edge quantity is
 // stored as [item][Fp] with the frame index fastest, Fp = F rounded up to a
-// multiple of 4.  A lane owns a "frame vector" of 4 consecutive frames, so each
-// access is a 16-byte (FP32), 8-byte (FP16) or 4-byte (int8) vector and a warp
-// touches one contiguous run per edge: the column index of an edge is loaded
-// once and reused by all frames.
+// multiple of 4.  A lane owns V consecutive frames (V = 1 or 4), so the warp
+// touches one contiguous run of 32 V elements per edge and the column index of
+// an edge is loaded once for all of them.
 //
 //   llr_i [n][Fp]   channel LLR (float; int8 on the 6-bit grid in integer mode)
 //   L     [n][Fp]   posterior (float; int16 in integer mode)
 //   msg   [E][Fp]   check-to-variable messages in CSR edge order (float/half/int8)
-//   sbits [M][W]    syndrome bits, 32 frames per word
+//   sbits [M][W]    syndrome bits, bit f%32 of word f/32 (W = Fp/32 rounded up)
 //   active[Fp]      1 while the frame is decoding
-//   unsat [2][Fp/4] per frame vector: bit i set if frame 4fv+i had an
-//                   unsatisfied check (double-buffered by iteration parity)
+//   unsat [2][W]    bit f%32 of word f/32 set if frame f failed a check in the
+//                   stopping test (double-buffered by iteration parity)
 //
 // One iteration = check kernel + variable kernel.  The check kernel of
 // iteration t reads L^(t-1) for every edge anyway, so it also forms the parity
@@ -22,6 +21,10 @@
 // the previous iteration, at no extra traffic.  The variable kernel of
 // iteration t then retires frames whose test passed (iters = t-1, posterior
 // frozen) and updates the others.
+//
+// Check kernels keep the per-edge state of pass 1 (phi values, or the v->c
+// signs) in registers for checks of degree <= DCMAX, so pass 2 only computes
+// and stores the outgoing messages; larger degrees use a variant that reloads.
 #include <math.h>
 
 #include <algorithm>
@@ -29,6 +32,7 @@
 
 #include "common.cuh"
 #include "profile.cuh"
+#include "qkdrec_selftest.h"
 
 namespace qkd {
 
@@ -40,65 +44,133 @@ constexpr int kChecksPerWarp = 4;
 constexpr int32_t kMaxFrames = 65535 * 32;  // syndrome packing uses one grid row per 32 frames
 
 // ---------------------------------------------------------------- vector I/O
-struct F4 { float v[4]; };
+template <int V> struct VF { float v[V]; };
+template <int V> struct VI { int v[V]; };
 
-__device__ __forceinline__ F4 ld_f4(const float *p) {
-    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-    return F4{{t.x, t.y, t.z, t.w}};
+template <int V> __device__ __forceinline__ VF<V> ldf(const float *p);
+template <> __device__ __forceinline__ VF<1> ldf<1>(const float *p) { return VF<1>{{__ldg(p)}}; }
+template <> __device__ __forceinline__ VF<4> ldf<4>(const float *p) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    return VF<4>{{t.x, t.y, t.z, t.w}};
 }
-__device__ __forceinline__ void st_f4(float *p, const F4 &a) {
+template <int V> __device__ __forceinline__ VF<V> ldf_plain(const float *p);  // coherent (written in-kernel)
+template <> __device__ __forceinline__ VF<1> ldf_plain<1>(const float *p) { return VF<1>{{*p}}; }
+template <> __device__ __forceinline__ VF<4> ldf_plain<4>(const float *p) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    return VF<4>{{t.x, t.y, t.z, t.w}};
+}
+template <int V> __device__ __forceinline__ void stf(float *p, const VF<V> &a);
+template <> __device__ __forceinline__ void stf<1>(float *p, const VF<1> &a) { *p = a.v[0]; }
+template <> __device__ __forceinline__ void stf<4>(float *p, const VF<4> &a) {
     *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
 }
-__device__ __forceinline__ F4 ld_msg(const float *p) { return ld_f4(p); }
-__device__ __forceinline__ void st_msg(float *p, const F4 &a) { st_f4(p, a); }
-__device__ __forceinline__ F4 ld_msg(const __half *p) {
+
+// messages: float or half storage, float arithmetic
+template <int V> __device__ __forceinline__ VF<V> ldm(const float *p) { return ldf<V>(p); }
+template <int V> __device__ __forceinline__ void stm(float *p, const VF<V> &a) { stf<V>(p, a); }
+template <int V> __device__ __forceinline__ VF<V> ldm(const __half *p);
+template <> __device__ __forceinline__ VF<1> ldm<1>(const __half *p) { return VF<1>{{__half2float(__ldg(p))}}; }
+template <> __device__ __forceinline__ VF<4> ldm<4>(const __half *p) {
     uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-    __half2 a = *reinterpret_cast<__half2 *>(&t.x), b = *reinterpret_cast<__half2 *>(&t.y);
-    float2 fa = __half22float2(a), fb = __half22float2(b);
-    return F4{{fa.x, fa.y, fb.x, fb.y}};
+    const float2 a = __half22float2(*reinterpret_cast<__half2 *>(&t.x));
+    const float2 b = __half22float2(*reinterpret_cast<__half2 *>(&t.y));
+    return VF<4>{{a.x, a.y, b.x, b.y}};
 }
-__device__ __forceinline__ void st_msg(__half *p, const F4 &a) {
+template <int V> __device__ __forceinline__ void stm(__half *p, const VF<V> &a);
+template <> __device__ __forceinline__ void stm<1>(__half *p, const VF<1> &a) { *p = __float2half_rn(a.v[0]); }
+template <> __device__ __forceinline__ void stm<4>(__half *p, const VF<4> &a) {
     __half2 x = __floats2half2_rn(a.v[0], a.v[1]), y = __floats2half2_rn(a.v[2], a.v[3]);
     uint2 t;
     t.x = *reinterpret_cast<uint32_t *>(&x);
     t.y = *reinterpret_cast<uint32_t *>(&y);
     *reinterpret_cast<uint2 *>(p) = t;
 }
+// value a message has once stored (FP16 rounding; identity for FP32)
+__device__ __forceinline__ float as_stored(float x, const float *) { return x; }
+__device__ __forceinline__ float as_stored(float x, const __half *) { return __half2float(__float2half_rn(x)); }
 
-// value a message has after being stored (FP16 rounding, identity for FP32)
-template <typename MsgT> __device__ __forceinline__ F4 as_stored(const F4 &a);
-template <> __device__ __forceinline__ F4 as_stored<float>(const F4 &a) { return a; }
-template <> __device__ __forceinline__ F4 as_stored<__half>(const F4 &a) {
-    F4 r;
-    for (int i = 0; i < 4; ++i) r.v[i] = __half2float(__float2half_rn(a.v[i]));
+// integer posteriors (int16) and messages / channel values (int8)
+template <int V> __device__ __forceinline__ VI<V> ldi16(const int16_t *p);
+template <> __device__ __forceinline__ VI<1> ldi16<1>(const int16_t *p) { return VI<1>{{*p}}; }
+template <> __device__ __forceinline__ VI<4> ldi16<4>(const int16_t *p) {
+    const short4 t = *reinterpret_cast<const short4 *>(p);
+    return VI<4>{{t.x, t.y, t.z, t.w}};
+}
+template <int V> __device__ __forceinline__ void sti16(int16_t *p, const VI<V> &a);
+template <> __device__ __forceinline__ void sti16<1>(int16_t *p, const VI<1> &a) { *p = (int16_t)a.v[0]; }
+template <> __device__ __forceinline__ void sti16<4>(int16_t *p, const VI<4> &a) {
+    *reinterpret_cast<short4 *>(p) = make_short4((short)a.v[0], (short)a.v[1], (short)a.v[2], (short)a.v[3]);
+}
+template <int V> __device__ __forceinline__ VI<V> ldi8(const int8_t *p);
+template <> __device__ __forceinline__ VI<1> ldi8<1>(const int8_t *p) { return VI<1>{{*p}}; }
+template <> __device__ __forceinline__ VI<4> ldi8<4>(const int8_t *p) {
+    const char4 t = *reinterpret_cast<const char4 *>(p);
+    return VI<4>{{t.x, t.y, t.z, t.w}};
+}
+template <int V> __device__ __forceinline__ void sti8(int8_t *p, const VI<V> &a);
+template <> __device__ __forceinline__ void sti8<1>(int8_t *p, const VI<1> &a) { *p = (int8_t)a.v[0]; }
+template <> __device__ __forceinline__ void sti8<4>(int8_t *p, const VI<4> &a) {
+    *reinterpret_cast<char4 *>(p) = make_char4((signed char)a.v[0], (signed char)a.v[1], (signed char)a.v[2],
+                                                (signed char)a.v[3]);
+}
+
+// column index read again in a second pass (volatile: not kept live from pass 1)
+__device__ __forceinline__ int32_t ld_index_again(const int32_t *p) {
+    int32_t r;
+    asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(r) : "l"(p));
     return r;
 }
 
-struct I4 { int v[4]; };
-__device__ __forceinline__ I4 ld_i8x4(const int8_t *p) {
-    char4 t = __ldg(reinterpret_cast<const char4 *>(p));
-    return I4{{t.x, t.y, t.z, t.w}};
-}
-__device__ __forceinline__ void st_i8x4(int8_t *p, const I4 &a) {
-    *reinterpret_cast<char4 *>(p) = make_char4((signed char)a.v[0], (signed char)a.v[1],
-                                                (signed char)a.v[2], (signed char)a.v[3]);
-}
-__device__ __forceinline__ I4 ld_i16x4(const int16_t *p) {
-    short4 t = __ldg(reinterpret_cast<const short4 *>(p));
-    return I4{{t.x, t.y, t.z, t.w}};
-}
-__device__ __forceinline__ void st_i16x4(int16_t *p, const I4 &a) {
-    *reinterpret_cast<short4 *>(p) = make_short4((short)a.v[0], (short)a.v[1], (short)a.v[2], (short)a.v[3]);
+// active flags of V frames as a bit mask (bit i = frame f0 + i)
+template <int V> __device__ __forceinline__ uint32_t active_bits(const uint8_t *p);
+template <> __device__ __forceinline__ uint32_t active_bits<1>(const uint8_t *p) { return *p ? 1u : 0u; }
+template <> __device__ __forceinline__ uint32_t active_bits<4>(const uint8_t *p) {
+    const uint32_t w = *reinterpret_cast<const uint32_t *>(p);
+    return (w & 1u) | ((w >> 7) & 2u) | ((w >> 14) & 4u) | ((w >> 21) & 8u);
 }
 
-// phi(x) = -ln tanh(x/2) = ln((e^x + 1)/(e^x - 1)), evaluated as log1p(2 / expm1(x));
-// it is its own inverse on (0, inf).
-__device__ __forceinline__ float phi_f(float x) { return log1pf(2.0f / expm1f(x)); }
-
-__device__ __forceinline__ uint32_t active4(const uint8_t *active, int64_t fv) {
-    return *reinterpret_cast<const uint32_t *>(active + 4 * fv);  // byte i = frame 4fv+i
+// ------------------------------------------------------------------- phi
+// phi(x) = -ln tanh(x/2) = ln((1 + u)/(1 - u)), u = e^-x, on [kAMin, kAMax]; it is
+// its own inverse.  Written from these identities and two Taylor series,
+// evaluated with the MUFU ex2/rcp/lg2 approximations (about 1e-6 relative):
+//   x >= 2       : u <= 0.135 and phi = 2 atanh(u) = 2u (1 + u^2/3 + u^4/5 + u^6/7) + O(u^9);
+//   0.5 <= x < 2 : phi = log2((1 + u)/(1 - u)) ln 2 with 1 - u >= 0.39 (no cancellation);
+//   x < 0.5      : 1 - u = 1 - e^-x from its Taylor series
+//                  x (1 - x/2 (1 - x/3 (1 - x/4 (1 - x/5 (1 - x/6 (1 - x/7 (1 - x/8))))))),
+//                  1 + u = 2 - (1 - u).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
-__device__ __forceinline__ bool act_bit(uint32_t a4, int i) { return (a4 >> (8 * i)) & 0xff; }
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float phi_fast(float x) {
+    const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+    const float u = ex2_approx(-x * kLog2e);
+    const float u2 = u * u;
+    const float series = 2.0f * u * (1.0f + u2 * (1.0f / 3.0f + u2 * (0.2f + u2 * (1.0f / 7.0f))));
+    float t = 1.0f - x * 0.125f;
+    t = 1.0f - x * (1.0f / 7.0f) * t;
+    t = 1.0f - x * (1.0f / 6.0f) * t;
+    t = 1.0f - x * 0.2f * t;
+    t = 1.0f - x * 0.25f * t;
+    t = 1.0f - x * (1.0f / 3.0f) * t;
+    t = 1.0f - x * 0.5f * t;
+    const float den = x < 0.5f ? x * t : 1.0f - u;
+    const float num = 2.0f - den;
+    const float r = lg2_approx(num * rcp_approx(den)) * kLn2;
+    return x >= 2.0f ? series : r;
+}
+__device__ __forceinline__ float phi_clamped(float x) { return phi_fast(fminf(fmaxf(x, kAMin), kAMax)); }
 
 // ------------------------------------------------------------- kernel args
 struct DecArgs {
@@ -111,9 +183,9 @@ struct DecArgs {
     void *L;
     void *msg;
     const void *llr_i;
-    int64_t FV, W;
+    int64_t Fp, FV, W;      // FV = Fp / 4 (the variable kernel's frame vectors)
     int32_t n, M;
-    int32_t fvw;            // frame vectors per warp row (power of two <= 32)
+    int32_t fvw;            // lanes per check row in check kernels (power of two <= 32)
     int32_t t;              // iteration index (1-based)
     int32_t early_stop;
     int32_t do_msgs;        // 0: parity test only
@@ -121,115 +193,169 @@ struct DecArgs {
     unsigned long long *prof;  // (units, bytes) counters of this launch's kernel class, or NULL
 };
 
-// Reduce 4-bit unsatisfied masks of the lanes that own the same frame vector,
-// across the warp and the block, then publish them with one atomic per vector.
-__device__ __forceinline__ void publish_unsat(uint32_t bits, int fvw, int lane, int warp,
-                                              int64_t fv, bool fv_ok, uint32_t *unsat) {
-    __shared__ uint32_t blk[32];
-    for (int m = fvw; m < 32; m <<= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, m);
-    if (threadIdx.x < 32) blk[threadIdx.x] = 0;
+// Merge the lanes' stopping-test bits (V bits at frame f0) into the 32-frame
+// words of this block's frame range, then publish each non-zero word with one
+// global atomic.
+template <int V>
+__device__ __forceinline__ void publish_unsat(uint32_t bits, int64_t f0, int64_t fbase, bool ok,
+                                              uint32_t *unsat) {
+    __shared__ uint32_t blk[8];
+    if (threadIdx.x < 8) blk[threadIdx.x] = 0;
     __syncthreads();
-    if (lane < fvw && bits) atomicOr(&blk[lane], bits);
+    const int wi = (int)((f0 >> 5) - (fbase >> 5));
+    if (ok && bits) atomicOr(&blk[wi], bits << (f0 & 31));
     __syncthreads();
-    if (warp == 0 && lane < fvw && fv_ok && blk[lane]) atomicOr(&unsat[fv], blk[lane]);
+    if (threadIdx.x < 8 && blk[threadIdx.x]) atomicOr(&unsat[(fbase >> 5) + threadIdx.x], blk[threadIdx.x]);
 }
 
 // --------------------------------------------------------- float check kernel
 // Lane layout: lane = slot * fvw + lfv; the warp serves 32/fvw checks at a time
-// (one per slot) over fvw frame vectors.  blockIdx.x walks check groups (so the
-// resident blocks share one range of frames and their posterior gathers hit L2),
-// blockIdx.y walks frame-vector ranges.
-template <int ALGO, typename MsgT>
-__global__ void __launch_bounds__(kCheckWarps * 32)
+// (one per slot) over fvw frame vectors of V frames.  blockIdx.x walks check
+// groups (so the resident blocks share one range of frames and their
+// posterior gathers hit L2), blockIdx.y walks frame ranges.
+template <int ALGO, typename MsgT, int V, int DCMAX>
+__global__ void __launch_bounds__(kCheckWarps * 32, 2)
 check_flood_f(DecArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     const float *L = reinterpret_cast<const float *>(a.L);
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
+    const int64_t nvec = a.Fp / V;
+    const uint32_t vmask = (1u << V) - 1u;
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
-        const int64_t fv = fb * fvw + lfv;
-        const bool fv_ok = fv < a.FV;
-        const uint32_t act = fv_ok ? active4(a.active, fv) : 0u;
+    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+        const int64_t fv = fb * fvw + lfv, f0 = fv * V;
+        const bool fv_ok = fv < nvec;
+        const uint32_t act = fv_ok ? active_bits<V>(a.active + f0) : 0u;
         uint32_t unsat_bits = 0;
         if (act) {
-            const int nact = __popc(act & 0x01010101u);
+            const int nact = __popc(act);
             const int64_t c0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
             for (int it = 0; it < kChecksPerWarp; ++it) {
                 const int64_t c = c0 + it * slots + slot;
                 if (c >= a.M) break;
-                const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1);
-                const uint32_t sw = __ldg(a.sbits + c * a.W + ((4 * fv) >> 5));
-                const uint32_t s4 = (sw >> ((4 * fv) & 31)) & 0xfu;
-                uint32_t par = s4;          // syndrome xor hard decisions of L
-                uint32_t neg = s4;          // syndrome xor signs of q
-                float acc0[4], acc1[4];     // SP: sum of phi except the largest, largest phi
-                int32_t arg[4];             //     OMS: min1, min2
-                for (int i = 0; i < 4; ++i) {
+                const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1), d = end - beg;
+                const uint32_t s = (__ldg(a.sbits + c * a.W + (f0 >> 5)) >> (f0 & 31)) & vmask;
+                uint32_t par = s;           // syndrome xor hard decisions of L
+                uint32_t sg[V];             // bit k: q of edge k negative
+                float acc0[V], acc1[V];     // SP: sum of phi except the largest, largest phi
+                int32_t arg[V];             // OMS: min1, min2
+                float fc[DCMAX > 0 ? DCMAX : 1][V];
+                for (int i = 0; i < V; ++i) {
+                    sg[i] = 0;
                     acc0[i] = ALGO == kSP ? 0.0f : INFINITY;
                     acc1[i] = ALGO == kSP ? 0.0f : INFINITY;
                     arg[i] = -1;
                 }
-                for (int32_t e = beg; e < end; ++e) {
-                    const int32_t v = __ldg(a.ci + e);
-                    const F4 Lv = ld_f4(L + ((int64_t)v * a.FV + fv) * 4);
-                    F4 mo = {{0.f, 0.f, 0.f, 0.f}};
-                    if (a.do_msgs) mo = ld_msg(msg + ((int64_t)e * a.FV + fv) * 4);
-                    for (int i = 0; i < 4; ++i) {
+                units += (unsigned long long)d * nact;
+                auto visit = [&](int k, const VF<V> &Lv, const VF<V> &mo, bool keep) {
+                    for (int i = 0; i < V; ++i) {
                         par ^= (uint32_t)(Lv.v[i] < 0.0f) << i;
                         const float q = Lv.v[i] - mo.v[i];
-                        neg ^= (uint32_t)(q < 0.0f) << i;
+                        if (k < 32) sg[i] |= (uint32_t)(q < 0.0f) << k;
                         if (ALGO == kSP) {
-                            const float f = phi_f(fminf(fmaxf(fabsf(q), kAMin), kAMax));
-                            if (f > acc1[i]) { acc0[i] += acc1[i]; acc1[i] = f; arg[i] = e; }
+                            const float f = phi_clamped(fabsf(q));
+                            if (keep) fc[k < DCMAX ? k : 0][i] = f;
+                            if (f > acc1[i]) { acc0[i] += acc1[i]; acc1[i] = f; arg[i] = k; }
                             else acc0[i] += f;
                         } else {
                             const float m = fabsf(q);
-                            if (m < acc0[i]) { acc1[i] = acc0[i]; acc0[i] = m; arg[i] = e; }
+                            if (m < acc0[i]) { acc1[i] = acc0[i]; acc0[i] = m; arg[i] = k; }
                             else if (m < acc1[i]) acc1[i] = m;
                         }
                     }
-                }
-                unsat_bits |= par;
-                units += (unsigned long long)(end - beg) * nact;
-                if (!a.do_msgs) continue;
-                for (int32_t e = beg; e < end; ++e) {
-                    const int32_t v = __ldg(a.ci + e);
-                    const F4 Lv = ld_f4(L + ((int64_t)v * a.FV + fv) * 4);
-                    MsgT *mp = msg + ((int64_t)e * a.FV + fv) * 4;
-                    const F4 mo = ld_msg(mp);
-                    F4 mn;
-                    for (int i = 0; i < 4; ++i) {
-                        const float q = Lv.v[i] - mo.v[i];
-                        const bool sneg = ((neg >> i) & 1u) ^ (q < 0.0f);
-                        float mag;
-                        if (ALGO == kSP) {
-                            const float f = phi_f(fminf(fmaxf(fabsf(q), kAMin), kAMax));
-                            const float ex = (e == arg[i]) ? acc0[i] : acc0[i] + (acc1[i] - f);
-                            mag = phi_f(fminf(fmaxf(ex, kAMin), kAMax));
-                        } else {
-                            mag = fmaxf(((e == arg[i]) ? acc1[i] : acc0[i]) - a.beta, 0.0f);
+                };
+                if (DCMAX > 0 && ALGO == kSP) {
+#pragma unroll
+                    for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
+                        if (k < d) {
+                            const int32_t e = beg + k;
+                            const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                            VF<V> mo;
+                            if (a.do_msgs) mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                            else for (int i = 0; i < V; ++i) mo.v[i] = 0.0f;
+                            visit(k, Lv, mo, true);
                         }
-                        mn.v[i] = sneg ? -mag : mag;
                     }
-                    st_msg(mp, mn);
+                } else {
+                    for (int k = 0; k < d; ++k) {
+                        const int32_t e = beg + k;
+                        const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                        VF<V> mo;
+                        if (a.do_msgs) mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                        else for (int i = 0; i < V; ++i) mo.v[i] = 0.0f;
+                        visit(k, Lv, mo, false);
+                    }
+                }
+                unsat_bits |= par & act;
+                if (!a.do_msgs) continue;
+                auto emit = [&](int k, float f_k, bool sneg_k, int i) {
+                    float mag;
+                    if (ALGO == kSP) {
+                        const float ex = (k == arg[i]) ? acc0[i] : acc0[i] + (acc1[i] - f_k);
+                        mag = phi_clamped(ex);
+                    } else {
+                        mag = fmaxf(((k == arg[i]) ? acc1[i] : acc0[i]) - a.beta, 0.0f);
+                    }
+                    return sneg_k ? -mag : mag;
+                };
+                if (DCMAX > 0 && ALGO == kSP) {
+                    uint32_t neg = s;       // syndrome xor all signs of q
+                    for (int i = 0; i < V; ++i) neg ^= (uint32_t)(__popc(sg[i]) & 1) << i;
+#pragma unroll
+                    for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
+                        if (k < d) {
+                            VF<V> mn;
+                            for (int i = 0; i < V; ++i)
+                                mn.v[i] = emit(k, fc[k][i], ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
+                            stm<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
+                        }
+                    }
+                } else if (DCMAX > 0) {
+                    // min-sum: the outgoing message needs only the signs kept in pass 1
+                    uint32_t neg = s;
+                    for (int i = 0; i < V; ++i) neg ^= (uint32_t)(__popc(sg[i]) & 1) << i;
+                    for (int k = 0; k < d; ++k) {
+                        VF<V> mn;
+                        for (int i = 0; i < V; ++i)
+                            mn.v[i] = emit(k, 0.0f, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
+                        stm<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
+                    }
+                } else {
+                    // degree above the register cache: signs and phi values again from memory
+                    uint32_t negall = s;
+                    for (int k = 0; k < d; ++k) {
+                        const int32_t e = beg + k;
+                        const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                        const VF<V> mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                        for (int i = 0; i < V; ++i) negall ^= (uint32_t)(Lv.v[i] - mo.v[i] < 0.0f) << i;
+                    }
+                    for (int k = 0; k < d; ++k) {
+                        const int32_t e = beg + k;
+                        const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                        MsgT *mp = msg + (int64_t)e * a.Fp + f0;
+                        const VF<V> mo = ldm<V>(mp);
+                        VF<V> mn;
+                        for (int i = 0; i < V; ++i) {
+                            const float q = Lv.v[i] - mo.v[i];
+                            const float f = ALGO == kSP ? phi_clamped(fabsf(q)) : 0.0f;
+                            mn.v[i] = emit(k, f, ((negall >> i) & 1u) ^ (q < 0.0f), i);
+                        }
+                        stm<V>(mp, mn);
+                    }
                 }
             }
-            // only frames still decoding count
-            uint32_t am = 0;
-            for (int i = 0; i < 4; ++i) am |= (uint32_t)act_bit(act, i) << i;
-            unsat_bits &= am;
         }
         if (a.early_stop || !a.do_msgs)
-            publish_unsat(unsat_bits, fvw, lane, warp, fv, fv_ok, a.unsat_cur);
+            publish_unsat<V>(unsat_bits, f0, fb * fvw * V, fv_ok, a.unsat_cur);
     }
     // messages read + written and the posterior gathered, per active edge-frame
     prof_add(a.prof, units, units * (a.do_msgs ? 2 * sizeof(MsgT) + 4 : 4));
 }
 
 // ----------------------------------------------------- integer check kernel
-template <bool UNUSED>
+template <int V, int DCMAX>
 __global__ void __launch_bounds__(kCheckWarps * 32)
 check_flood_i(DecArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -237,62 +363,80 @@ check_flood_i(DecArgs a) {
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     const int16_t *L = reinterpret_cast<const int16_t *>(a.L);
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
+    const int64_t nvec = a.Fp / V;
+    const uint32_t vmask = (1u << V) - 1u;
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
-        const int64_t fv = fb * fvw + lfv;
-        const bool fv_ok = fv < a.FV;
-        const uint32_t act = fv_ok ? active4(a.active, fv) : 0u;
+    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+        const int64_t fv = fb * fvw + lfv, f0 = fv * V;
+        const bool fv_ok = fv < nvec;
+        const uint32_t act = fv_ok ? active_bits<V>(a.active + f0) : 0u;
         uint32_t unsat_bits = 0;
         if (act) {
-            const int nact = __popc(act & 0x01010101u);
+            const int nact = __popc(act);
             const int64_t c0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
             for (int it = 0; it < kChecksPerWarp; ++it) {
                 const int64_t c = c0 + it * slots + slot;
                 if (c >= a.M) break;
-                const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1);
-                const uint32_t sw = __ldg(a.sbits + c * a.W + ((4 * fv) >> 5));
-                const uint32_t s4 = (sw >> ((4 * fv) & 31)) & 0xfu;
-                uint32_t par = s4, neg = s4;
-                int mn1[4], mn2[4], arg[4];
-                for (int i = 0; i < 4; ++i) { mn1[i] = 1 << 20; mn2[i] = 1 << 20; arg[i] = -1; }
-                for (int32_t e = beg; e < end; ++e) {
-                    const int32_t v = __ldg(a.ci + e);
-                    const I4 Lv = ld_i16x4(L + ((int64_t)v * a.FV + fv) * 4);
-                    I4 mo = {{0, 0, 0, 0}};
-                    if (a.do_msgs) mo = ld_i8x4(msg + ((int64_t)e * a.FV + fv) * 4);
-                    for (int i = 0; i < 4; ++i) {
+                const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1), d = end - beg;
+                const uint32_t s = (__ldg(a.sbits + c * a.W + (f0 >> 5)) >> (f0 & 31)) & vmask;
+                uint32_t par = s, sg[V];
+                int mn1[V], mn2[V], arg[V];
+                for (int i = 0; i < V; ++i) { sg[i] = 0; mn1[i] = 1 << 20; mn2[i] = 1 << 20; arg[i] = -1; }
+                units += (unsigned long long)d * nact;
+                auto visit = [&](int k, const VI<V> &Lv, const VI<V> &mo) {
+                    for (int i = 0; i < V; ++i) {
                         par ^= (uint32_t)(Lv.v[i] < 0) << i;
                         const int q = max(min(Lv.v[i] - mo.v[i], kQMax), -kQMax);
-                        neg ^= (uint32_t)(q < 0) << i;
+                        if (k < 32) sg[i] |= (uint32_t)(q < 0) << k;
                         const int m = q < 0 ? -q : q;
-                        if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = e; }
+                        if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = k; }
                         else if (m < mn2[i]) mn2[i] = m;
                     }
-                }
-                unsat_bits |= par;
-                units += (unsigned long long)(end - beg) * nact;
+                };
+                auto load = [&](int k, VI<V> &Lv, VI<V> &mo) {
+                    const int32_t e = beg + k;
+                    Lv = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                    if (a.do_msgs) mo = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
+                    else for (int i = 0; i < V; ++i) mo.v[i] = 0;
+                };
+                for (int k = 0; k < d; ++k) { VI<V> Lv, mo; load(k, Lv, mo); visit(k, Lv, mo); }
+                unsat_bits |= par & act;
                 if (!a.do_msgs) continue;
-                for (int32_t e = beg; e < end; ++e) {
-                    const int32_t v = __ldg(a.ci + e);
-                    const I4 Lv = ld_i16x4(L + ((int64_t)v * a.FV + fv) * 4);
-                    int8_t *mp = msg + ((int64_t)e * a.FV + fv) * 4;
-                    const I4 mo = ld_i8x4(mp);
-                    I4 mn;
-                    for (int i = 0; i < 4; ++i) {
-                        const int q = max(min(Lv.v[i] - mo.v[i], kQMax), -kQMax);
-                        const bool sneg = ((neg >> i) & 1u) ^ (q < 0);
-                        const int mag = max(((e == arg[i]) ? mn2[i] : mn1[i]) - 1, 0);
-                        mn.v[i] = sneg ? -mag : mag;
+                auto emit = [&](int k, bool sneg, int i) {
+                    const int mag = max(((k == arg[i]) ? mn2[i] : mn1[i]) - 1, 0);
+                    return sneg ? -mag : mag;
+                };
+                if (DCMAX > 0) {
+                    // the outgoing message needs only the signs kept in pass 1
+                    uint32_t neg = s;
+                    for (int i = 0; i < V; ++i) neg ^= (uint32_t)(__popc(sg[i]) & 1) << i;
+                    for (int k = 0; k < d; ++k) {
+                        VI<V> mn;
+                        for (int i = 0; i < V; ++i) mn.v[i] = emit(k, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
+                        sti8<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
                     }
-                    st_i8x4(mp, mn);
+                } else {
+                    uint32_t negall = s;
+                    for (int k = 0; k < d; ++k) {
+                        VI<V> Lv, mo;
+                        load(k, Lv, mo);
+                        for (int i = 0; i < V; ++i)
+                            negall ^= (uint32_t)(max(min(Lv.v[i] - mo.v[i], kQMax), -kQMax) < 0) << i;
+                    }
+                    for (int k = 0; k < d; ++k) {
+                        VI<V> Lv, mo, mn;
+                        load(k, Lv, mo);
+                        for (int i = 0; i < V; ++i) {
+                            const int q = max(min(Lv.v[i] - mo.v[i], kQMax), -kQMax);
+                            mn.v[i] = emit(k, ((negall >> i) & 1u) ^ (q < 0), i);
+                        }
+                        sti8<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
+                    }
                 }
             }
-            uint32_t am = 0;
-            for (int i = 0; i < 4; ++i) am |= (uint32_t)act_bit(act, i) << i;
-            unsat_bits &= am;
         }
         if (a.early_stop || !a.do_msgs)
-            publish_unsat(unsat_bits, fvw, lane, warp, fv, fv_ok, a.unsat_cur);
+            publish_unsat<V>(unsat_bits, f0, fb * fvw * V, fv_ok, a.unsat_cur);
     }
     prof_add(a.prof, units, units * (a.do_msgs ? 4 : 2));
 }
@@ -300,6 +444,7 @@ check_flood_i(DecArgs a) {
 // ------------------------------------------------------------ variable kernels
 // Retire frames whose stopping test passed on L^(t-1); update the rest:
 // L_v = llr_v + sum of the messages on the edges of v (ascending edge order).
+// Four frames per lane.
 template <int PREC>
 __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
     const int64_t total = (int64_t)a.n * a.FV;
@@ -309,25 +454,19 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
     constexpr unsigned cs = PREC == kI8 ? 1 : 4, ls = PREC == kI8 ? 2 : 4;
     unsigned long long units = 0, bytes = 0;
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-        const int64_t v = item / a.FV, fv = item - v * a.FV;
-        const uint32_t act = active4(a.active, fv);
+        const int64_t v = item / a.FV, fv = item - v * a.FV, f0 = 4 * fv;
+        if (v == 0 && (fv & 7) == 0 && a.early_stop) a.unsat_next[fv >> 3] = 0;  // next test starts clear
+        const uint32_t act = active_bits<4>(a.active + f0);
         if (!act) continue;
-        uint32_t upd = 0;  // frames to update
-        uint32_t done = 0; // frames retiring now
-        const uint32_t u = a.early_stop ? __ldcg(a.unsat_cur + fv) : 0xfu;
-        for (int i = 0; i < 4; ++i) {
-            if (!act_bit(act, i)) continue;
-            if (a.early_stop && !((u >> i) & 1u)) done |= 1u << i;
-            else upd |= 1u << i;
-        }
-        if (v == 0) {
+        const uint32_t u = a.early_stop ? (__ldcg(a.unsat_cur + (f0 >> 5)) >> (f0 & 31)) & 0xfu : 0xfu;
+        const uint32_t done = a.early_stop ? (act & ~u) : 0u;  // frames retiring now
+        const uint32_t upd = act & ~done;                      // frames to update
+        if (v == 0)
             for (int i = 0; i < 4; ++i)
                 if ((done >> i) & 1u) {
-                    a.active[4 * fv + i] = 0;
-                    a.iters_i[4 * fv + i] = a.t - 1;
+                    a.active[f0 + i] = 0;
+                    a.iters_i[f0 + i] = a.t - 1;
                 }
-            if (a.early_stop) a.unsat_next[fv] = 0;
-        }
         if (!upd) continue;
         const int32_t vb = __ldg(a.vptr + v), ve = __ldg(a.vptr + v + 1);
         const unsigned nu = __popc(upd);
@@ -335,38 +474,34 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
         bytes += (unsigned long long)nu * ((ve - vb) * ms + cs + ls);
         if (PREC != kI8) {
             float *L = reinterpret_cast<float *>(a.L);
-            const float *llr = reinterpret_cast<const float *>(a.llr_i);
-            F4 s = ld_f4(llr + item * 4);
+            VF<4> s = ldf<4>(reinterpret_cast<const float *>(a.llr_i) + item * 4);
             for (int32_t k = vb; k < ve; ++k) {
-                const int32_t e = __ldg(a.vedge + k);
-                F4 m;
-                if (PREC == kF32) m = ld_msg(reinterpret_cast<const float *>(a.msg) + ((int64_t)e * a.FV + fv) * 4);
-                else m = ld_msg(reinterpret_cast<const __half *>(a.msg) + ((int64_t)e * a.FV + fv) * 4);
+                const int64_t e = __ldg(a.vedge + k);
+                VF<4> m;
+                if (PREC == kF32) m = ldm<4>(reinterpret_cast<const float *>(a.msg) + e * a.Fp + f0);
+                else m = ldm<4>(reinterpret_cast<const __half *>(a.msg) + e * a.Fp + f0);
                 for (int i = 0; i < 4; ++i) s.v[i] += m.v[i];
             }
             if (upd != 0xfu) {
-                const F4 old = *reinterpret_cast<const F4 *>(L + item * 4);
+                const VF<4> old = ldf_plain<4>(L + item * 4);
                 for (int i = 0; i < 4; ++i)
                     if (!((upd >> i) & 1u)) s.v[i] = old.v[i];
             }
-            st_f4(L + item * 4, s);
+            stf<4>(L + item * 4, s);
         } else {
             int16_t *L = reinterpret_cast<int16_t *>(a.L);
-            const I4 q = ld_i8x4(reinterpret_cast<const int8_t *>(a.llr_i) + item * 4);
-            int s[4] = {q.v[0], q.v[1], q.v[2], q.v[3]};
+            VI<4> s = ldi8<4>(reinterpret_cast<const int8_t *>(a.llr_i) + item * 4);
             for (int32_t k = vb; k < ve; ++k) {
-                const int32_t e = __ldg(a.vedge + k);
-                const I4 m = ld_i8x4(reinterpret_cast<const int8_t *>(a.msg) + ((int64_t)e * a.FV + fv) * 4);
-                for (int i = 0; i < 4; ++i) s[i] = max(min(s[i] + m.v[i], kPMax), -kPMax);
+                const int64_t e = __ldg(a.vedge + k);
+                const VI<4> m = ldi8<4>(reinterpret_cast<const int8_t *>(a.msg) + e * a.Fp + f0);
+                for (int i = 0; i < 4; ++i) s.v[i] = max(min(s.v[i] + m.v[i], kPMax), -kPMax);
             }
-            I4 r = {{s[0], s[1], s[2], s[3]}};
             if (upd != 0xfu) {
-                const short4 o = *reinterpret_cast<const short4 *>(L + item * 4);
-                const int ov[4] = {o.x, o.y, o.z, o.w};
+                const VI<4> old = ldi16<4>(L + item * 4);
                 for (int i = 0; i < 4; ++i)
-                    if (!((upd >> i) & 1u)) r.v[i] = ov[i];
+                    if (!((upd >> i) & 1u)) s.v[i] = old.v[i];
             }
-            st_i16x4(L + item * 4, r);
+            sti16<4>(L + item * 4, s);
         }
     }
     prof_add(a.prof, units, bytes);
@@ -424,19 +559,19 @@ __global__ void prep_synd(const uint8_t *__restrict__ synd, int32_t F, int32_t M
 
 // per-frame state; `mask` marks the frames this decode owns (all real frames,
 // or only the frames a low-precision pass left unsatisfied)
-__global__ void init_state(int32_t F, int64_t Fp, const uint8_t *__restrict__ conv_prev,
+__global__ void init_state(int32_t F, int64_t Fp, int64_t W, const uint8_t *__restrict__ conv_prev,
                            uint8_t *active, uint8_t *mask, int32_t *iters_i, uint32_t *unsat0,
                            uint32_t *unsat1) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < W) {
+        unsat0[f] = 0;
+        unsat1[f] = 0;
+    }
     if (f >= Fp) return;
     const uint8_t a = (f < F) && (!conv_prev || !conv_prev[f]);
     active[f] = a;
     mask[f] = a;
     iters_i[f] = 0;
-    if ((f & 3) == 0) {
-        unsat0[f >> 2] = 0;
-        unsat1[f >> 2] = 0;
-    }
 }
 
 // `accumulate`: a re-decode adds its iterations to those of the first pass.
@@ -448,7 +583,7 @@ __global__ void finalize(int32_t F, int32_t T, int32_t accumulate, const uint8_t
     const int32_t base = accumulate ? iters_out[f] : 0;
     if (active[f]) {
         iters_out[f] = base + T;
-        conv_out[f] = !((unsat[f >> 2] >> (f & 3)) & 1u);
+        conv_out[f] = !((unsat[f >> 5] >> (f & 31)) & 1u);
     } else {
         iters_out[f] = base + iters_i[f];
         conv_out[f] = 1;
@@ -503,8 +638,8 @@ static Layout make_layout(const CodeDev &d, int32_t F, int prec) {
     l.sbits = take((size_t)d.M * l.W * 4);
     l.active = take((size_t)l.Fp);
     l.mask = take((size_t)l.Fp);
-    l.unsat0 = take((size_t)l.FV * 4);
-    l.unsat1 = take((size_t)l.FV * 4);
+    l.unsat0 = take((size_t)l.W * 4);
+    l.unsat1 = take((size_t)l.W * 4);
     l.iters = take((size_t)l.Fp * 4);
     l.total = off;
     return l;
@@ -529,8 +664,27 @@ struct Prepared {
     uint8_t *mask;
 };
 
+// register-cache size of the check kernels for a code: 8 or 32 edges, 0 = reload
+static int dc_class(const CodeDev &d) { return d.dc_max <= 8 ? 8 : (d.dc_max <= 32 ? 32 : 0); }
+
+// Launch geometry of a check-type kernel with V frames per lane.
+struct Geom {
+    dim3 grid;
+    int fvw;
+};
+static Geom check_geom(int64_t Fp, int V, int64_t checks) {
+    Geom g;
+    const int64_t nvec = Fp / V;
+    g.fvw = 1;
+    while (g.fvw < 32 && g.fvw < nvec) g.fvw <<= 1;
+    const int64_t per_block = (int64_t)kCheckWarps * kChecksPerWarp * (32 / g.fvw);
+    const int64_t fblocks = ceil_div(nvec, g.fvw);
+    g.grid = dim3((unsigned)ceil_div(checks, per_block), (unsigned)(fblocks < 65535 ? fblocks : 65535));
+    return g;
+}
+
 // Shared set-up of one decode pass: per-frame state, interleaved LLRs and
-// posteriors, packed syndromes, zero messages, and the launch geometry.
+// posteriors, packed syndromes, zero messages.
 static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
                              const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, char *ws,
                              const Layout &l, cudaStream_t st, DecArgs &a, Prepared &pr) {
@@ -544,12 +698,12 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     a.L = ws + l.L;
     a.msg = ws + l.msg;
     a.llr_i = ws + l.llr_i;
+    a.Fp = l.Fp;
     a.FV = l.FV;
     a.W = l.W;
     a.n = d.n;
     a.M = d.M;
-    a.fvw = 1;
-    while (a.fvw < 32 && a.fvw < l.FV) a.fvw <<= 1;
+    a.fvw = 32;
     a.t = 0;
     a.do_msgs = 1;
     a.early_stop = o.early_stop ? 1 : 0;
@@ -560,11 +714,10 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     pr.mask = reinterpret_cast<uint8_t *>(ws + l.mask);
     a.unsat_cur = pr.unsat[0];
     a.unsat_next = pr.unsat[1];
-
     {
         prof::Scope ps(prof::kPrep, st);
-        init_state<<<(unsigned)ceil_div(l.Fp, 256), 256, 0, st>>>(F, l.Fp, conv_prev, a.active, pr.mask,
-                                                                 a.iters_i, pr.unsat[0], pr.unsat[1]);
+        init_state<<<(unsigned)ceil_div(std::max<int64_t>(l.Fp, l.W), 256), 256, 0, st>>>(
+            F, l.Fp, l.W, conv_prev, a.active, pr.mask, a.iters_i, pr.unsat[0], pr.unsat[1]);
     }
     QKD_LAUNCHED("init_state");
     {
@@ -572,14 +725,14 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
         dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
         if (prec == kI8) prep_llr<kI8><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, o.llr_step, ws + l.llr_i, ws + l.L);
         else prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, o.llr_step, ws + l.llr_i, ws + l.L);
-        QKD_LAUNCHED("prep_llr");
     }
+    QKD_LAUNCHED("prep_llr");
     {
         prof::Scope ps(prof::kPrep, st);
         dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)l.W);
         prep_synd<<<grd, 256, 0, st>>>(synd, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits));
-        QKD_LAUNCHED("prep_synd");
     }
+    QKD_LAUNCHED("prep_synd");
     const size_t ms = prec == kF32 ? 4 : (prec == kF16 ? 2 : 1);
     QKD_CUDA(cudaMemsetAsync(ws + l.msg, 0, (size_t)d.E * l.Fp * ms, st));
     return QKDREC_OK;
@@ -605,6 +758,41 @@ static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const 
     return QKDREC_OK;
 }
 
+// Launch one flooding check kernel (or its parity-only form).  SP keeps one
+// frame per lane so that the phi values of a check fit in registers; min-sum
+// only keeps sign bits and runs four frames per lane.
+static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaStream_t st) {
+    const int dcc = dc_class(d);
+    const int V = (prec != kI8 && algo == QKDREC_SP_FLOOD && dcc > 0) ? 1 : 4;
+    const Geom g = check_geom(a.Fp, V, d.M);
+    a.fvw = g.fvw;
+    const dim3 B(kCheckWarps * 32);
+#define QKD_CHK(ALG, T, VV, DC) check_flood_f<ALG, T, VV, DC><<<g.grid, B, 0, st>>>(a)
+    if (prec == kI8) {
+        if (dcc > 0) check_flood_i<4, 32><<<g.grid, B, 0, st>>>(a);
+        else check_flood_i<4, 0><<<g.grid, B, 0, st>>>(a);
+    } else if (algo == QKDREC_SP_FLOOD) {
+        if (prec == kF32) {
+            if (dcc == 8) QKD_CHK(kSP, float, 1, 8);
+            else if (dcc == 32) QKD_CHK(kSP, float, 1, 32);
+            else QKD_CHK(kSP, float, 4, 0);
+        } else {
+            if (dcc == 8) QKD_CHK(kSP, __half, 1, 8);
+            else if (dcc == 32) QKD_CHK(kSP, __half, 1, 32);
+            else QKD_CHK(kSP, __half, 4, 0);
+        }
+    } else {
+        if (prec == kF32) {
+            if (dcc > 0) QKD_CHK(kOMS, float, 4, 32);
+            else QKD_CHK(kOMS, float, 4, 0);
+        } else {
+            if (dcc > 0) QKD_CHK(kOMS, __half, 4, 32);
+            else QKD_CHK(kOMS, __half, 4, 0);
+        }
+    }
+#undef QKD_CHK
+}
+
 // One flooding decode pass over the frames selected by conv_prev (NULL = all).
 static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
                                const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev,
@@ -615,10 +803,6 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
     Prepared pr;
     qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, ws, l, st, a, pr);
     if (s != QKDREC_OK) return s;
-    const int slots = 32 / a.fvw;
-    const int64_t checks_per_block = (int64_t)kCheckWarps * kChecksPerWarp * slots;
-    const int64_t fblocks = ceil_div(l.FV, a.fvw);
-    dim3 cgrid((unsigned)ceil_div(d.M, checks_per_block), (unsigned)(fblocks < 65535 ? fblocks : 65535));
     const int64_t vitems = (int64_t)d.n * l.FV;
     const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(vitems, 256), (int64_t)sm_count() * 64);
 
@@ -633,14 +817,7 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
                                                      : (prec == kF32 ? prof::kCheckOmsF32 : prof::kCheckOmsF16);
         a.prof = prof::counters(kind);
         prof::Scope ps(kind, st);
-        if (prec == kI8) check_flood_i<true><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
-        else if (o.algo == QKDREC_SP_FLOOD) {
-            if (prec == kF32) check_flood_f<kSP, float><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
-            else check_flood_f<kSP, __half><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
-        } else {
-            if (prec == kF32) check_flood_f<kOMS, float><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
-            else check_flood_f<kOMS, __half><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
-        }
+        launch_check(a, d, o.algo, prec, st);
     };
     for (int t = 1; t <= o.max_iter; ++t) {
         check(t, 1);
@@ -667,11 +844,27 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
 
 #include "decode_layered.cuh"
 
+__global__ void phi_selftest_kernel(const float *__restrict__ x, int64_t count, float *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = phi_clamped(x[i]);
+}
+
 }  // namespace qkd
 
 using namespace qkd;
 
 extern "C" {
+
+qkdrec_status qkdrec_selftest_phi(const float *x, int64_t count, float *out, void *stream) {
+    clear_error();
+    if (count < 0) QKD_FAIL(QKDREC_ERR_ARG, "count < 0");
+    if (count == 0) return QKDREC_OK;
+    if (!x || !out) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    phi_selftest_kernel<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 4096), 256, 0, as_stream(stream)>>>(
+        x, count, out);
+    QKD_LAUNCHED("phi_selftest_kernel");
+    return QKDREC_OK;
+}
 
 void qkdrec_decode_opts_default(qkdrec_decode_opts *o) {
     if (!o) return;

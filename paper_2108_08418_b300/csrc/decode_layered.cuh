@@ -7,69 +7,100 @@
 //   L_v = q + m_cv.
 // One kernel launch per layer; after the last layer a parity-only pass tests
 // the syndrome of the hard decision, and a small kernel retires the frames
-// whose test passed.
+// whose test passed.  With one frame per lane (V = 1) the q values of a check
+// stay in registers between the two passes; the V = 4 variant for degrees
+// above the register cache reads them again and keeps retired frames frozen.
 
 // ------------------------------------------------------------ float layered
-template <typename MsgT>
-__global__ void __launch_bounds__(kCheckWarps * 32)
+template <typename MsgT, int V, int DCMAX>
+__global__ void __launch_bounds__(kCheckWarps * 32, 2)
 layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     float *L = reinterpret_cast<float *>(a.L);
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
+    const int64_t nvec = a.Fp / V;
+    const uint32_t vmask = (1u << V) - 1u;
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
-        const int64_t fv = fb * fvw + lfv;
-        if (fv >= a.FV) continue;
-        const uint32_t act = active4(a.active, fv);
+    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+        const int64_t fv = fb * fvw + lfv, f0 = fv * V;
+        if (fv >= nvec) continue;
+        const uint32_t act = active_bits<V>(a.active + f0);
         if (!act) continue;
-        const int nact = __popc(act & 0x01010101u);
+        const int nact = __popc(act);
         const int64_t k0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
         for (int it = 0; it < kChecksPerWarp; ++it) {
-            const int64_t k = k0 + it * slots + slot;
-            if (k >= lsize) break;
-            const int32_t c = __ldg(lchk + lbeg + k);
-            const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1);
-            const uint32_t sw = __ldg(a.sbits + (int64_t)c * a.W + ((4 * fv) >> 5));
-            uint32_t neg = (sw >> ((4 * fv) & 31)) & 0xfu;
-            units += (unsigned long long)(end - beg) * nact;
-            float mn1[4], mn2[4];
-            int32_t arg[4];
-            for (int i = 0; i < 4; ++i) { mn1[i] = INFINITY; mn2[i] = INFINITY; arg[i] = -1; }
-            for (int32_t e = beg; e < end; ++e) {
-                const int32_t v = __ldg(a.ci + e);
-                const F4 Lv = *reinterpret_cast<const F4 *>(L + ((int64_t)v * a.FV + fv) * 4);
-                const F4 mo = ld_msg(msg + ((int64_t)e * a.FV + fv) * 4);
-                for (int i = 0; i < 4; ++i) {
-                    const float q = Lv.v[i] - mo.v[i];
-                    neg ^= (uint32_t)(q < 0.0f) << i;
-                    const float m = fabsf(q);
-                    if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = e; }
-                    else if (m < mn2[i]) mn2[i] = m;
+            const int64_t kk = k0 + it * slots + slot;
+            if (kk >= lsize) break;
+            const int32_t c = __ldg(lchk + lbeg + kk);
+            const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1), d = end - beg;
+            uint32_t neg = (__ldg(a.sbits + (int64_t)c * a.W + (f0 >> 5)) >> (f0 & 31)) & vmask;
+            units += (unsigned long long)d * nact;
+            float mn1[V], mn2[V], qc[DCMAX > 0 ? DCMAX : 1][V];
+            int32_t arg[V];
+            for (int i = 0; i < V; ++i) { mn1[i] = INFINITY; mn2[i] = INFINITY; arg[i] = -1; }
+            auto visit = [&](int k, float q, int i) {
+                neg ^= (uint32_t)(q < 0.0f) << i;
+                const float m = fabsf(q);
+                if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = k; }
+                else if (m < mn2[i]) mn2[i] = m;
+            };
+            auto magnitude = [&](int k, int i) {
+                return fmaxf(((k == arg[i]) ? mn2[i] : mn1[i]) - a.beta, 0.0f);
+            };
+            if (DCMAX > 0) {
+#pragma unroll
+                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
+                    if (k < d) {
+                        const int32_t e = beg + k;
+                        const VF<V> Lv = ldf_plain<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                        const VF<V> mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                        for (int i = 0; i < V; ++i) {
+                            qc[k][i] = Lv.v[i] - mo.v[i];
+                            visit(k, qc[k][i], i);
+                        }
+                    }
                 }
-            }
-            for (int32_t e = beg; e < end; ++e) {
-                const int32_t v = __ldg(a.ci + e);
-                float *Lp = L + ((int64_t)v * a.FV + fv) * 4;
-                const F4 Lv = *reinterpret_cast<const F4 *>(Lp);
-                MsgT *mp = msg + ((int64_t)e * a.FV + fv) * 4;
-                const F4 mo = ld_msg(mp);
-                F4 mn, Ln;
-                for (int i = 0; i < 4; ++i) {
-                    const float q = Lv.v[i] - mo.v[i];
-                    const bool sneg = ((neg >> i) & 1u) ^ (q < 0.0f);
-                    const float mag = fmaxf(((e == arg[i]) ? mn2[i] : mn1[i]) - a.beta, 0.0f);
-                    mn.v[i] = sneg ? -mag : mag;
+#pragma unroll
+                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
+                    if (k < d) {
+                        const int32_t e = beg + k;
+                        VF<V> mn, Ln;
+                        for (int i = 0; i < V; ++i) {
+                            const float q = qc[k][i];
+                            const float mag = magnitude(k, i);
+                            mn.v[i] = (((neg >> i) & 1u) ^ (q < 0.0f)) ? -mag : mag;
+                            // later layers subtract the stored (possibly FP16-rounded) message
+                            Ln.v[i] = q + as_stored(mn.v[i], msg);
+                        }
+                        stm<V>(msg + (int64_t)e * a.Fp + f0, mn);
+                        stf<V>(L + (int64_t)ld_index_again(a.ci + e) * a.Fp + f0, Ln);
+                    }
                 }
-                st_msg(mp, mn);
-                // the stored (possibly FP16-rounded) message is what later layers subtract
-                const F4 ms = as_stored<MsgT>(mn);
-                for (int i = 0; i < 4; ++i) {
-                    const float q = Lv.v[i] - mo.v[i];
-                    Ln.v[i] = act_bit(act, i) ? q + ms.v[i] : Lv.v[i];
+            } else {
+                for (int k = 0; k < d; ++k) {
+                    const int32_t e = beg + k;
+                    const VF<V> Lv = ldf_plain<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                    const VF<V> mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                    for (int i = 0; i < V; ++i) visit(k, Lv.v[i] - mo.v[i], i);
                 }
-                st_f4(Lp, Ln);
+                for (int k = 0; k < d; ++k) {
+                    const int32_t e = beg + k;
+                    float *Lp = L + (int64_t)__ldg(a.ci + e) * a.Fp + f0;
+                    const VF<V> Lv = ldf_plain<V>(Lp);
+                    MsgT *mp = msg + (int64_t)e * a.Fp + f0;
+                    const VF<V> mo = ldm<V>(mp);
+                    VF<V> mn, Ln;
+                    for (int i = 0; i < V; ++i) {
+                        const float q = Lv.v[i] - mo.v[i];
+                        const float mag = magnitude(k, i);
+                        mn.v[i] = (((neg >> i) & 1u) ^ (q < 0.0f)) ? -mag : mag;
+                        Ln.v[i] = ((act >> i) & 1u) ? q + as_stored(mn.v[i], msg) : Lv.v[i];
+                    }
+                    stm<V>(mp, mn);
+                    stf<V>(Lp, Ln);
+                }
             }
         }
     }
@@ -78,63 +109,94 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 }
 
 // ---------------------------------------------------------- integer layered
-__global__ void __launch_bounds__(kCheckWarps * 32)
+template <int V, int DCMAX>
+__global__ void __launch_bounds__(kCheckWarps * 32, 2)
 layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
     int16_t *L = reinterpret_cast<int16_t *>(a.L);
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
+    const int64_t nvec = a.Fp / V;
+    const uint32_t vmask = (1u << V) - 1u;
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < a.FV; fb += gridDim.y) {
-        const int64_t fv = fb * fvw + lfv;
-        if (fv >= a.FV) continue;
-        const uint32_t act = active4(a.active, fv);
+    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+        const int64_t fv = fb * fvw + lfv, f0 = fv * V;
+        if (fv >= nvec) continue;
+        const uint32_t act = active_bits<V>(a.active + f0);
         if (!act) continue;
-        const int nact = __popc(act & 0x01010101u);
+        const int nact = __popc(act);
         const int64_t k0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
         for (int it = 0; it < kChecksPerWarp; ++it) {
-            const int64_t k = k0 + it * slots + slot;
-            if (k >= lsize) break;
-            const int32_t c = __ldg(lchk + lbeg + k);
-            const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1);
-            const uint32_t sw = __ldg(a.sbits + (int64_t)c * a.W + ((4 * fv) >> 5));
-            uint32_t neg = (sw >> ((4 * fv) & 31)) & 0xfu;
-            units += (unsigned long long)(end - beg) * nact;
-            int mn1[4], mn2[4], arg[4];
-            for (int i = 0; i < 4; ++i) { mn1[i] = 1 << 20; mn2[i] = 1 << 20; arg[i] = -1; }
-            for (int32_t e = beg; e < end; ++e) {
-                const int32_t v = __ldg(a.ci + e);
-                const short4 l4 = *reinterpret_cast<const short4 *>(L + ((int64_t)v * a.FV + fv) * 4);
-                const int Lv[4] = {l4.x, l4.y, l4.z, l4.w};
-                const I4 mo = ld_i8x4(msg + ((int64_t)e * a.FV + fv) * 4);
-                for (int i = 0; i < 4; ++i) {
-                    const int qf = max(min(Lv[i] - mo.v[i], kPMax), -kPMax);
-                    const int q = max(min(qf, kQMax), -kQMax);
-                    neg ^= (uint32_t)(q < 0) << i;
-                    const int m = q < 0 ? -q : q;
-                    if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = e; }
-                    else if (m < mn2[i]) mn2[i] = m;
+            const int64_t kk = k0 + it * slots + slot;
+            if (kk >= lsize) break;
+            const int32_t c = __ldg(lchk + lbeg + kk);
+            const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1), d = end - beg;
+            uint32_t neg = (__ldg(a.sbits + (int64_t)c * a.W + (f0 >> 5)) >> (f0 & 31)) & vmask;
+            units += (unsigned long long)d * nact;
+            int mn1[V], mn2[V], arg[V], qc[DCMAX > 0 ? DCMAX : 1][V];
+            for (int i = 0; i < V; ++i) { mn1[i] = 1 << 20; mn2[i] = 1 << 20; arg[i] = -1; }
+            // q_full = sat16(L - m); the v->c message is q_full clipped to 6 bits
+            auto visit = [&](int k, int qf, int i) {
+                const int q = max(min(qf, kQMax), -kQMax);
+                neg ^= (uint32_t)(q < 0) << i;
+                const int m = q < 0 ? -q : q;
+                if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = k; }
+                else if (m < mn2[i]) mn2[i] = m;
+            };
+            auto message = [&](int k, int qf, int i) {
+                const int q = max(min(qf, kQMax), -kQMax);
+                const int mag = max(((k == arg[i]) ? mn2[i] : mn1[i]) - 1, 0);
+                return (((neg >> i) & 1u) ^ (q < 0)) ? -mag : mag;
+            };
+            if (DCMAX > 0) {
+#pragma unroll
+                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
+                    if (k < d) {
+                        const int32_t e = beg + k;
+                        const VI<V> Lv = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                        const VI<V> mo = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
+                        for (int i = 0; i < V; ++i) {
+                            qc[k][i] = max(min(Lv.v[i] - mo.v[i], kPMax), -kPMax);
+                            visit(k, qc[k][i], i);
+                        }
+                    }
                 }
-            }
-            for (int32_t e = beg; e < end; ++e) {
-                const int32_t v = __ldg(a.ci + e);
-                int16_t *Lp = L + ((int64_t)v * a.FV + fv) * 4;
-                const short4 l4 = *reinterpret_cast<const short4 *>(Lp);
-                const int Lv[4] = {l4.x, l4.y, l4.z, l4.w};
-                int8_t *mp = msg + ((int64_t)e * a.FV + fv) * 4;
-                const I4 mo = ld_i8x4(mp);
-                I4 mn, Ln;
-                for (int i = 0; i < 4; ++i) {
-                    const int qf = max(min(Lv[i] - mo.v[i], kPMax), -kPMax);
-                    const int q = max(min(qf, kQMax), -kQMax);
-                    const bool sneg = ((neg >> i) & 1u) ^ (q < 0);
-                    const int mag = max(((e == arg[i]) ? mn2[i] : mn1[i]) - 1, 0);
-                    mn.v[i] = sneg ? -mag : mag;
-                    Ln.v[i] = act_bit(act, i) ? max(min(qf + mn.v[i], kPMax), -kPMax) : Lv[i];
+#pragma unroll
+                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
+                    if (k < d) {
+                        const int32_t e = beg + k;
+                        VI<V> mn, Ln;
+                        for (int i = 0; i < V; ++i) {
+                            mn.v[i] = message(k, qc[k][i], i);
+                            Ln.v[i] = max(min(qc[k][i] + mn.v[i], kPMax), -kPMax);
+                        }
+                        sti8<V>(msg + (int64_t)e * a.Fp + f0, mn);
+                        sti16<V>(L + (int64_t)ld_index_again(a.ci + e) * a.Fp + f0, Ln);
+                    }
                 }
-                st_i8x4(mp, mn);
-                st_i16x4(Lp, Ln);
+            } else {
+                for (int k = 0; k < d; ++k) {
+                    const int32_t e = beg + k;
+                    const VI<V> Lv = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                    const VI<V> mo = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
+                    for (int i = 0; i < V; ++i) visit(k, max(min(Lv.v[i] - mo.v[i], kPMax), -kPMax), i);
+                }
+                for (int k = 0; k < d; ++k) {
+                    const int32_t e = beg + k;
+                    int16_t *Lp = L + (int64_t)__ldg(a.ci + e) * a.Fp + f0;
+                    const VI<V> Lv = ldi16<V>(Lp);
+                    int8_t *mp = msg + (int64_t)e * a.Fp + f0;
+                    const VI<V> mo = ldi8<V>(mp);
+                    VI<V> mn, Ln;
+                    for (int i = 0; i < V; ++i) {
+                        const int qf = max(min(Lv.v[i] - mo.v[i], kPMax), -kPMax);
+                        mn.v[i] = message(k, qf, i);
+                        Ln.v[i] = ((act >> i) & 1u) ? max(min(qf + mn.v[i], kPMax), -kPMax) : Lv.v[i];
+                    }
+                    sti8<V>(mp, mn);
+                    sti16<V>(Lp, Ln);
+                }
             }
         }
     }
@@ -143,15 +205,37 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 
 // Retire frames whose stopping test passed after iteration t (iters = t) and
 // clear the other parity buffer for the next test.
-__global__ void retire(int64_t Fp, int32_t t, uint8_t *active, int32_t *iters_i,
+__global__ void retire(int64_t Fp, int64_t W, int32_t t, uint8_t *active, int32_t *iters_i,
                        const uint32_t *__restrict__ unsat_cur, uint32_t *unsat_next) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < W) unsat_next[f] = 0;
     if (f >= Fp) return;
-    if (active[f] && !((unsat_cur[f >> 2] >> (f & 3)) & 1u)) {
+    if (active[f] && !((unsat_cur[f >> 5] >> (f & 31)) & 1u)) {
         active[f] = 0;
         iters_i[f] = t;
     }
-    if ((f & 3) == 0) unsat_next[f >> 2] = 0;
+}
+
+static void launch_layer(DecArgs a, const CodeDev &d, int prec, int32_t lb, int32_t ls, cudaStream_t st) {
+    const int dcc = dc_class(d);
+    const int V = dcc > 0 ? 1 : 4;
+    const Geom g = check_geom(a.Fp, V, ls);
+    a.fvw = g.fvw;
+    const dim3 B(kCheckWarps * 32);
+    const int32_t *lc = d.layer_chk;
+    if (prec == kI8) {
+        if (dcc == 8) layer_oms_i<1, 8><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        else if (dcc == 32) layer_oms_i<1, 32><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        else layer_oms_i<4, 0><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+    } else if (prec == kF16) {
+        if (dcc == 8) layer_oms_f<__half, 1, 8><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        else if (dcc == 32) layer_oms_f<__half, 1, 32><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        else layer_oms_f<__half, 4, 0><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+    } else {
+        if (dcc == 8) layer_oms_f<float, 1, 8><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        else if (dcc == 32) layer_oms_f<float, 1, 32><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        else layer_oms_f<float, 4, 0><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+    }
 }
 
 qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
@@ -163,46 +247,36 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *syn
     Prepared pr;
     qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, ws, l, st, a, pr);
     if (s != QKDREC_OK) return s;
-    const int slots = 32 / a.fvw;
-    const int64_t checks_per_block = (int64_t)kCheckWarps * kChecksPerWarp * slots;
-    const int64_t fblocks = ceil_div(l.FV, a.fvw);
-    const unsigned gy = (unsigned)(fblocks < 65535 ? fblocks : 65535);
     const std::vector<int32_t> &lptr = d.h_layer_ptr;
     const int T = o.max_iter;
     auto parity = [&](int t) {
-        a.t = t;
-        a.do_msgs = 0;
-        a.early_stop = 1;
-        a.unsat_cur = pr.unsat[t & 1];
-        a.unsat_next = pr.unsat[(t + 1) & 1];
+        DecArgs p = a;
+        p.t = t;
+        p.do_msgs = 0;
+        p.early_stop = 1;
+        p.unsat_cur = pr.unsat[t & 1];
+        p.unsat_next = pr.unsat[(t + 1) & 1];
         const int kind = prec == kI8 ? prof::kParityI8 : prof::kParityF32;
-        a.prof = prof::counters(kind);
+        p.prof = prof::counters(kind);
         prof::Scope ps(kind, st);
-        dim3 cgrid((unsigned)ceil_div(d.M, checks_per_block), gy);
-        if (prec == kI8) check_flood_i<true><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
-        else if (prec == kF16) check_flood_f<kOMS, __half><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
-        else check_flood_f<kOMS, float><<<cgrid, kCheckWarps * 32, 0, st>>>(a);
+        launch_check(p, d, QKDREC_OMS_FLOOD, prec, st);
     };
     auto retire_at = [&](int t) {
         prof::Scope ps(prof::kFinish, st);
-        retire<<<(unsigned)ceil_div(l.Fp, 256), 256, 0, st>>>(l.Fp, t, a.active, a.iters_i, pr.unsat[t & 1],
-                                                             pr.unsat[(t + 1) & 1]);
+        retire<<<(unsigned)ceil_div(std::max<int64_t>(l.Fp, l.W), 256), 256, 0, st>>>(
+            l.Fp, l.W, t, a.active, a.iters_i, pr.unsat[t & 1], pr.unsat[(t + 1) & 1]);
     };
     if (o.early_stop) {
         parity(0);
         retire_at(0);
         QKD_LAUNCHED("retire");
     }
+    const int lkind = prec == kI8 ? prof::kLayerI8 : (prec == kF16 ? prof::kLayerF16 : prof::kLayerF32);
     for (int t = 1; t <= T; ++t) {
-        const int lkind = prec == kI8 ? prof::kLayerI8 : (prec == kF16 ? prof::kLayerF16 : prof::kLayerF32);
         a.prof = prof::counters(lkind);
         for (int32_t ly = 0; ly < d.n_layers; ++ly) {
             prof::Scope ps(lkind, st);
-            const int32_t lb = lptr[ly], ls = lptr[ly + 1] - lptr[ly];
-            dim3 g((unsigned)ceil_div(ls, checks_per_block), gy);
-            if (prec == kI8) layer_oms_i<<<g, kCheckWarps * 32, 0, st>>>(a, d.layer_chk, lb, ls);
-            else if (prec == kF16) layer_oms_f<__half><<<g, kCheckWarps * 32, 0, st>>>(a, d.layer_chk, lb, ls);
-            else layer_oms_f<float><<<g, kCheckWarps * 32, 0, st>>>(a, d.layer_chk, lb, ls);
+            launch_layer(a, d, prec, lptr[ly], lptr[ly + 1] - lptr[ly], st);
         }
         QKD_LAUNCHED("layer_oms");
         if (o.early_stop) {

@@ -58,49 +58,42 @@ struct __align__(8) LlrParams {
     int32_t m, K, j;
 };
 
-constexpr float kTailSigma = 5.0f;   // intervals farther than this (in sigma_n) use FP64
 constexpr float kSkipNats = 25.0f;   // terms below e^-25 of the set's nearest term are dropped
+constexpr float kFarNats = 50.0f;    // both sets below e^-50: the set sums are redone in FP64
 constexpr float kLn05 = -0.69314718055994531f;
 
-// log P(k|x) for an interval within kTailSigma of x: FP32 complementary error
-// functions taken on the side of x the interval lies on.
-__device__ __forceinline__ float logp_near(float a, float b) {
-    const float r2 = 0.70710678118654752f;
-    float P;
-    if (a >= 0.0f) P = 0.5f * (erfcf(a * r2) - erfcf(b * r2));
-    else if (b <= 0.0f) P = 0.5f * (erfcf(-b * r2) - erfcf(-a * r2));
-    else P = 1.0f - 0.5f * erfcf(-a * r2) - 0.5f * erfcf(b * r2);
-    return logf(P);
-}
-
-// log Q(z) for z >= 0 in FP64 through the scaled complement erfcx, so that the
-// far Gaussian tail never underflows.
-__device__ __forceinline__ double log_q(double z) {
-    const double r2 = 0.70710678118654752440;
+// log Q(z), z >= 0, through the scaled complement erfcx (no underflow at any z):
+// Q(z) = erfc(z/sqrt 2)/2 = erfcx(z/sqrt 2) exp(-z^2/2)/2.
+__device__ __forceinline__ float log_q32(float z) {
     if (isinf(z)) return -INFINITY;
-    double u = z * r2;
-    return log(0.5 * erfcx(u)) - u * u;
+    return logf(0.5f * erfcxf(z * 0.70710678118654752f)) - 0.5f * z * z;
+}
+__device__ __forceinline__ double log_q64(double z) {
+    if (isinf(z)) return -INFINITY;
+    return log(0.5 * erfcx(z * 0.70710678118654752440)) - 0.5 * z * z;
 }
 
-// log P(k|x) in FP64 for a tail interval: the interval lies entirely on one
-// side of x, at standardised near edge dn >= 0 and far edge df >= dn.
-__device__ __forceinline__ double logp_tail(double dn, double df) {
-    double ln = log_q(dn);
-    double lf = log_q(df);
-    return ln + log1p(-exp(lf - ln));
-}
-
-__device__ __forceinline__ float logp_interval(const LlrParams &p, int k, float x, double xd,
-                                               float d) {
-    if (d <= kTailSigma) {
-        float a = (p.tf[k] - x) * p.inv_sigma;
-        float b = (p.tf[k + 1] - x) * p.inv_sigma;
-        return logp_near(a, b);
+// log P(k | x) for standardised interval bounds a < b:
+//   interval containing x : log(1 - Q(-a) - Q(b));
+//   interval beside x     : near edge dn, far edge df on the same side,
+//                           log(Q(dn) - Q(df)) = log Q(dn) + log(-expm1(log Q(df) - log Q(dn))).
+__device__ __forceinline__ float logp32(float a, float b) {
+    if (a < 0.0f && b > 0.0f) {
+        const float r2 = 0.70710678118654752f;
+        return log1pf(-0.5f * (erfcf(-a * r2) + erfcf(b * r2)));
     }
-    double a = (p.td[k] - xd) * p.inv_sigma_d;
-    double b = (p.td[k + 1] - xd) * p.inv_sigma_d;
-    double r = a >= 0.0 ? logp_tail(a, b) : logp_tail(-b, -a);
-    return (float)r;
+    const float dn = a >= 0.0f ? a : -b, df = a >= 0.0f ? b : -a;
+    const float ln = log_q32(dn);
+    return ln + logf(-expm1f(log_q32(df) - ln));
+}
+__device__ __forceinline__ double logp64(double a, double b) {
+    if (a < 0.0 && b > 0.0) {
+        const double r2 = 0.70710678118654752440;
+        return log1p(-0.5 * (erfc(-a * r2) + erfc(b * r2)));
+    }
+    const double dn = a >= 0.0 ? a : -b, df = a >= 0.0 ? b : -a;
+    const double ln = log_q64(dn);
+    return ln + log(-expm1(log_q64(df) - ln));
 }
 
 // standardised distance from x to interval k (0 if x lies inside)
@@ -108,6 +101,13 @@ __device__ __forceinline__ float interval_dist(const LlrParams &p, int k, float 
     float a = (p.tf[k] - x) * p.inv_sigma;
     float b = (p.tf[k + 1] - x) * p.inv_sigma;
     return a >= 0.0f ? a : (b <= 0.0f ? -b : 0.0f);
+}
+
+__device__ __forceinline__ float lp_interval32(const LlrParams &p, int k, float x) {
+    return logp32((p.tf[k] - x) * p.inv_sigma, (p.tf[k + 1] - x) * p.inv_sigma);
+}
+__device__ __forceinline__ double lp_interval64(const LlrParams &p, int k, double x) {
+    return logp64((p.td[k] - x) * p.inv_sigma_d, (p.td[k + 1] - x) * p.inv_sigma_d);
 }
 
 __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
@@ -125,50 +125,68 @@ __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
     const LlrParams &p = sp;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int nc = p.K >> p.j;  // candidates consistent with the lower bits
+    const float lg_half_n = logf(0.5f * (float)nc);   // log |K_b|
     unsigned long long units = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
         ++units;
-        float x = xs[i];
-        double xd = (double)x;
+        const float x = xs[i];
         int low = 0;
         for (int b = 0; b < p.j; ++b) low |= (int)(lower[(int64_t)b * count + i] & 1) << b;
         // nearest candidate of each set
         float dmin[2] = {INFINITY, INFINITY};
         int kmin[2] = {0, 0};
         for (int u = 0; u < nc; ++u) {
-            int k = p.k_of_label[(u << p.j) | low];
-            float d = interval_dist(p, k, x);
-            int b = u & 1;
+            const int k = p.k_of_label[(u << p.j) | low];
+            const float d = interval_dist(p, k, x);
+            const int b = u & 1;
             if (d < dmin[b]) { dmin[b] = d; kmin[b] = k; }
         }
-        float lpn[2];
-        lpn[0] = logp_interval(p, kmin[0], x, xd, dmin[0]);
-        lpn[1] = logp_interval(p, kmin[1], x, xd, dmin[1]);
+        const float lpn0 = lp_interval32(p, kmin[0], x), lpn1 = lp_interval32(p, kmin[1], x);
         // a set whose whole mass is provably more than the clip below the other's
         // nearest term cannot move the clipped result
-        const float lg_half_n = logf(0.5f * (float)nc);   // log |K_b|
-        float ub0 = lg_half_n + (dmin[0] > 0.0f ? kLn05 - 0.5f * dmin[0] * dmin[0] : 0.0f);
-        float ub1 = lg_half_n + (dmin[1] > 0.0f ? kLn05 - 0.5f * dmin[1] * dmin[1] : 0.0f);
+        const float ub0 = lg_half_n + (dmin[0] > 0.0f ? kLn05 - 0.5f * dmin[0] * dmin[0] : 0.0f);
+        const float ub1 = lg_half_n + (dmin[1] > 0.0f ? kLn05 - 0.5f * dmin[1] * dmin[1] : 0.0f);
         float llr;
-        if (ub1 < lpn[0] - kLlrClip) {
+        if (ub1 < lpn0 - kLlrClip) {
             llr = kLlrClip;
-        } else if (ub0 < lpn[1] - kLlrClip) {
+        } else if (ub0 < lpn1 - kLlrClip) {
             llr = -kLlrClip;
-        } else {
-            float s[2] = {1.0f, 1.0f};
+        } else if (fmaxf(lpn0, lpn1) >= -kFarNats) {
+            // FP32: sums relative to each set's nearest term
+            float s0 = 1.0f, s1 = 1.0f;
             for (int u = 0; u < nc; ++u) {
-                int k = p.k_of_label[(u << p.j) | low];
-                int b = u & 1;
+                const int k = p.k_of_label[(u << p.j) | low];
+                const int b = u & 1;
                 if (k == kmin[b]) continue;
-                float d = interval_dist(p, k, x);
-                float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
-                if (bound < lpn[b] - kSkipNats) continue;
-                s[b] += expf(logp_interval(p, k, x, xd, d) - lpn[b]);
+                const float d = interval_dist(p, k, x);
+                const float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
+                const float ref = b ? lpn1 : lpn0;
+                if (bound < ref - kSkipNats) continue;
+                const float t = expf(lp_interval32(p, k, x) - ref);
+                if (b) s1 += t;
+                else s0 += t;
             }
-            llr = (lpn[0] + logf(s[0])) - (lpn[1] + logf(s[1]));
-            llr = fminf(fmaxf(llr, -kLlrClip), kLlrClip);
+            llr = (lpn0 + logf(s0)) - (lpn1 + logf(s1));
+        } else {
+            // far Gaussian tails of both sets (x beyond e^-50 of every candidate):
+            // the log-probabilities are large, so the difference is formed in FP64
+            const double xd = (double)x;
+            const double r0 = lp_interval64(p, kmin[0], xd), r1 = lp_interval64(p, kmin[1], xd);
+            double s0 = 1.0, s1 = 1.0;
+            for (int u = 0; u < nc; ++u) {
+                const int k = p.k_of_label[(u << p.j) | low];
+                const int b = u & 1;
+                if (k == kmin[b]) continue;
+                const float d = interval_dist(p, k, x);
+                const float bound = kLn05 - 0.5f * d * d;
+                if (bound < (b ? lpn1 : lpn0) - kSkipNats) continue;
+                const double t = exp(lp_interval64(p, k, xd) - (b ? r1 : r0));
+                if (b) s1 += t;
+                else s0 += t;
+            }
+            llr = (float)((r0 + log(s0)) - (r1 + log(s1)));
         }
-        out[i] = llr;
+        out[i] = fminf(fmaxf(llr, -kLlrClip), kLlrClip);
     }
     // x and the lower bits read, the LLR written
     prof_add(prof, units, units * (8 + p.j));

@@ -21,8 +21,8 @@ def L():
     return q.lib()
 
 
-def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "qkdrec.h")).read()
+def declared_symbols(header="qkdrec.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(qkdrec_[a-z0-9_]+)\s*\(", src)))
 
@@ -33,6 +33,10 @@ def test_every_declared_symbol_is_exported(L):
     for n in names:
         assert hasattr(L, n), n
     assert sorted(q.EXPORTED) == names
+    for header in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        for n in declared_symbols(header):
+            assert hasattr(L, n), (header, n)
+    assert sorted(q.SELFTEST) == declared_symbols("qkdrec_selftest.h")
 
 
 def test_version(L):
