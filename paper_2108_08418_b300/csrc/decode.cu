@@ -41,6 +41,8 @@ enum Algo { kSP = 0, kOMS = 1 };
 
 constexpr int kCheckWarps = 8;   // warps per check-kernel block
 constexpr int kChecksPerWarp = 4;
+// edge loads issued together in the first pass of a check (per lane: V frames each)
+template <int V> __host__ __device__ constexpr int chunk_of() { return V == 1 ? 8 : 4; }
 constexpr int32_t kMaxFrames = 65535 * 32;  // syndrome packing uses one grid row per 32 frames
 
 // ---------------------------------------------------------------- vector I/O
@@ -223,6 +225,7 @@ check_flood_f(DecArgs a) {
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
+    constexpr int CH = chunk_of<V>();
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
@@ -266,26 +269,34 @@ check_flood_f(DecArgs a) {
                         }
                     }
                 };
+                // loads of CH edges are issued together (indices past the last
+                // edge are clamped to it), so a warp keeps CH requests in flight
+                auto load = [&](int k, VF<V> &Lv, VF<V> &mo) {
+                    const int32_t e = beg + min(k, d - 1);
+                    Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                    if (a.do_msgs) mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                    else for (int i = 0; i < V; ++i) mo.v[i] = 0.0f;
+                };
                 if (DCMAX > 0 && ALGO == kSP) {
 #pragma unroll
-                    for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
-                        if (k < d) {
-                            const int32_t e = beg + k;
-                            const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                            VF<V> mo;
-                            if (a.do_msgs) mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
-                            else for (int i = 0; i < V; ++i) mo.v[i] = 0.0f;
-                            visit(k, Lv, mo, true);
+                    for (int k0 = 0; k0 < (DCMAX > 0 ? DCMAX : 1); k0 += CH) {
+                        if (k0 < d) {
+                            VF<V> Lv[CH], mo[CH];
+#pragma unroll
+                            for (int j = 0; j < CH; ++j) load(k0 + j, Lv[j], mo[j]);
+#pragma unroll
+                            for (int j = 0; j < CH; ++j)
+                                if (k0 + j < d) visit(k0 + j, Lv[j], mo[j], true);
                         }
                     }
                 } else {
-                    for (int k = 0; k < d; ++k) {
-                        const int32_t e = beg + k;
-                        const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                        VF<V> mo;
-                        if (a.do_msgs) mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
-                        else for (int i = 0; i < V; ++i) mo.v[i] = 0.0f;
-                        visit(k, Lv, mo, false);
+                    for (int k0 = 0; k0 < d; k0 += CH) {
+                        VF<V> Lv[CH], mo[CH];
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) load(k0 + j, Lv[j], mo[j]);
+#pragma unroll
+                        for (int j = 0; j < CH; ++j)
+                            if (k0 + j < d) visit(k0 + j, Lv[j], mo[j], false);
                     }
                 }
                 unsat_bits |= par & act;
@@ -365,6 +376,7 @@ check_flood_i(DecArgs a) {
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
+    constexpr int CH = chunk_of<V>();
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
@@ -399,7 +411,14 @@ check_flood_i(DecArgs a) {
                     if (a.do_msgs) mo = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
                     else for (int i = 0; i < V; ++i) mo.v[i] = 0;
                 };
-                for (int k = 0; k < d; ++k) { VI<V> Lv, mo; load(k, Lv, mo); visit(k, Lv, mo); }
+                for (int k0 = 0; k0 < d; k0 += CH) {
+                    VI<V> Lv[CH], mo[CH];
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) load(min(k0 + j, d - 1), Lv[j], mo[j]);
+#pragma unroll
+                    for (int j = 0; j < CH; ++j)
+                        if (k0 + j < d) visit(k0 + j, Lv[j], mo[j]);
+                }
                 unsat_bits |= par & act;
                 if (!a.do_msgs) continue;
                 auto emit = [&](int k, bool sneg, int i) {

@@ -22,6 +22,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
+    constexpr int CH = chunk_of<V>();
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
@@ -50,15 +51,25 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
                 return fmaxf(((k == arg[i]) ? mn2[i] : mn1[i]) - a.beta, 0.0f);
             };
             if (DCMAX > 0) {
+                // CH edge loads in flight (indices past the last edge clamped to it)
 #pragma unroll
-                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
-                    if (k < d) {
-                        const int32_t e = beg + k;
-                        const VF<V> Lv = ldf_plain<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                        const VF<V> mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
-                        for (int i = 0; i < V; ++i) {
-                            qc[k][i] = Lv.v[i] - mo.v[i];
-                            visit(k, qc[k][i], i);
+                for (int k0 = 0; k0 < (DCMAX > 0 ? DCMAX : 1); k0 += CH) {
+                    if (k0 < d) {
+                        VF<V> Lv[CH], mo[CH];
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) {
+                            const int32_t e = beg + min(k0 + j, d - 1);
+                            Lv[j] = ldf_plain<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                            mo[j] = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                        }
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) {
+                            if (k0 + j < d) {
+                                for (int i = 0; i < V; ++i) {
+                                    qc[k0 + j][i] = Lv[j].v[i] - mo[j].v[i];
+                                    visit(k0 + j, qc[k0 + j][i], i);
+                                }
+                            }
                         }
                     }
                 }
@@ -119,6 +130,7 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
+    constexpr int CH = chunk_of<V>();
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
@@ -151,14 +163,23 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             };
             if (DCMAX > 0) {
 #pragma unroll
-                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
-                    if (k < d) {
-                        const int32_t e = beg + k;
-                        const VI<V> Lv = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                        const VI<V> mo = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
-                        for (int i = 0; i < V; ++i) {
-                            qc[k][i] = max(min(Lv.v[i] - mo.v[i], kPMax), -kPMax);
-                            visit(k, qc[k][i], i);
+                for (int k0 = 0; k0 < (DCMAX > 0 ? DCMAX : 1); k0 += CH) {
+                    if (k0 < d) {
+                        VI<V> Lv[CH], mo[CH];
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) {
+                            const int32_t e = beg + min(k0 + j, d - 1);
+                            Lv[j] = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
+                            mo[j] = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
+                        }
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) {
+                            if (k0 + j < d) {
+                                for (int i = 0; i < V; ++i) {
+                                    qc[k0 + j][i] = max(min(Lv[j].v[i] - mo[j].v[i], kPMax), -kPMax);
+                                    visit(k0 + j, qc[k0 + j][i], i);
+                                }
+                            }
                         }
                     }
                 }
