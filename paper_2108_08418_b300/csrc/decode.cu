@@ -67,25 +67,41 @@ template <> __device__ __forceinline__ void stf<4>(float *p, const VF<4> &a) {
     *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
 }
 
-// messages: float or half storage, float arithmetic
-template <int V> __device__ __forceinline__ VF<V> ldm(const float *p) { return ldf<V>(p); }
-template <int V> __device__ __forceinline__ void stm(float *p, const VF<V> &a) { stf<V>(p, a); }
+// messages: float or half storage, float arithmetic.  Messages are touched
+// once per kernel and the whole array exceeds L2, so they are loaded and
+// stored with the streaming (evict-first) hint to keep L2 for the posteriors.
+template <int V> __device__ __forceinline__ VF<V> ldm(const float *p);
+template <> __device__ __forceinline__ VF<1> ldm<1>(const float *p) { return VF<1>{{__ldcs(p)}}; }
+template <> __device__ __forceinline__ VF<4> ldm<4>(const float *p) {
+    const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+    return VF<4>{{t.x, t.y, t.z, t.w}};
+}
+template <int V> __device__ __forceinline__ void stm(float *p, const VF<V> &a);
+template <> __device__ __forceinline__ void stm<1>(float *p, const VF<1> &a) { __stcs(p, a.v[0]); }
+template <> __device__ __forceinline__ void stm<4>(float *p, const VF<4> &a) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(a.v[0], a.v[1], a.v[2], a.v[3]));
+}
 template <int V> __device__ __forceinline__ VF<V> ldm(const __half *p);
-template <> __device__ __forceinline__ VF<1> ldm<1>(const __half *p) { return VF<1>{{__half2float(__ldg(p))}}; }
+template <> __device__ __forceinline__ VF<1> ldm<1>(const __half *p) {
+    const unsigned short r = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return VF<1>{{__half2float(__ushort_as_half(r))}};
+}
 template <> __device__ __forceinline__ VF<4> ldm<4>(const __half *p) {
-    uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+    uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
     const float2 a = __half22float2(*reinterpret_cast<__half2 *>(&t.x));
     const float2 b = __half22float2(*reinterpret_cast<__half2 *>(&t.y));
     return VF<4>{{a.x, a.y, b.x, b.y}};
 }
 template <int V> __device__ __forceinline__ void stm(__half *p, const VF<V> &a);
-template <> __device__ __forceinline__ void stm<1>(__half *p, const VF<1> &a) { *p = __float2half_rn(a.v[0]); }
+template <> __device__ __forceinline__ void stm<1>(__half *p, const VF<1> &a) {
+    __stcs(reinterpret_cast<unsigned short *>(p), __half_as_ushort(__float2half_rn(a.v[0])));
+}
 template <> __device__ __forceinline__ void stm<4>(__half *p, const VF<4> &a) {
     __half2 x = __floats2half2_rn(a.v[0], a.v[1]), y = __floats2half2_rn(a.v[2], a.v[3]);
     uint2 t;
     t.x = *reinterpret_cast<uint32_t *>(&x);
     t.y = *reinterpret_cast<uint32_t *>(&y);
-    *reinterpret_cast<uint2 *>(p) = t;
+    __stcs(reinterpret_cast<uint2 *>(p), t);
 }
 // value a message has once stored (FP16 rounding; identity for FP32)
 __device__ __forceinline__ float as_stored(float x, const float *) { return x; }
@@ -109,11 +125,21 @@ template <> __device__ __forceinline__ VI<4> ldi8<4>(const int8_t *p) {
     const char4 t = *reinterpret_cast<const char4 *>(p);
     return VI<4>{{t.x, t.y, t.z, t.w}};
 }
+template <int V> __device__ __forceinline__ VI<V> ldi8s(const int8_t *p);   // streaming (messages)
+template <> __device__ __forceinline__ VI<1> ldi8s<1>(const int8_t *p) {
+    return VI<1>{{(int)(signed char)__ldcs(reinterpret_cast<const char *>(p))}};
+}
+template <> __device__ __forceinline__ VI<4> ldi8s<4>(const int8_t *p) {
+    const char4 t = __ldcs(reinterpret_cast<const char4 *>(p));
+    return VI<4>{{t.x, t.y, t.z, t.w}};
+}
 template <int V> __device__ __forceinline__ void sti8(int8_t *p, const VI<V> &a);
-template <> __device__ __forceinline__ void sti8<1>(int8_t *p, const VI<1> &a) { *p = (int8_t)a.v[0]; }
+template <> __device__ __forceinline__ void sti8<1>(int8_t *p, const VI<1> &a) {
+    __stcs(reinterpret_cast<char *>(p), (char)a.v[0]);
+}
 template <> __device__ __forceinline__ void sti8<4>(int8_t *p, const VI<4> &a) {
-    *reinterpret_cast<char4 *>(p) = make_char4((signed char)a.v[0], (signed char)a.v[1], (signed char)a.v[2],
-                                                (signed char)a.v[3]);
+    __stcs(reinterpret_cast<char4 *>(p), make_char4((signed char)a.v[0], (signed char)a.v[1], (signed char)a.v[2],
+                                                    (signed char)a.v[3]));
 }
 
 // column index read again in a second pass (volatile: not kept live from pass 1)
@@ -193,7 +219,17 @@ struct DecArgs {
     int32_t do_msgs;        // 0: parity test only
     float beta;             // OMS offset (float modes)
     unsigned long long *prof;  // (units, bytes) counters of this launch's kernel class, or NULL
+    int64_t E;              // edges
+    int32_t lgfb;           // log2 of the frame block FB
 };
+
+// Position of (item, frame f) in a frame-block-major array [Fp/FB][items][FB]:
+// the FB frames of one item are contiguous and one frame block of all items is
+// one contiguous region, so a kernel sweeping the checks of one frame range
+// streams through consecutive memory.
+__device__ __forceinline__ int64_t fpos(int64_t item, int64_t items, int64_t f, int lgfb) {
+    return (((f >> lgfb) * items + item) << lgfb) + (f & ((1 << lgfb) - 1));
+}
 
 // Merge the lanes' stopping-test bits (V bits at frame f0) into the 32-frame
 // words of this block's frame range, then publish each non-zero word with one
@@ -230,6 +266,7 @@ check_flood_f(DecArgs a) {
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         const bool fv_ok = fv < nvec;
+        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
         const uint32_t act = fv_ok ? active_bits<V>(a.active + f0) : 0u;
         uint32_t unsat_bits = 0;
         if (act) {
@@ -273,8 +310,8 @@ check_flood_f(DecArgs a) {
                 // edge are clamped to it), so a warp keeps CH requests in flight
                 auto load = [&](int k, VF<V> &Lv, VF<V> &mo) {
                     const int32_t e = beg + min(k, d - 1);
-                    Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                    if (a.do_msgs) mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                    Lv = ldf<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                    if (a.do_msgs) mo = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
                     else for (int i = 0; i < V; ++i) mo.v[i] = 0.0f;
                 };
                 if (DCMAX > 0 && ALGO == kSP) {
@@ -320,7 +357,7 @@ check_flood_f(DecArgs a) {
                             VF<V> mn;
                             for (int i = 0; i < V; ++i)
                                 mn.v[i] = emit(k, fc[k][i], ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
-                            stm<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
+                            stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
                         }
                     }
                 } else if (DCMAX > 0) {
@@ -331,21 +368,21 @@ check_flood_f(DecArgs a) {
                         VF<V> mn;
                         for (int i = 0; i < V; ++i)
                             mn.v[i] = emit(k, 0.0f, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
-                        stm<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
+                        stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
                     }
                 } else {
                     // degree above the register cache: signs and phi values again from memory
                     uint32_t negall = s;
                     for (int k = 0; k < d; ++k) {
                         const int32_t e = beg + k;
-                        const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                        const VF<V> mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                        const VF<V> mo = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
                         for (int i = 0; i < V; ++i) negall ^= (uint32_t)(Lv.v[i] - mo.v[i] < 0.0f) << i;
                     }
                     for (int k = 0; k < d; ++k) {
                         const int32_t e = beg + k;
-                        const VF<V> Lv = ldf<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                        MsgT *mp = msg + (int64_t)e * a.Fp + f0;
+                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                        MsgT *mp = msg + bM + ((int64_t)(e) << a.lgfb);
                         const VF<V> mo = ldm<V>(mp);
                         VF<V> mn;
                         for (int i = 0; i < V; ++i) {
@@ -381,6 +418,7 @@ check_flood_i(DecArgs a) {
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         const bool fv_ok = fv < nvec;
+        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
         const uint32_t act = fv_ok ? active_bits<V>(a.active + f0) : 0u;
         uint32_t unsat_bits = 0;
         if (act) {
@@ -407,8 +445,8 @@ check_flood_i(DecArgs a) {
                 };
                 auto load = [&](int k, VI<V> &Lv, VI<V> &mo) {
                     const int32_t e = beg + k;
-                    Lv = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                    if (a.do_msgs) mo = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
+                    Lv = ldi16<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                    if (a.do_msgs) mo = ldi8s<V>(msg + bM + ((int64_t)(e) << a.lgfb));
                     else for (int i = 0; i < V; ++i) mo.v[i] = 0;
                 };
                 for (int k0 = 0; k0 < d; k0 += CH) {
@@ -432,7 +470,7 @@ check_flood_i(DecArgs a) {
                     for (int k = 0; k < d; ++k) {
                         VI<V> mn;
                         for (int i = 0; i < V; ++i) mn.v[i] = emit(k, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
-                        sti8<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
+                        sti8<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
                     }
                 } else {
                     uint32_t negall = s;
@@ -449,7 +487,7 @@ check_flood_i(DecArgs a) {
                             const int q = max(min(Lv.v[i] - mo.v[i], kQMax), -kQMax);
                             mn.v[i] = emit(k, ((negall >> i) & 1u) ^ (q < 0), i);
                         }
-                        sti8<V>(msg + (int64_t)(beg + k) * a.Fp + f0, mn);
+                        sti8<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
                     }
                 }
             }
@@ -474,6 +512,7 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
     unsigned long long units = 0, bytes = 0;
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
         const int64_t v = item / a.FV, fv = item - v * a.FV, f0 = 4 * fv;
+        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);
         if (v == 0 && (fv & 7) == 0 && a.early_stop) a.unsat_next[fv >> 3] = 0;  // next test starts clear
         const uint32_t act = active_bits<4>(a.active + f0);
         if (!act) continue;
@@ -488,39 +527,40 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
                 }
         if (!upd) continue;
         const int32_t vb = __ldg(a.vptr + v), ve = __ldg(a.vptr + v + 1);
+        const int64_t pv = bL + ((int64_t)(v) << a.lgfb);
         const unsigned nu = __popc(upd);
         units += nu;
         bytes += (unsigned long long)nu * ((ve - vb) * ms + cs + ls);
         if (PREC != kI8) {
             float *L = reinterpret_cast<float *>(a.L);
-            VF<4> s = ldf<4>(reinterpret_cast<const float *>(a.llr_i) + item * 4);
+            VF<4> s = ldf<4>(reinterpret_cast<const float *>(a.llr_i) + pv);
             for (int32_t k = vb; k < ve; ++k) {
                 const int64_t e = __ldg(a.vedge + k);
                 VF<4> m;
-                if (PREC == kF32) m = ldm<4>(reinterpret_cast<const float *>(a.msg) + e * a.Fp + f0);
-                else m = ldm<4>(reinterpret_cast<const __half *>(a.msg) + e * a.Fp + f0);
+                if (PREC == kF32) m = ldm<4>(reinterpret_cast<const float *>(a.msg) + bM + ((int64_t)(e) << a.lgfb));
+                else m = ldm<4>(reinterpret_cast<const __half *>(a.msg) + bM + ((int64_t)(e) << a.lgfb));
                 for (int i = 0; i < 4; ++i) s.v[i] += m.v[i];
             }
             if (upd != 0xfu) {
-                const VF<4> old = ldf_plain<4>(L + item * 4);
+                const VF<4> old = ldf_plain<4>(L + pv);
                 for (int i = 0; i < 4; ++i)
                     if (!((upd >> i) & 1u)) s.v[i] = old.v[i];
             }
-            stf<4>(L + item * 4, s);
+            stf<4>(L + pv, s);
         } else {
             int16_t *L = reinterpret_cast<int16_t *>(a.L);
-            VI<4> s = ldi8<4>(reinterpret_cast<const int8_t *>(a.llr_i) + item * 4);
+            VI<4> s = ldi8<4>(reinterpret_cast<const int8_t *>(a.llr_i) + pv);
             for (int32_t k = vb; k < ve; ++k) {
                 const int64_t e = __ldg(a.vedge + k);
-                const VI<4> m = ldi8<4>(reinterpret_cast<const int8_t *>(a.msg) + e * a.Fp + f0);
+                const VI<4> m = ldi8s<4>(reinterpret_cast<const int8_t *>(a.msg) + bM + ((int64_t)(e) << a.lgfb));
                 for (int i = 0; i < 4; ++i) s.v[i] = max(min(s.v[i] + m.v[i], kPMax), -kPMax);
             }
             if (upd != 0xfu) {
-                const VI<4> old = ldi16<4>(L + item * 4);
+                const VI<4> old = ldi16<4>(L + pv);
                 for (int i = 0; i < 4; ++i)
                     if (!((upd >> i) & 1u)) s.v[i] = old.v[i];
             }
-            sti16<4>(L + item * 4, s);
+            sti16<4>(L + pv, s);
         }
     }
     prof_add(a.prof, units, bytes);
@@ -530,8 +570,8 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
 // llr [F][n] -> llr_i [n][Fp] and L [n][Fp]; padding frames get a
 // confident all-zero word (they satisfy a zero syndrome at iteration 0).
 template <int PREC>
-__global__ void prep_llr(const float *__restrict__ llr, int32_t F, int32_t n, int64_t Fp, float step,
-                         void *llr_i, void *L) {
+__global__ void prep_llr(const float *__restrict__ llr, int32_t F, int32_t n, int64_t Fp, int lgfb,
+                         float step, void *llr_i, void *L) {
     __shared__ float tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t v0 = (int64_t)blockIdx.x * 32, f0 = (int64_t)blockIdx.y * 32;
@@ -546,7 +586,7 @@ __global__ void prep_llr(const float *__restrict__ llr, int32_t F, int32_t n, in
         const int64_t v = v0 + ty + r, f = f0 + tx;
         if (v >= n || f >= Fp) continue;
         const float val = tile[tx][ty + r];
-        const int64_t o = v * Fp + f;
+        const int64_t o = fpos(v, n, f, lgfb);
         if (PREC == kI8) {
             // round half away from zero on the step grid, clip to +-31
             const float rr = val / step;
@@ -611,7 +651,7 @@ __global__ void finalize(int32_t F, int32_t T, int32_t accumulate, const uint8_t
 
 // L [n][Fp] -> bits [F][n] (+ posterior [F][n]) for the frames in `mask`.
 template <int PREC>
-__global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, float step,
+__global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int lgfb, float step,
                           const uint8_t *__restrict__ mask, uint8_t *bits, float *post) {
     __shared__ float tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -620,8 +660,8 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, floa
         const int64_t v = v0 + ty + r, f = f0 + tx;
         float val = 0.0f;
         if (v < n && f < Fp) {
-            if (PREC == kI8) val = (float)reinterpret_cast<const int16_t *>(Lp)[v * Fp + f];
-            else val = reinterpret_cast<const float *>(Lp)[v * Fp + f];
+            if (PREC == kI8) val = (float)reinterpret_cast<const int16_t *>(Lp)[fpos(v, n, f, lgfb)];
+            else val = reinterpret_cast<const float *>(Lp)[fpos(v, n, f, lgfb)];
         }
         tile[tx][ty + r] = val;
     }
@@ -638,12 +678,26 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, floa
 // ------------------------------------------------------------------ layout
 struct Layout {
     int64_t Fp, FV, W;
+    int lgfb;
     size_t llr_i, L, msg, sbits, active, mask, unsat0, unsat1, iters, total;
 };
 
-static Layout make_layout(const CodeDev &d, int32_t F, int prec) {
+// register-cache size of the check kernels for a code: 8 or 32 edges, 0 = reload
+static int dc_class(const CodeDev &d) { return d.dc_max <= 8 ? 8 : (d.dc_max <= 32 ? 32 : 0); }
+
+// Frames per lane of the main kernel of a decode: one for sum-product and for
+// the layered schedule (their per-edge state lives in registers), four for
+// flooding min-sum.  The frame block is 32 lanes' worth of frames.
+static int lanes_v(const CodeDev &d, int algo, int prec) {
+    if (dc_class(d) == 0) return 4;
+    if (algo == QKDREC_OMS_LAYERED) return 1;
+    return (algo == QKDREC_SP_FLOOD && prec != kI8) ? 1 : 4;
+}
+
+static Layout make_layout(const CodeDev &d, int32_t F, int algo, int prec) {
     Layout l;
-    l.Fp = align_up((size_t)(F > 0 ? F : 1), 4);
+    l.lgfb = lanes_v(d, algo, prec) == 1 ? 5 : 7;
+    l.Fp = align_up((size_t)(F > 0 ? F : 1), (size_t)1 << l.lgfb);
     l.FV = l.Fp / 4;
     l.W = ceil_div(l.Fp, 32);
     const size_t ms = prec == kF32 ? 4 : (prec == kF16 ? 2 : 1);
@@ -670,9 +724,9 @@ static bool opts_ok(const qkdrec_decode_opts *o) {
 }
 
 static size_t workspace_for(const CodeDev &d, int32_t F, const qkdrec_decode_opts *o) {
-    size_t b = make_layout(d, F, o->prec).total;
+    size_t b = make_layout(d, F, o->algo, o->prec).total;
     if (o->fallback_f32 && o->prec != kF32) {
-        size_t b32 = make_layout(d, F, kF32).total;
+        size_t b32 = make_layout(d, F, o->algo, kF32).total;
         if (b32 > b) b = b32;
     }
     return b;
@@ -682,9 +736,6 @@ struct Prepared {
     uint32_t *unsat[2];
     uint8_t *mask;
 };
-
-// register-cache size of the check kernels for a code: 8 or 32 edges, 0 = reload
-static int dc_class(const CodeDev &d) { return d.dc_max <= 8 ? 8 : (d.dc_max <= 32 ? 32 : 0); }
 
 // Launch geometry of a check-type kernel with V frames per lane.
 struct Geom {
@@ -719,6 +770,8 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     a.llr_i = ws + l.llr_i;
     a.Fp = l.Fp;
     a.FV = l.FV;
+    a.E = d.E;
+    a.lgfb = l.lgfb;
     a.W = l.W;
     a.n = d.n;
     a.M = d.M;
@@ -742,8 +795,9 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     {
         prof::Scope ps(prof::kPrep, st);
         dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
-        if (prec == kI8) prep_llr<kI8><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, o.llr_step, ws + l.llr_i, ws + l.L);
-        else prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, o.llr_step, ws + l.llr_i, ws + l.L);
+        if (prec == kI8)
+            prep_llr<kI8><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L);
+        else prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L);
     }
     QKD_LAUNCHED("prep_llr");
     {
@@ -771,8 +825,9 @@ static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const 
     QKD_LAUNCHED("finalize");
     prof::Scope ps(prof::kFinish, st);
     dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
-    if (prec == kI8) write_out<kI8><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, o.llr_step, pr.mask, bits_out, post_out);
-    else write_out<kF32><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, o.llr_step, pr.mask, bits_out, post_out);
+    if (prec == kI8)
+        write_out<kI8><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out, post_out);
+    else write_out<kF32><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out, post_out);
     QKD_LAUNCHED("write_out");
     return QKDREC_OK;
 }
@@ -817,7 +872,7 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
                                const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev,
                                uint8_t *bits_out, int32_t *iters_out, uint8_t *conv_out,
                                float *post_out, char *ws, cudaStream_t st) {
-    const Layout l = make_layout(d, F, prec);
+    const Layout l = make_layout(d, F, o.algo, prec);
     DecArgs a;
     Prepared pr;
     qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, ws, l, st, a, pr);

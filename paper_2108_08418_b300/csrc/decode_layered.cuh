@@ -27,6 +27,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         if (fv >= nvec) continue;
+        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
         const uint32_t act = active_bits<V>(a.active + f0);
         if (!act) continue;
         const int nact = __popc(act);
@@ -59,8 +60,8 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
                             const int32_t e = beg + min(k0 + j, d - 1);
-                            Lv[j] = ldf_plain<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                            mo[j] = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                            Lv[j] = ldf_plain<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                            mo[j] = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
                         }
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
@@ -85,22 +86,22 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
                             // later layers subtract the stored (possibly FP16-rounded) message
                             Ln.v[i] = q + as_stored(mn.v[i], msg);
                         }
-                        stm<V>(msg + (int64_t)e * a.Fp + f0, mn);
-                        stf<V>(L + (int64_t)ld_index_again(a.ci + e) * a.Fp + f0, Ln);
+                        stm<V>(msg + bM + ((int64_t)(e) << a.lgfb), mn);
+                        stf<V>(L + bL + ((int64_t)(ld_index_again(a.ci + e)) << a.lgfb), Ln);
                     }
                 }
             } else {
                 for (int k = 0; k < d; ++k) {
                     const int32_t e = beg + k;
-                    const VF<V> Lv = ldf_plain<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                    const VF<V> mo = ldm<V>(msg + (int64_t)e * a.Fp + f0);
+                    const VF<V> Lv = ldf_plain<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                    const VF<V> mo = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
                     for (int i = 0; i < V; ++i) visit(k, Lv.v[i] - mo.v[i], i);
                 }
                 for (int k = 0; k < d; ++k) {
                     const int32_t e = beg + k;
-                    float *Lp = L + (int64_t)__ldg(a.ci + e) * a.Fp + f0;
+                    float *Lp = L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb);
                     const VF<V> Lv = ldf_plain<V>(Lp);
-                    MsgT *mp = msg + (int64_t)e * a.Fp + f0;
+                    MsgT *mp = msg + bM + ((int64_t)(e) << a.lgfb);
                     const VF<V> mo = ldm<V>(mp);
                     VF<V> mn, Ln;
                     for (int i = 0; i < V; ++i) {
@@ -135,6 +136,7 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         if (fv >= nvec) continue;
+        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
         const uint32_t act = active_bits<V>(a.active + f0);
         if (!act) continue;
         const int nact = __popc(act);
@@ -169,8 +171,8 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
                             const int32_t e = beg + min(k0 + j, d - 1);
-                            Lv[j] = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                            mo[j] = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
+                            Lv[j] = ldi16<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                            mo[j] = ldi8s<V>(msg + bM + ((int64_t)(e) << a.lgfb));
                         }
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
@@ -192,22 +194,22 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
                             mn.v[i] = message(k, qc[k][i], i);
                             Ln.v[i] = max(min(qc[k][i] + mn.v[i], kPMax), -kPMax);
                         }
-                        sti8<V>(msg + (int64_t)e * a.Fp + f0, mn);
-                        sti16<V>(L + (int64_t)ld_index_again(a.ci + e) * a.Fp + f0, Ln);
+                        sti8<V>(msg + bM + ((int64_t)(e) << a.lgfb), mn);
+                        sti16<V>(L + bL + ((int64_t)(ld_index_again(a.ci + e)) << a.lgfb), Ln);
                     }
                 }
             } else {
                 for (int k = 0; k < d; ++k) {
                     const int32_t e = beg + k;
-                    const VI<V> Lv = ldi16<V>(L + (int64_t)__ldg(a.ci + e) * a.Fp + f0);
-                    const VI<V> mo = ldi8<V>(msg + (int64_t)e * a.Fp + f0);
+                    const VI<V> Lv = ldi16<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
+                    const VI<V> mo = ldi8s<V>(msg + bM + ((int64_t)(e) << a.lgfb));
                     for (int i = 0; i < V; ++i) visit(k, max(min(Lv.v[i] - mo.v[i], kPMax), -kPMax), i);
                 }
                 for (int k = 0; k < d; ++k) {
                     const int32_t e = beg + k;
-                    int16_t *Lp = L + (int64_t)__ldg(a.ci + e) * a.Fp + f0;
+                    int16_t *Lp = L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb);
                     const VI<V> Lv = ldi16<V>(Lp);
-                    int8_t *mp = msg + (int64_t)e * a.Fp + f0;
+                    int8_t *mp = msg + bM + ((int64_t)(e) << a.lgfb);
                     const VI<V> mo = ldi8<V>(mp);
                     VI<V> mn, Ln;
                     for (int i = 0; i < V; ++i) {
@@ -238,8 +240,8 @@ __global__ void retire(int64_t Fp, int64_t W, int32_t t, uint8_t *active, int32_
 }
 
 static void launch_layer(DecArgs a, const CodeDev &d, int prec, int32_t lb, int32_t ls, cudaStream_t st) {
+    const int V = lanes_v(d, QKDREC_OMS_LAYERED, prec);
     const int dcc = dc_class(d);
-    const int V = dcc > 0 ? 1 : 4;
     const Geom g = check_geom(a.Fp, V, ls);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
@@ -263,7 +265,7 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *syn
                           const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev,
                           uint8_t *bits_out, int32_t *iters_out, uint8_t *conv_out, float *post_out,
                           char *ws, cudaStream_t st) {
-    const Layout l = make_layout(d, F, prec);
+    const Layout l = make_layout(d, F, o.algo, prec);
     DecArgs a;
     Prepared pr;
     qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, ws, l, st, a, pr);
