@@ -251,9 +251,18 @@ __device__ __forceinline__ void publish_unsat(uint32_t bits, int64_t f0, int64_t
 // (one per slot) over fvw frame vectors of V frames.  blockIdx.x walks check
 // groups (so the resident blocks share one range of frames and their
 // posterior gathers hit L2), blockIdx.y walks frame ranges.
-template <int ALGO, typename MsgT, int V, int DCMAX>
-__global__ void __launch_bounds__(kCheckWarps * 32, 2)
+//
+// CACHED (check degree <= kStash): pass 1 keeps what pass 2 needs -- the signs
+// of the v->c messages in a bit mask and, for sum-product, phi(|q|) of every
+// edge in shared memory ([warp][edge][lane], conflict-free) -- so pass 2 only
+// computes and stores the outgoing messages.  Otherwise pass 2 reads the
+// posteriors and old messages again.
+constexpr int kStash = 32;
+
+template <int ALGO, typename MsgT, int V, bool CACHED>
+__global__ void __launch_bounds__(kCheckWarps * 32, 3)
 check_flood_f(DecArgs a) {
+    extern __shared__ float stash[];  // SP cached: [kCheckWarps][kStash][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
@@ -262,6 +271,8 @@ check_flood_f(DecArgs a) {
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
     constexpr int CH = chunk_of<V>();
+    constexpr bool SP_STASH = ALGO == kSP && CACHED && V == 1;
+    float *my = stash + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
@@ -281,7 +292,6 @@ check_flood_f(DecArgs a) {
                 uint32_t sg[V];             // bit k: q of edge k negative
                 float acc0[V], acc1[V];     // SP: sum of phi except the largest, largest phi
                 int32_t arg[V];             // OMS: min1, min2
-                float fc[DCMAX > 0 ? DCMAX : 1][V];
                 for (int i = 0; i < V; ++i) {
                     sg[i] = 0;
                     acc0[i] = ALGO == kSP ? 0.0f : INFINITY;
@@ -289,51 +299,36 @@ check_flood_f(DecArgs a) {
                     arg[i] = -1;
                 }
                 units += (unsigned long long)d * nact;
-                auto visit = [&](int k, const VF<V> &Lv, const VF<V> &mo, bool keep) {
-                    for (int i = 0; i < V; ++i) {
-                        par ^= (uint32_t)(Lv.v[i] < 0.0f) << i;
-                        const float q = Lv.v[i] - mo.v[i];
-                        if (k < 32) sg[i] |= (uint32_t)(q < 0.0f) << k;
-                        if (ALGO == kSP) {
-                            const float f = phi_clamped(fabsf(q));
-                            if (keep) fc[k < DCMAX ? k : 0][i] = f;
-                            if (f > acc1[i]) { acc0[i] += acc1[i]; acc1[i] = f; arg[i] = k; }
-                            else acc0[i] += f;
-                        } else {
-                            const float m = fabsf(q);
-                            if (m < acc0[i]) { acc1[i] = acc0[i]; acc0[i] = m; arg[i] = k; }
-                            else if (m < acc1[i]) acc1[i] = m;
-                        }
-                    }
-                };
                 // loads of CH edges are issued together (indices past the last
                 // edge are clamped to it), so a warp keeps CH requests in flight
-                auto load = [&](int k, VF<V> &Lv, VF<V> &mo) {
-                    const int32_t e = beg + min(k, d - 1);
-                    Lv = ldf<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                    if (a.do_msgs) mo = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
-                    else for (int i = 0; i < V; ++i) mo.v[i] = 0.0f;
-                };
-                if (DCMAX > 0 && ALGO == kSP) {
+                for (int k0 = 0; k0 < d; k0 += CH) {
+                    VF<V> Lv[CH], mo[CH];
 #pragma unroll
-                    for (int k0 = 0; k0 < (DCMAX > 0 ? DCMAX : 1); k0 += CH) {
-                        if (k0 < d) {
-                            VF<V> Lv[CH], mo[CH];
-#pragma unroll
-                            for (int j = 0; j < CH; ++j) load(k0 + j, Lv[j], mo[j]);
-#pragma unroll
-                            for (int j = 0; j < CH; ++j)
-                                if (k0 + j < d) visit(k0 + j, Lv[j], mo[j], true);
-                        }
+                    for (int j = 0; j < CH; ++j) {
+                        const int32_t e = beg + min(k0 + j, d - 1);
+                        Lv[j] = ldf<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
+                        if (a.do_msgs) mo[j] = ldm<V>(msg + bM + ((int64_t)e << a.lgfb));
+                        else for (int i = 0; i < V; ++i) mo[j].v[i] = 0.0f;
                     }
-                } else {
-                    for (int k0 = 0; k0 < d; k0 += CH) {
-                        VF<V> Lv[CH], mo[CH];
 #pragma unroll
-                        for (int j = 0; j < CH; ++j) load(k0 + j, Lv[j], mo[j]);
-#pragma unroll
-                        for (int j = 0; j < CH; ++j)
-                            if (k0 + j < d) visit(k0 + j, Lv[j], mo[j], false);
+                    for (int j = 0; j < CH; ++j) {
+                        const int k = k0 + j;
+                        if (k >= d) break;
+                        for (int i = 0; i < V; ++i) {
+                            par ^= (uint32_t)(Lv[j].v[i] < 0.0f) << i;
+                            const float q = Lv[j].v[i] - mo[j].v[i];
+                            if (CACHED) sg[i] |= (uint32_t)(q < 0.0f) << k;
+                            if (ALGO == kSP) {
+                                const float f = phi_clamped(fabsf(q));
+                                if (SP_STASH) my[k * 32] = f;
+                                if (f > acc1[i]) { acc0[i] += acc1[i]; acc1[i] = f; arg[i] = k; }
+                                else acc0[i] += f;
+                            } else {
+                                const float m = fabsf(q);
+                                if (m < acc0[i]) { acc1[i] = acc0[i]; acc0[i] = m; arg[i] = k; }
+                                else if (m < acc1[i]) acc1[i] = m;
+                            }
+                        }
                     }
                 }
                 unsat_bits |= par & act;
@@ -348,41 +343,28 @@ check_flood_f(DecArgs a) {
                     }
                     return sneg_k ? -mag : mag;
                 };
-                if (DCMAX > 0 && ALGO == kSP) {
+                if (CACHED && (ALGO != kSP || SP_STASH)) {
                     uint32_t neg = s;       // syndrome xor all signs of q
-                    for (int i = 0; i < V; ++i) neg ^= (uint32_t)(__popc(sg[i]) & 1) << i;
-#pragma unroll
-                    for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
-                        if (k < d) {
-                            VF<V> mn;
-                            for (int i = 0; i < V; ++i)
-                                mn.v[i] = emit(k, fc[k][i], ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
-                            stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
-                        }
-                    }
-                } else if (DCMAX > 0) {
-                    // min-sum: the outgoing message needs only the signs kept in pass 1
-                    uint32_t neg = s;
                     for (int i = 0; i < V; ++i) neg ^= (uint32_t)(__popc(sg[i]) & 1) << i;
                     for (int k = 0; k < d; ++k) {
                         VF<V> mn;
                         for (int i = 0; i < V; ++i)
-                            mn.v[i] = emit(k, 0.0f, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
+                            mn.v[i] = emit(k, SP_STASH ? my[k * 32] : 0.0f, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
                         stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
                     }
                 } else {
-                    // degree above the register cache: signs and phi values again from memory
+                    // signs and phi values again from memory
                     uint32_t negall = s;
                     for (int k = 0; k < d; ++k) {
                         const int32_t e = beg + k;
-                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                        const VF<V> mo = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
+                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
+                        const VF<V> mo = ldm<V>(msg + bM + ((int64_t)e << a.lgfb));
                         for (int i = 0; i < V; ++i) negall ^= (uint32_t)(Lv.v[i] - mo.v[i] < 0.0f) << i;
                     }
                     for (int k = 0; k < d; ++k) {
                         const int32_t e = beg + k;
-                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                        MsgT *mp = msg + bM + ((int64_t)(e) << a.lgfb);
+                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
+                        MsgT *mp = msg + bM + ((int64_t)e << a.lgfb);
                         const VF<V> mo = ldm<V>(mp);
                         VF<V> mn;
                         for (int i = 0; i < V; ++i) {
@@ -683,7 +665,7 @@ struct Layout {
 };
 
 // register-cache size of the check kernels for a code: 8 or 32 edges, 0 = reload
-static int dc_class(const CodeDev &d) { return d.dc_max <= 8 ? 8 : (d.dc_max <= 32 ? 32 : 0); }
+static int dc_class(const CodeDev &d) { return d.dc_max <= 8 ? 8 : (d.dc_max <= kStash ? 32 : 0); }
 
 // Frames per lane of the main kernel of a decode: one for sum-product and for
 // the layered schedule (their per-edge state lives in registers), four for
@@ -836,35 +818,32 @@ static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const 
 // frame per lane so that the phi values of a check fit in registers; min-sum
 // only keeps sign bits and runs four frames per lane.
 static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaStream_t st) {
-    const int dcc = dc_class(d);
-    const int V = (prec != kI8 && algo == QKDREC_SP_FLOOD && dcc > 0) ? 1 : 4;
+    const bool cached = dc_class(d) > 0;
+    const int V = (prec != kI8 && algo == QKDREC_SP_FLOOD && cached) ? 1 : 4;
     const Geom g = check_geom(a.Fp, V, d.M);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
-#define QKD_CHK(ALG, T, VV, DC) check_flood_f<ALG, T, VV, DC><<<g.grid, B, 0, st>>>(a)
+    const size_t stash = (size_t)kCheckWarps * kStash * 32 * sizeof(float);
     if (prec == kI8) {
-        if (dcc > 0) check_flood_i<4, 32><<<g.grid, B, 0, st>>>(a);
+        if (cached) check_flood_i<4, 32><<<g.grid, B, 0, st>>>(a);
         else check_flood_i<4, 0><<<g.grid, B, 0, st>>>(a);
     } else if (algo == QKDREC_SP_FLOOD) {
         if (prec == kF32) {
-            if (dcc == 8) QKD_CHK(kSP, float, 1, 8);
-            else if (dcc == 32) QKD_CHK(kSP, float, 1, 32);
-            else QKD_CHK(kSP, float, 4, 0);
+            if (cached) check_flood_f<kSP, float, 1, true><<<g.grid, B, stash, st>>>(a);
+            else check_flood_f<kSP, float, 4, false><<<g.grid, B, 0, st>>>(a);
         } else {
-            if (dcc == 8) QKD_CHK(kSP, __half, 1, 8);
-            else if (dcc == 32) QKD_CHK(kSP, __half, 1, 32);
-            else QKD_CHK(kSP, __half, 4, 0);
+            if (cached) check_flood_f<kSP, __half, 1, true><<<g.grid, B, stash, st>>>(a);
+            else check_flood_f<kSP, __half, 4, false><<<g.grid, B, 0, st>>>(a);
         }
     } else {
         if (prec == kF32) {
-            if (dcc > 0) QKD_CHK(kOMS, float, 4, 32);
-            else QKD_CHK(kOMS, float, 4, 0);
+            if (cached) check_flood_f<kOMS, float, 4, true><<<g.grid, B, 0, st>>>(a);
+            else check_flood_f<kOMS, float, 4, false><<<g.grid, B, 0, st>>>(a);
         } else {
-            if (dcc > 0) QKD_CHK(kOMS, __half, 4, 32);
-            else QKD_CHK(kOMS, __half, 4, 0);
+            if (cached) check_flood_f<kOMS, __half, 4, true><<<g.grid, B, 0, st>>>(a);
+            else check_flood_f<kOMS, __half, 4, false><<<g.grid, B, 0, st>>>(a);
         }
     }
-#undef QKD_CHK
 }
 
 // One flooding decode pass over the frames selected by conv_prev (NULL = all).

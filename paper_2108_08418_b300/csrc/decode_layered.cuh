@@ -12,9 +12,12 @@
 // above the register cache reads them again and keeps retired frames frozen.
 
 // ------------------------------------------------------------ float layered
-template <typename MsgT, int V, int DCMAX>
-__global__ void __launch_bounds__(kCheckWarps * 32, 2)
+// CACHED (degree <= kStash, one frame per lane): the q values of a check are
+// kept in shared memory ([warp][edge][lane]) between the two passes.
+template <typename MsgT, int V, bool CACHED>
+__global__ void __launch_bounds__(kCheckWarps * 32, 3)
 layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
+    extern __shared__ float qstash[];  // [kCheckWarps][kStash][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
@@ -23,6 +26,8 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
     constexpr int CH = chunk_of<V>();
+    constexpr bool STASH = CACHED && V == 1;
+    float *my = qstash + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
@@ -31,88 +36,63 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
         const uint32_t act = active_bits<V>(a.active + f0);
         if (!act) continue;
         const int nact = __popc(act);
-        const int64_t k0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
+        const int64_t k0c = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
         for (int it = 0; it < kChecksPerWarp; ++it) {
-            const int64_t kk = k0 + it * slots + slot;
+            const int64_t kk = k0c + it * slots + slot;
             if (kk >= lsize) break;
             const int32_t c = __ldg(lchk + lbeg + kk);
             const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1), d = end - beg;
             uint32_t neg = (__ldg(a.sbits + (int64_t)c * a.W + (f0 >> 5)) >> (f0 & 31)) & vmask;
             units += (unsigned long long)d * nact;
-            float mn1[V], mn2[V], qc[DCMAX > 0 ? DCMAX : 1][V];
+            float mn1[V], mn2[V];
             int32_t arg[V];
             for (int i = 0; i < V; ++i) { mn1[i] = INFINITY; mn2[i] = INFINITY; arg[i] = -1; }
-            auto visit = [&](int k, float q, int i) {
-                neg ^= (uint32_t)(q < 0.0f) << i;
-                const float m = fabsf(q);
-                if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = k; }
-                else if (m < mn2[i]) mn2[i] = m;
-            };
-            auto magnitude = [&](int k, int i) {
-                return fmaxf(((k == arg[i]) ? mn2[i] : mn1[i]) - a.beta, 0.0f);
-            };
-            if (DCMAX > 0) {
-                // CH edge loads in flight (indices past the last edge clamped to it)
+            // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
+            for (int k0 = 0; k0 < d; k0 += CH) {
+                VF<V> Lv[CH], mo[CH];
 #pragma unroll
-                for (int k0 = 0; k0 < (DCMAX > 0 ? DCMAX : 1); k0 += CH) {
-                    if (k0 < d) {
-                        VF<V> Lv[CH], mo[CH];
-#pragma unroll
-                        for (int j = 0; j < CH; ++j) {
-                            const int32_t e = beg + min(k0 + j, d - 1);
-                            Lv[j] = ldf_plain<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                            mo[j] = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
-                        }
-#pragma unroll
-                        for (int j = 0; j < CH; ++j) {
-                            if (k0 + j < d) {
-                                for (int i = 0; i < V; ++i) {
-                                    qc[k0 + j][i] = Lv[j].v[i] - mo[j].v[i];
-                                    visit(k0 + j, qc[k0 + j][i], i);
-                                }
-                            }
-                        }
-                    }
+                for (int j = 0; j < CH; ++j) {
+                    const int32_t e = beg + min(k0 + j, d - 1);
+                    Lv[j] = ldf_plain<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
+                    mo[j] = ldm<V>(msg + bM + ((int64_t)e << a.lgfb));
                 }
 #pragma unroll
-                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
-                    if (k < d) {
-                        const int32_t e = beg + k;
-                        VF<V> mn, Ln;
-                        for (int i = 0; i < V; ++i) {
-                            const float q = qc[k][i];
-                            const float mag = magnitude(k, i);
-                            mn.v[i] = (((neg >> i) & 1u) ^ (q < 0.0f)) ? -mag : mag;
-                            // later layers subtract the stored (possibly FP16-rounded) message
-                            Ln.v[i] = q + as_stored(mn.v[i], msg);
-                        }
-                        stm<V>(msg + bM + ((int64_t)(e) << a.lgfb), mn);
-                        stf<V>(L + bL + ((int64_t)(ld_index_again(a.ci + e)) << a.lgfb), Ln);
-                    }
-                }
-            } else {
-                for (int k = 0; k < d; ++k) {
-                    const int32_t e = beg + k;
-                    const VF<V> Lv = ldf_plain<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                    const VF<V> mo = ldm<V>(msg + bM + ((int64_t)(e) << a.lgfb));
-                    for (int i = 0; i < V; ++i) visit(k, Lv.v[i] - mo.v[i], i);
-                }
-                for (int k = 0; k < d; ++k) {
-                    const int32_t e = beg + k;
-                    float *Lp = L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb);
-                    const VF<V> Lv = ldf_plain<V>(Lp);
-                    MsgT *mp = msg + bM + ((int64_t)(e) << a.lgfb);
-                    const VF<V> mo = ldm<V>(mp);
-                    VF<V> mn, Ln;
+                for (int j = 0; j < CH; ++j) {
+                    const int k = k0 + j;
+                    if (k >= d) break;
                     for (int i = 0; i < V; ++i) {
-                        const float q = Lv.v[i] - mo.v[i];
-                        const float mag = magnitude(k, i);
-                        mn.v[i] = (((neg >> i) & 1u) ^ (q < 0.0f)) ? -mag : mag;
-                        Ln.v[i] = ((act >> i) & 1u) ? q + as_stored(mn.v[i], msg) : Lv.v[i];
+                        const float q = Lv[j].v[i] - mo[j].v[i];
+                        if (STASH) my[k * 32] = q;
+                        neg ^= (uint32_t)(q < 0.0f) << i;
+                        const float m = fabsf(q);
+                        if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = k; }
+                        else if (m < mn2[i]) mn2[i] = m;
                     }
-                    stm<V>(mp, mn);
-                    stf<V>(Lp, Ln);
                 }
+            }
+            // pass 2: new messages and posteriors L = q + m
+            for (int k = 0; k < d; ++k) {
+                const int32_t e = beg + k;
+                float *Lp = L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb);
+                MsgT *mp = msg + bM + ((int64_t)e << a.lgfb);
+                VF<V> q, Lold;
+                if (STASH) {
+                    q.v[0] = my[k * 32];
+                } else {
+                    Lold = ldf_plain<V>(Lp);
+                    const VF<V> mo = ldm<V>(mp);
+                    for (int i = 0; i < V; ++i) q.v[i] = Lold.v[i] - mo.v[i];
+                }
+                VF<V> mn, Ln;
+                for (int i = 0; i < V; ++i) {
+                    const float mag = fmaxf(((k == arg[i]) ? mn2[i] : mn1[i]) - a.beta, 0.0f);
+                    mn.v[i] = (((neg >> i) & 1u) ^ (q.v[i] < 0.0f)) ? -mag : mag;
+                    // later layers subtract the stored (possibly FP16-rounded) message;
+                    // a retired frame keeps its posterior
+                    Ln.v[i] = (STASH || ((act >> i) & 1u)) ? q.v[i] + as_stored(mn.v[i], msg) : Lold.v[i];
+                }
+                stm<V>(mp, mn);
+                stf<V>(Lp, Ln);
             }
         }
     }
@@ -121,9 +101,10 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 }
 
 // ---------------------------------------------------------- integer layered
-template <int V, int DCMAX>
-__global__ void __launch_bounds__(kCheckWarps * 32, 2)
+template <int V, bool CACHED>
+__global__ void __launch_bounds__(kCheckWarps * 32, 3)
 layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
+    extern __shared__ float qstash[];  // [kCheckWarps][kStash][32], holds ints
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
@@ -132,6 +113,8 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
     constexpr int CH = chunk_of<V>();
+    constexpr bool STASH = CACHED && V == 1;
+    int *my = reinterpret_cast<int *>(qstash) + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
@@ -140,86 +123,61 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
         const uint32_t act = active_bits<V>(a.active + f0);
         if (!act) continue;
         const int nact = __popc(act);
-        const int64_t k0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
+        const int64_t k0c = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
         for (int it = 0; it < kChecksPerWarp; ++it) {
-            const int64_t kk = k0 + it * slots + slot;
+            const int64_t kk = k0c + it * slots + slot;
             if (kk >= lsize) break;
             const int32_t c = __ldg(lchk + lbeg + kk);
             const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1), d = end - beg;
             uint32_t neg = (__ldg(a.sbits + (int64_t)c * a.W + (f0 >> 5)) >> (f0 & 31)) & vmask;
             units += (unsigned long long)d * nact;
-            int mn1[V], mn2[V], arg[V], qc[DCMAX > 0 ? DCMAX : 1][V];
+            int mn1[V], mn2[V], arg[V];
             for (int i = 0; i < V; ++i) { mn1[i] = 1 << 20; mn2[i] = 1 << 20; arg[i] = -1; }
             // q_full = sat16(L - m); the v->c message is q_full clipped to 6 bits
-            auto visit = [&](int k, int qf, int i) {
-                const int q = max(min(qf, kQMax), -kQMax);
-                neg ^= (uint32_t)(q < 0) << i;
-                const int m = q < 0 ? -q : q;
-                if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = k; }
-                else if (m < mn2[i]) mn2[i] = m;
-            };
-            auto message = [&](int k, int qf, int i) {
-                const int q = max(min(qf, kQMax), -kQMax);
-                const int mag = max(((k == arg[i]) ? mn2[i] : mn1[i]) - 1, 0);
-                return (((neg >> i) & 1u) ^ (q < 0)) ? -mag : mag;
-            };
-            if (DCMAX > 0) {
+            for (int k0 = 0; k0 < d; k0 += CH) {
+                VI<V> Lv[CH], mo[CH];
 #pragma unroll
-                for (int k0 = 0; k0 < (DCMAX > 0 ? DCMAX : 1); k0 += CH) {
-                    if (k0 < d) {
-                        VI<V> Lv[CH], mo[CH];
-#pragma unroll
-                        for (int j = 0; j < CH; ++j) {
-                            const int32_t e = beg + min(k0 + j, d - 1);
-                            Lv[j] = ldi16<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                            mo[j] = ldi8s<V>(msg + bM + ((int64_t)(e) << a.lgfb));
-                        }
-#pragma unroll
-                        for (int j = 0; j < CH; ++j) {
-                            if (k0 + j < d) {
-                                for (int i = 0; i < V; ++i) {
-                                    qc[k0 + j][i] = max(min(Lv[j].v[i] - mo[j].v[i], kPMax), -kPMax);
-                                    visit(k0 + j, qc[k0 + j][i], i);
-                                }
-                            }
-                        }
-                    }
+                for (int j = 0; j < CH; ++j) {
+                    const int32_t e = beg + min(k0 + j, d - 1);
+                    Lv[j] = ldi16<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
+                    mo[j] = ldi8s<V>(msg + bM + ((int64_t)e << a.lgfb));
                 }
 #pragma unroll
-                for (int k = 0; k < (DCMAX > 0 ? DCMAX : 1); ++k) {
-                    if (k < d) {
-                        const int32_t e = beg + k;
-                        VI<V> mn, Ln;
-                        for (int i = 0; i < V; ++i) {
-                            mn.v[i] = message(k, qc[k][i], i);
-                            Ln.v[i] = max(min(qc[k][i] + mn.v[i], kPMax), -kPMax);
-                        }
-                        sti8<V>(msg + bM + ((int64_t)(e) << a.lgfb), mn);
-                        sti16<V>(L + bL + ((int64_t)(ld_index_again(a.ci + e)) << a.lgfb), Ln);
-                    }
-                }
-            } else {
-                for (int k = 0; k < d; ++k) {
-                    const int32_t e = beg + k;
-                    const VI<V> Lv = ldi16<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                    const VI<V> mo = ldi8s<V>(msg + bM + ((int64_t)(e) << a.lgfb));
-                    for (int i = 0; i < V; ++i) visit(k, max(min(Lv.v[i] - mo.v[i], kPMax), -kPMax), i);
-                }
-                for (int k = 0; k < d; ++k) {
-                    const int32_t e = beg + k;
-                    int16_t *Lp = L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb);
-                    const VI<V> Lv = ldi16<V>(Lp);
-                    int8_t *mp = msg + bM + ((int64_t)(e) << a.lgfb);
-                    const VI<V> mo = ldi8<V>(mp);
-                    VI<V> mn, Ln;
+                for (int j = 0; j < CH; ++j) {
+                    const int k = k0 + j;
+                    if (k >= d) break;
                     for (int i = 0; i < V; ++i) {
-                        const int qf = max(min(Lv.v[i] - mo.v[i], kPMax), -kPMax);
-                        mn.v[i] = message(k, qf, i);
-                        Ln.v[i] = ((act >> i) & 1u) ? max(min(qf + mn.v[i], kPMax), -kPMax) : Lv.v[i];
+                        const int qf = max(min(Lv[j].v[i] - mo[j].v[i], kPMax), -kPMax);
+                        if (STASH) my[k * 32] = qf;
+                        const int q = max(min(qf, kQMax), -kQMax);
+                        neg ^= (uint32_t)(q < 0) << i;
+                        const int m = q < 0 ? -q : q;
+                        if (m < mn1[i]) { mn2[i] = mn1[i]; mn1[i] = m; arg[i] = k; }
+                        else if (m < mn2[i]) mn2[i] = m;
                     }
-                    sti8<V>(mp, mn);
-                    sti16<V>(Lp, Ln);
                 }
+            }
+            for (int k = 0; k < d; ++k) {
+                const int32_t e = beg + k;
+                int16_t *Lp = L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb);
+                int8_t *mp = msg + bM + ((int64_t)e << a.lgfb);
+                VI<V> qf, Lold;
+                if (STASH) {
+                    qf.v[0] = my[k * 32];
+                } else {
+                    Lold = ldi16<V>(Lp);
+                    const VI<V> mo = ldi8s<V>(mp);
+                    for (int i = 0; i < V; ++i) qf.v[i] = max(min(Lold.v[i] - mo.v[i], kPMax), -kPMax);
+                }
+                VI<V> mn, Ln;
+                for (int i = 0; i < V; ++i) {
+                    const int q = max(min(qf.v[i], kQMax), -kQMax);
+                    const int mag = max(((k == arg[i]) ? mn2[i] : mn1[i]) - 1, 0);
+                    mn.v[i] = (((neg >> i) & 1u) ^ (q < 0)) ? -mag : mag;
+                    Ln.v[i] = (STASH || ((act >> i) & 1u)) ? max(min(qf.v[i] + mn.v[i], kPMax), -kPMax) : Lold.v[i];
+                }
+                sti8<V>(mp, mn);
+                sti16<V>(Lp, Ln);
             }
         }
     }
@@ -241,23 +199,20 @@ __global__ void retire(int64_t Fp, int64_t W, int32_t t, uint8_t *active, int32_
 
 static void launch_layer(DecArgs a, const CodeDev &d, int prec, int32_t lb, int32_t ls, cudaStream_t st) {
     const int V = lanes_v(d, QKDREC_OMS_LAYERED, prec);
-    const int dcc = dc_class(d);
     const Geom g = check_geom(a.Fp, V, ls);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
+    const size_t stash = (size_t)kCheckWarps * kStash * 32 * sizeof(float);
     const int32_t *lc = d.layer_chk;
     if (prec == kI8) {
-        if (dcc == 8) layer_oms_i<1, 8><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
-        else if (dcc == 32) layer_oms_i<1, 32><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
-        else layer_oms_i<4, 0><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        if (V == 1) layer_oms_i<1, true><<<g.grid, B, stash, st>>>(a, lc, lb, ls);
+        else layer_oms_i<4, false><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
     } else if (prec == kF16) {
-        if (dcc == 8) layer_oms_f<__half, 1, 8><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
-        else if (dcc == 32) layer_oms_f<__half, 1, 32><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
-        else layer_oms_f<__half, 4, 0><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        if (V == 1) layer_oms_f<__half, 1, true><<<g.grid, B, stash, st>>>(a, lc, lb, ls);
+        else layer_oms_f<__half, 4, false><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
     } else {
-        if (dcc == 8) layer_oms_f<float, 1, 8><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
-        else if (dcc == 32) layer_oms_f<float, 1, 32><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
-        else layer_oms_f<float, 4, 0><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
+        if (V == 1) layer_oms_f<float, 1, true><<<g.grid, B, stash, st>>>(a, lc, lb, ls);
+        else layer_oms_f<float, 4, false><<<g.grid, B, 0, st>>>(a, lc, lb, ls);
     }
 }
 
