@@ -158,14 +158,14 @@ template <> __device__ __forceinline__ uint32_t active_bits<4>(const uint8_t *p)
 }
 
 // ------------------------------------------------------------------- phi
-// phi(x) = -ln tanh(x/2) = ln((1 + u)/(1 - u)), u = e^-x, on [kAMin, kAMax]; it is
-// its own inverse.  Written from these identities and two Taylor series,
-// evaluated with the MUFU ex2/rcp/lg2 approximations (about 1e-6 relative):
-//   x >= 2       : u <= 0.135 and phi = 2 atanh(u) = 2u (1 + u^2/3 + u^4/5 + u^6/7) + O(u^9);
-//   0.5 <= x < 2 : phi = log2((1 + u)/(1 - u)) ln 2 with 1 - u >= 0.39 (no cancellation);
-//   x < 0.5      : 1 - u = 1 - e^-x from its Taylor series
-//                  x (1 - x/2 (1 - x/3 (1 - x/4 (1 - x/5 (1 - x/6 (1 - x/7 (1 - x/8))))))),
-//                  1 + u = 2 - (1 - u).
+// phi(x) = -ln tanh(x/2) = ln coth(x/2) = ln((1 + u)/(1 - u)), u = e^-x, on
+// [kAMin, kAMax]; it is its own inverse.  Written from these identities and
+// series, evaluated with the MUFU ex2/rcp/lg2 approximations (about 2e-6
+// relative), one lg2 shared by the two lower ranges:
+//   x >= 2          : u <= 0.135, phi = 2 atanh(u) = 2u (1 + u^2/3 + u^4/5 + u^6/7) + O(u^9);
+//   0.03 <= x < 2   : phi = log2((1 + u)/(1 - u)) ln 2, 1 - u >= 0.0296;
+//   x < 0.03        : coth(y) y = 1 + y^2/3 - y^4/45 + ..., so with y = x/2
+//                     phi = ln(2/x) + x^2/12 - 7 x^4/1440 + O(x^6).
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -185,18 +185,13 @@ __device__ __forceinline__ float phi_fast(float x) {
     const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
     const float u = ex2_approx(-x * kLog2e);
     const float u2 = u * u;
-    const float series = 2.0f * u * (1.0f + u2 * (1.0f / 3.0f + u2 * (0.2f + u2 * (1.0f / 7.0f))));
-    float t = 1.0f - x * 0.125f;
-    t = 1.0f - x * (1.0f / 7.0f) * t;
-    t = 1.0f - x * (1.0f / 6.0f) * t;
-    t = 1.0f - x * 0.2f * t;
-    t = 1.0f - x * 0.25f * t;
-    t = 1.0f - x * (1.0f / 3.0f) * t;
-    t = 1.0f - x * 0.5f * t;
-    const float den = x < 0.5f ? x * t : 1.0f - u;
-    const float num = 2.0f - den;
-    const float r = lg2_approx(num * rcp_approx(den)) * kLn2;
-    return x >= 2.0f ? series : r;
+    const float big = 2.0f * u * (1.0f + u2 * (1.0f / 3.0f + u2 * (0.2f + u2 * (1.0f / 7.0f))));
+    const bool small = x < 0.03f;
+    const float arg = small ? 0.5f * x : (1.0f + u) * rcp_approx(1.0f - u);
+    const float lg = lg2_approx(arg) * kLn2;
+    const float x2 = x * x;
+    const float low = small ? x2 * (1.0f / 12.0f - x2 * (7.0f / 1440.0f)) - lg : lg;
+    return x >= 2.0f ? big : low;
 }
 __device__ __forceinline__ float phi_clamped(float x) { return phi_fast(fminf(fmaxf(x, kAMin), kAMax)); }
 
@@ -315,12 +310,15 @@ check_flood_f(DecArgs a) {
                         const int k = k0 + j;
                         if (k >= d) break;
                         for (int i = 0; i < V; ++i) {
-                            par ^= (uint32_t)(Lv[j].v[i] < 0.0f) << i;
+                            par ^= (uint32_t)(Lv[j].v[i] < 0.0f) << i;   // -0.0 counts as 0
                             const float q = Lv[j].v[i] - mo[j].v[i];
-                            if (CACHED) sg[i] |= (uint32_t)(q < 0.0f) << k;
+                            if (CACHED && !SP_STASH) sg[i] |= (uint32_t)(q < 0.0f) << k;
                             if (ALGO == kSP) {
                                 const float f = phi_clamped(fabsf(q));
-                                if (SP_STASH) my[k * 32] = f;
+                                if (SP_STASH) {
+                                    my[k * 32] = q < 0.0f ? -f : f;   // sign of q travels with phi
+                                    sg[i] ^= (uint32_t)(q < 0.0f);   // parity of the signs
+                                }
                                 if (f > acc1[i]) { acc0[i] += acc1[i]; acc1[i] = f; arg[i] = k; }
                                 else acc0[i] += f;
                             } else {
@@ -343,13 +341,21 @@ check_flood_f(DecArgs a) {
                     }
                     return sneg_k ? -mag : mag;
                 };
-                if (CACHED && (ALGO != kSP || SP_STASH)) {
+                if (SP_STASH) {
+                    const uint32_t neg = (s ^ sg[0]) & 1u;   // syndrome xor all signs of q
+                    for (int k = 0; k < d; ++k) {
+                        const float fs = my[k * 32];
+                        VF<V> mn;
+                        mn.v[0] = emit(k, fabsf(fs), neg ^ (__float_as_uint(fs) >> 31), 0);
+                        stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
+                    }
+                } else if (CACHED && ALGO != kSP) {
                     uint32_t neg = s;       // syndrome xor all signs of q
                     for (int i = 0; i < V; ++i) neg ^= (uint32_t)(__popc(sg[i]) & 1) << i;
                     for (int k = 0; k < d; ++k) {
                         VF<V> mn;
                         for (int i = 0; i < V; ++i)
-                            mn.v[i] = emit(k, SP_STASH ? my[k * 32] : 0.0f, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
+                            mn.v[i] = emit(k, 0.0f, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
                         stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
                     }
                 } else {
