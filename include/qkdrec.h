@@ -200,6 +200,35 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
                                   int32_t *iters_out, uint8_t *conv_out, float *post_out,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * No-allocation variant of qkdrec_decode_batch.  The paper has no counterpart:
+ * this serves callers that cannot allocate device memory when they decode --
+ * for example code running under a memory manager that owns all of the
+ * device's memory, or a latency-critical reconciliation loop in which an
+ * allocation (which may synchronise the device) is not allowed.
+ * It runs the same decoder on a fixed workspace of
+ * qkdrec_decode_static_capacity() bytes (32 MiB) compiled into the library as
+ * a device array; every device that loads the library holds that array until
+ * the process exits.  The caller still passes the inputs and outputs, exactly
+ * as for qkdrec_decode_batch.
+ *  - A request whose workspace (qkdrec_decode_workspace_size) is larger than
+ *    the array fails with QKDREC_ERR_ARG before anything is enqueued; split
+ *    the frames over several calls.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls share the one array.  Calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race and corrupt each other's
+ *    results: serialise them.  Each call initialises every part of the array
+ *    it reads, so what a previous call left there does not matter.
+ *  - No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+size_t qkdrec_decode_static_capacity(void);
+qkdrec_status qkdrec_decode_batch_static(qkdrec_code_t code, const float *llr, const uint8_t *synd,
+                                         int32_t F, const qkdrec_decode_opts *opts, uint8_t *bits_out,
+                                         int32_t *iters_out, uint8_t *conv_out, float *post_out,
+                                         void *stream);
+
 /* ------------------------------------------------------------- measurement */
 
 /* Per-kernel-class totals collected between qkdrec_profile_begin/end. */

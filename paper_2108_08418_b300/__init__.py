@@ -33,6 +33,7 @@ EXPORTED = [
     "qkdrec_decode_opts_default", "qkdrec_decode_workspace_size", "qkdrec_decode_batch",
     "qkdrec_slice_capacity", "qkdrec_last_error", "qkdrec_version",
     "qkdrec_profile_begin", "qkdrec_profile_end",
+    "qkdrec_decode_static_capacity", "qkdrec_decode_batch_static",
 ]
 SELFTEST = ["qkdrec_selftest_phi"]
 
@@ -79,6 +80,8 @@ def lib():
         "qkdrec_decode_workspace_size": (U, [P, I32, P, P]),
         "qkdrec_decode_batch": (U, [P, P, P, I32, P, P, P, P, P, P, ctypes.c_size_t, P]),
         "qkdrec_slice_capacity": (U, [D, I32, I32, D, D, U, D, P]),
+        "qkdrec_decode_static_capacity": (ctypes.c_size_t, []),
+        "qkdrec_decode_batch_static": (U, [P, P, P, I32, P, P, P, P, P, P]),
         "qkdrec_profile_begin": (U, []),
         "qkdrec_selftest_phi": (U, [P, I64, P, P]),
         "qkdrec_profile_end": (U, [P, I32, P]),
@@ -272,6 +275,40 @@ def qkdrec_decode_batch(code: Code, llr, synd, opts: DecodeOpts | None = None, w
                                      ctypes.c_void_p(out["converged"].data_ptr()),
                                      ctypes.c_void_p(post.data_ptr()) if post is not None else None,
                                      ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(llr)))
+    return out
+
+
+def qkdrec_decode_static_capacity() -> int:
+    """Bytes of the decoder workspace compiled into the library."""
+    return lib().qkdrec_decode_static_capacity()
+
+
+def qkdrec_decode_batch_static(code: Code, llr, synd, opts: DecodeOpts | None = None, want_post: bool = False,
+                               out=None):
+    """qkdrec_decode_batch on the library's built-in device workspace (no device
+    allocation by the library; outputs are allocated here unless given)."""
+    torch = _torch()
+    opts = opts or DecodeOpts()
+    llr2 = llr.reshape(-1, code.n)
+    F = llr2.shape[0]
+    if synd.numel() != F * code.M:
+        raise ValueError("synd must be uint8 [F][M]")
+    lp = _dev(llr2, torch.float32, "llr")
+    sp = _dev(synd, torch.uint8, "synd")
+    dev = llr.device
+    if out is None:
+        out = dict(bits=torch.empty((F, code.n), dtype=torch.uint8, device=dev),
+                   iters=torch.empty(F, dtype=torch.int32, device=dev),
+                   converged=torch.empty(F, dtype=torch.uint8, device=dev),
+                   post=torch.empty((F, code.n), dtype=torch.float32, device=dev) if want_post else None)
+    o = opts.c()
+    post = out.get("post")
+    _check(lib().qkdrec_decode_batch_static(code.handle, lp, sp, F, ctypes.byref(o),
+                                            ctypes.c_void_p(out["bits"].data_ptr()),
+                                            ctypes.c_void_p(out["iters"].data_ptr()),
+                                            ctypes.c_void_p(out["converged"].data_ptr()),
+                                            ctypes.c_void_p(post.data_ptr()) if post is not None else None,
+                                            _stream(llr)))
     return out
 
 
