@@ -43,6 +43,8 @@ constexpr int kCheckWarps = 8;   // warps per check-kernel block
 constexpr int kChecksPerWarp = 4;
 // edge loads issued together in the first pass of a check (per lane: V frames each)
 template <int V> __host__ __device__ constexpr int chunk_of() { return V == 1 ? 8 : 4; }
+// frame block of the layout a kernel with V frames per lane runs on: 32 lanes' worth
+template <int V> __host__ __device__ constexpr int lgfb_of() { return V == 1 ? 5 : 7; }
 constexpr int32_t kMaxFrames = 65535 * 32;  // syndrome packing uses one grid row per 32 frames
 
 // ---------------------------------------------------------------- vector I/O
@@ -266,14 +268,19 @@ check_flood_f(DecArgs a) {
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
     constexpr int CH = chunk_of<V>();
+    constexpr int LG = lgfb_of<V>();
     constexpr bool SP_STASH = ALGO == kSP && CACHED && V == 1;
     float *my = stash + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         const bool fv_ok = fv < nvec;
-        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
+        const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
         const uint32_t act = fv_ok ? active_bits<V>(a.active + f0) : 0u;
+        // a warp on one check (fvw = 32) whose lanes all decode reads the check's
+        // column indices once, one per lane, and broadcasts them by shuffles;
+        // decided here, where all 32 lanes are converged
+        const bool whole_warp = CACHED && fvw == 32 && __all_sync(0xffffffffu, act != 0u);
         uint32_t unsat_bits = 0;
         if (act) {
             const int nact = __popc(act);
@@ -294,15 +301,18 @@ check_flood_f(DecArgs a) {
                     arg[i] = -1;
                 }
                 units += (unsigned long long)d * nact;
+                const int32_t my_col = whole_warp && lane < d ? __ldg(a.ci + beg + lane) : 0;
                 // loads of CH edges are issued together (indices past the last
                 // edge are clamped to it), so a warp keeps CH requests in flight
                 for (int k0 = 0; k0 < d; k0 += CH) {
                     VF<V> Lv[CH], mo[CH];
 #pragma unroll
                     for (int j = 0; j < CH; ++j) {
-                        const int32_t e = beg + min(k0 + j, d - 1);
-                        Lv[j] = ldf<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
-                        if (a.do_msgs) mo[j] = ldm<V>(msg + bM + ((int64_t)e << a.lgfb));
+                        const int kk = min(k0 + j, d - 1);
+                        const int32_t e = beg + kk;
+                        const int32_t col = whole_warp ? __shfl_sync(0xffffffffu, my_col, kk) : __ldg(a.ci + e);
+                        Lv[j] = ldf<V>(L + bL + ((uint32_t)col << LG));
+                        if (a.do_msgs) mo[j] = ldm<V>(msg + bM + ((uint32_t)(e) << LG));
                         else for (int i = 0; i < V; ++i) mo[j].v[i] = 0.0f;
                     }
 #pragma unroll
@@ -347,7 +357,7 @@ check_flood_f(DecArgs a) {
                         const float fs = my[k * 32];
                         VF<V> mn;
                         mn.v[0] = emit(k, fabsf(fs), neg ^ (__float_as_uint(fs) >> 31), 0);
-                        stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
+                        stm<V>(msg + bM + ((uint32_t)(beg + k) << LG), mn);
                     }
                 } else if (CACHED && ALGO != kSP) {
                     uint32_t neg = s;       // syndrome xor all signs of q
@@ -356,21 +366,21 @@ check_flood_f(DecArgs a) {
                         VF<V> mn;
                         for (int i = 0; i < V; ++i)
                             mn.v[i] = emit(k, 0.0f, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
-                        stm<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
+                        stm<V>(msg + bM + ((uint32_t)(beg + k) << LG), mn);
                     }
                 } else {
                     // signs and phi values again from memory
                     uint32_t negall = s;
                     for (int k = 0; k < d; ++k) {
                         const int32_t e = beg + k;
-                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
-                        const VF<V> mo = ldm<V>(msg + bM + ((int64_t)e << a.lgfb));
+                        const VF<V> Lv = ldf<V>(L + bL + ((uint32_t)__ldg(a.ci + e) << LG));
+                        const VF<V> mo = ldm<V>(msg + bM + ((uint32_t)(e) << LG));
                         for (int i = 0; i < V; ++i) negall ^= (uint32_t)(Lv.v[i] - mo.v[i] < 0.0f) << i;
                     }
                     for (int k = 0; k < d; ++k) {
                         const int32_t e = beg + k;
-                        const VF<V> Lv = ldf<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
-                        MsgT *mp = msg + bM + ((int64_t)e << a.lgfb);
+                        const VF<V> Lv = ldf<V>(L + bL + ((uint32_t)__ldg(a.ci + e) << LG));
+                        MsgT *mp = msg + bM + ((uint32_t)(e) << LG);
                         const VF<V> mo = ldm<V>(mp);
                         VF<V> mn;
                         for (int i = 0; i < V; ++i) {
@@ -402,11 +412,12 @@ check_flood_i(DecArgs a) {
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
     constexpr int CH = chunk_of<V>();
+    constexpr int LG = lgfb_of<V>();
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         const bool fv_ok = fv < nvec;
-        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
+        const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
         const uint32_t act = fv_ok ? active_bits<V>(a.active + f0) : 0u;
         uint32_t unsat_bits = 0;
         if (act) {
@@ -433,8 +444,8 @@ check_flood_i(DecArgs a) {
                 };
                 auto load = [&](int k, VI<V> &Lv, VI<V> &mo) {
                     const int32_t e = beg + k;
-                    Lv = ldi16<V>(L + bL + ((int64_t)(__ldg(a.ci + e)) << a.lgfb));
-                    if (a.do_msgs) mo = ldi8s<V>(msg + bM + ((int64_t)(e) << a.lgfb));
+                    Lv = ldi16<V>(L + bL + ((uint32_t)(__ldg(a.ci + e)) << LG));
+                    if (a.do_msgs) mo = ldi8s<V>(msg + bM + ((uint32_t)(e) << LG));
                     else for (int i = 0; i < V; ++i) mo.v[i] = 0;
                 };
                 for (int k0 = 0; k0 < d; k0 += CH) {
@@ -458,7 +469,7 @@ check_flood_i(DecArgs a) {
                     for (int k = 0; k < d; ++k) {
                         VI<V> mn;
                         for (int i = 0; i < V; ++i) mn.v[i] = emit(k, ((neg >> i) & 1u) ^ ((sg[i] >> k) & 1u), i);
-                        sti8<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
+                        sti8<V>(msg + bM + ((uint32_t)(beg + k) << LG), mn);
                     }
                 } else {
                     uint32_t negall = s;
@@ -475,7 +486,7 @@ check_flood_i(DecArgs a) {
                             const int q = max(min(Lv.v[i] - mo.v[i], kQMax), -kQMax);
                             mn.v[i] = emit(k, ((negall >> i) & 1u) ^ (q < 0), i);
                         }
-                        sti8<V>(msg + bM + ((int64_t)(beg + k) << a.lgfb), mn);
+                        sti8<V>(msg + bM + ((uint32_t)(beg + k) << LG), mn);
                     }
                 }
             }
@@ -684,7 +695,7 @@ static int lanes_v(const CodeDev &d, int algo, int prec) {
 
 static Layout make_layout(const CodeDev &d, int32_t F, int algo, int prec) {
     Layout l;
-    l.lgfb = lanes_v(d, algo, prec) == 1 ? 5 : 7;
+    l.lgfb = lanes_v(d, algo, prec) == 1 ? lgfb_of<1>() : lgfb_of<4>();
     l.Fp = align_up((size_t)(F > 0 ? F : 1), (size_t)1 << l.lgfb);
     l.FV = l.Fp / 4;
     l.W = ceil_div(l.Fp, 32);
@@ -823,30 +834,36 @@ static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const 
 // Launch one flooding check kernel (or its parity-only form).  SP keeps one
 // frame per lane so that the phi values of a check fit in registers; min-sum
 // only keeps sign bits and runs four frames per lane.
+// The kernels' frame block is fixed at compile time by V (lgfb_of), so V follows
+// the layout of the decode: one frame per lane on 32-frame blocks (sum-product
+// and layered schedules), four on 128-frame blocks (flooding min-sum).
 static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaStream_t st) {
     const bool cached = dc_class(d) > 0;
-    const int V = (prec != kI8 && algo == QKDREC_SP_FLOOD && cached) ? 1 : 4;
+    const int V = a.lgfb == lgfb_of<1>() ? 1 : 4;
     const Geom g = check_geom(a.Fp, V, d.M);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
     const size_t stash = (size_t)kCheckWarps * kStash * 32 * sizeof(float);
     if (prec == kI8) {
-        if (cached) check_flood_i<4, 32><<<g.grid, B, 0, st>>>(a);
+        if (V == 1) check_flood_i<1, 32><<<g.grid, B, 0, st>>>(a);
+        else if (cached) check_flood_i<4, 32><<<g.grid, B, 0, st>>>(a);
         else check_flood_i<4, 0><<<g.grid, B, 0, st>>>(a);
     } else if (algo == QKDREC_SP_FLOOD) {
         if (prec == kF32) {
-            if (cached) check_flood_f<kSP, float, 1, true><<<g.grid, B, stash, st>>>(a);
+            if (V == 1) check_flood_f<kSP, float, 1, true><<<g.grid, B, stash, st>>>(a);
             else check_flood_f<kSP, float, 4, false><<<g.grid, B, 0, st>>>(a);
         } else {
-            if (cached) check_flood_f<kSP, __half, 1, true><<<g.grid, B, stash, st>>>(a);
+            if (V == 1) check_flood_f<kSP, __half, 1, true><<<g.grid, B, stash, st>>>(a);
             else check_flood_f<kSP, __half, 4, false><<<g.grid, B, 0, st>>>(a);
         }
     } else {
         if (prec == kF32) {
-            if (cached) check_flood_f<kOMS, float, 4, true><<<g.grid, B, 0, st>>>(a);
+            if (V == 1) check_flood_f<kOMS, float, 1, true><<<g.grid, B, 0, st>>>(a);
+            else if (cached) check_flood_f<kOMS, float, 4, true><<<g.grid, B, 0, st>>>(a);
             else check_flood_f<kOMS, float, 4, false><<<g.grid, B, 0, st>>>(a);
         } else {
-            if (cached) check_flood_f<kOMS, __half, 4, true><<<g.grid, B, 0, st>>>(a);
+            if (V == 1) check_flood_f<kOMS, __half, 1, true><<<g.grid, B, 0, st>>>(a);
+            else if (cached) check_flood_f<kOMS, __half, 4, true><<<g.grid, B, 0, st>>>(a);
             else check_flood_f<kOMS, __half, 4, false><<<g.grid, B, 0, st>>>(a);
         }
     }

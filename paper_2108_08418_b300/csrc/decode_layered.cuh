@@ -26,14 +26,18 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
     constexpr int CH = chunk_of<V>();
+    constexpr int LG = lgfb_of<V>();
     constexpr bool STASH = CACHED && V == 1;
     float *my = qstash + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         if (fv >= nvec) continue;
-        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
+        const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
         const uint32_t act = active_bits<V>(a.active + f0);
+        // a warp on one check (fvw = 32; then no lane left the loop above) whose
+        // lanes all decode reads the column indices once and broadcasts them
+        const bool whole_warp = CACHED && fvw == 32 && __all_sync(0xffffffffu, act != 0u);
         if (!act) continue;
         const int nact = __popc(act);
         const int64_t k0c = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
@@ -47,14 +51,17 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             float mn1[V], mn2[V];
             int32_t arg[V];
             for (int i = 0; i < V; ++i) { mn1[i] = INFINITY; mn2[i] = INFINITY; arg[i] = -1; }
+            const int32_t my_col = whole_warp && lane < d ? __ldg(a.ci + beg + lane) : 0;
             // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
             for (int k0 = 0; k0 < d; k0 += CH) {
                 VF<V> Lv[CH], mo[CH];
 #pragma unroll
                 for (int j = 0; j < CH; ++j) {
-                    const int32_t e = beg + min(k0 + j, d - 1);
-                    Lv[j] = ldf_plain<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
-                    mo[j] = ldm<V>(msg + bM + ((int64_t)e << a.lgfb));
+                    const int kk = min(k0 + j, d - 1);
+                    const int32_t e = beg + kk;
+                    const int32_t col = whole_warp ? __shfl_sync(0xffffffffu, my_col, kk) : __ldg(a.ci + e);
+                    Lv[j] = ldf_plain<V>(L + bL + ((uint32_t)col << LG));
+                    mo[j] = ldm<V>(msg + bM + ((uint32_t)(e) << LG));
                 }
 #pragma unroll
                 for (int j = 0; j < CH; ++j) {
@@ -73,8 +80,9 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             // pass 2: new messages and posteriors L = q + m
             for (int k = 0; k < d; ++k) {
                 const int32_t e = beg + k;
-                float *Lp = L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb);
-                MsgT *mp = msg + bM + ((int64_t)e << a.lgfb);
+                const int32_t col = whole_warp ? __shfl_sync(0xffffffffu, my_col, k) : __ldg(a.ci + e);
+                float *Lp = L + bL + ((uint32_t)col << LG);
+                MsgT *mp = msg + bM + ((uint32_t)(e) << LG);
                 VF<V> q, Lold;
                 if (STASH) {
                     q.v[0] = my[k * 32];
@@ -113,13 +121,14 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
     constexpr int CH = chunk_of<V>();
+    constexpr int LG = lgfb_of<V>();
     constexpr bool STASH = CACHED && V == 1;
     int *my = reinterpret_cast<int *>(qstash) + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
     for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         if (fv >= nvec) continue;
-        const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);  // item 0 of this lane
+        const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
         const uint32_t act = active_bits<V>(a.active + f0);
         if (!act) continue;
         const int nact = __popc(act);
@@ -139,8 +148,8 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 #pragma unroll
                 for (int j = 0; j < CH; ++j) {
                     const int32_t e = beg + min(k0 + j, d - 1);
-                    Lv[j] = ldi16<V>(L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb));
-                    mo[j] = ldi8s<V>(msg + bM + ((int64_t)e << a.lgfb));
+                    Lv[j] = ldi16<V>(L + bL + ((uint32_t)__ldg(a.ci + e) << LG));
+                    mo[j] = ldi8s<V>(msg + bM + ((uint32_t)(e) << LG));
                 }
 #pragma unroll
                 for (int j = 0; j < CH; ++j) {
@@ -159,8 +168,8 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             }
             for (int k = 0; k < d; ++k) {
                 const int32_t e = beg + k;
-                int16_t *Lp = L + bL + ((int64_t)__ldg(a.ci + e) << a.lgfb);
-                int8_t *mp = msg + bM + ((int64_t)e << a.lgfb);
+                int16_t *Lp = L + bL + ((uint32_t)__ldg(a.ci + e) << LG);
+                int8_t *mp = msg + bM + ((uint32_t)(e) << LG);
                 VI<V> qf, Lold;
                 if (STASH) {
                     qf.v[0] = my[k * 32];
@@ -198,7 +207,7 @@ __global__ void retire(int64_t Fp, int64_t W, int32_t t, uint8_t *active, int32_
 }
 
 static void launch_layer(DecArgs a, const CodeDev &d, int prec, int32_t lb, int32_t ls, cudaStream_t st) {
-    const int V = lanes_v(d, QKDREC_OMS_LAYERED, prec);
+    const int V = a.lgfb == lgfb_of<1>() ? 1 : 4;
     const Geom g = check_geom(a.Fp, V, ls);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
