@@ -277,10 +277,6 @@ check_flood_f(DecArgs a) {
         const bool fv_ok = fv < nvec;
         const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
         const uint32_t act = fv_ok ? active_bits<V>(a.active + f0) : 0u;
-        // a warp on one check (fvw = 32) whose lanes all decode reads the check's
-        // column indices once, one per lane, and broadcasts them by shuffles;
-        // decided here, where all 32 lanes are converged
-        const bool whole_warp = CACHED && fvw == 32 && __all_sync(0xffffffffu, act != 0u);
         uint32_t unsat_bits = 0;
         if (act) {
             const int nact = __popc(act);
@@ -301,7 +297,6 @@ check_flood_f(DecArgs a) {
                     arg[i] = -1;
                 }
                 units += (unsigned long long)d * nact;
-                const int32_t my_col = whole_warp && lane < d ? __ldg(a.ci + beg + lane) : 0;
                 // loads of CH edges are issued together (indices past the last
                 // edge are clamped to it), so a warp keeps CH requests in flight
                 for (int k0 = 0; k0 < d; k0 += CH) {
@@ -310,7 +305,7 @@ check_flood_f(DecArgs a) {
                     for (int j = 0; j < CH; ++j) {
                         const int kk = min(k0 + j, d - 1);
                         const int32_t e = beg + kk;
-                        const int32_t col = whole_warp ? __shfl_sync(0xffffffffu, my_col, kk) : __ldg(a.ci + e);
+                        const int32_t col = __ldg(a.ci + e);
                         Lv[j] = ldf<V>(L + bL + ((uint32_t)col << LG));
                         if (a.do_msgs) mo[j] = ldm<V>(msg + bM + ((uint32_t)(e) << LG));
                         else for (int i = 0; i < V; ++i) mo[j].v[i] = 0.0f;

@@ -35,9 +35,6 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
         if (fv >= nvec) continue;
         const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
         const uint32_t act = active_bits<V>(a.active + f0);
-        // a warp on one check (fvw = 32; then no lane left the loop above) whose
-        // lanes all decode reads the column indices once and broadcasts them
-        const bool whole_warp = CACHED && fvw == 32 && __all_sync(0xffffffffu, act != 0u);
         if (!act) continue;
         const int nact = __popc(act);
         const int64_t k0c = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
@@ -51,7 +48,6 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             float mn1[V], mn2[V];
             int32_t arg[V];
             for (int i = 0; i < V; ++i) { mn1[i] = INFINITY; mn2[i] = INFINITY; arg[i] = -1; }
-            const int32_t my_col = whole_warp && lane < d ? __ldg(a.ci + beg + lane) : 0;
             // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
             for (int k0 = 0; k0 < d; k0 += CH) {
                 VF<V> Lv[CH], mo[CH];
@@ -59,7 +55,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
                 for (int j = 0; j < CH; ++j) {
                     const int kk = min(k0 + j, d - 1);
                     const int32_t e = beg + kk;
-                    const int32_t col = whole_warp ? __shfl_sync(0xffffffffu, my_col, kk) : __ldg(a.ci + e);
+                    const int32_t col = __ldg(a.ci + e);
                     Lv[j] = ldf_plain<V>(L + bL + ((uint32_t)col << LG));
                     mo[j] = ldm<V>(msg + bM + ((uint32_t)(e) << LG));
                 }
@@ -80,7 +76,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
             // pass 2: new messages and posteriors L = q + m
             for (int k = 0; k < d; ++k) {
                 const int32_t e = beg + k;
-                const int32_t col = whole_warp ? __shfl_sync(0xffffffffu, my_col, k) : __ldg(a.ci + e);
+                const int32_t col = __ldg(a.ci + e);
                 float *Lp = L + bL + ((uint32_t)col << LG);
                 MsgT *mp = msg + bM + ((uint32_t)(e) << LG);
                 VF<V> q, Lold;
