@@ -68,6 +68,8 @@ def _lib():
         lib.oracle_oms_flood.argtypes = [I, I, P, P, P, P, I, I, D, I, P, P, P, P]
         lib.oracle_oms_layered.argtypes = [I, I, P, P, I, P, P, P, P, I, I, D, I, P, P, P, P]
         lib.oracle_ioms.argtypes = [I, I, I, P, P, I, P, P, P, P, I, I, D, I, P, P, P, P]
+        lib.oracle_woms.argtypes = [I, I, P, P, P, P, P, I, I, P, P, P, P, P, P]
+        lib.oracle_woms.restype = I
         for f in (lib.oracle_sp_flood, lib.oracle_oms_flood, lib.oracle_oms_layered, lib.oracle_ioms):
             f.restype = I
         _LIB = lib
@@ -379,3 +381,33 @@ def decode(row_ptr, col_idx, llr, synd, algo: str = "sp_flood", max_iter: int = 
     if rc != 0:
         raise MemoryError("oracle decoder allocation")
     return dict(bits=bits, iters=iters, converged=conv, post=post)
+
+
+# ------------------------------------------------ weighted min-sum and gradient (a7)
+def woms(row_ptr, col_idx, llr, synd, target, alpha, beta, want_post: bool = False):
+    """Unrolled weighted offset min-sum (flooding, T = len(alpha) iterations) and the
+    reverse-mode gradient of the mean binary cross-entropy loss -- see bp.c.
+
+    alpha, beta: [T][2] (degree class 0 = the code's smallest check degree).
+    Returns dict(loss float, galpha [T][2], gbeta [T][2], post [F][n] or None).
+    """
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    llr = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float64)
+    synd = np.ascontiguousarray(np.atleast_2d(synd), dtype=np.uint8)
+    tgt = np.ascontiguousarray(np.atleast_2d(target), dtype=np.uint8)
+    a = np.ascontiguousarray(alpha, dtype=np.float64).reshape(-1, 2)
+    b = np.ascontiguousarray(beta, dtype=np.float64).reshape(-1, 2)
+    T = a.shape[0]
+    F, n = llr.shape
+    M = rp.shape[0] - 1
+    ga = np.zeros((T, 2))
+    gb = np.zeros((T, 2))
+    post = np.zeros((F, n)) if want_post else None
+    loss = ctypes.c_double()
+    P = lambda x: x.ctypes.data if x is not None else None
+    rc = _lib().oracle_woms(n, M, P(rp), P(ci), P(llr), P(synd), P(tgt), F, T, P(a), P(b),
+                            ctypes.byref(loss), P(ga), P(gb), P(post))
+    if rc != 0:
+        raise MemoryError("oracle woms allocation")
+    return dict(loss=loss.value, galpha=ga, gbeta=gb, post=post)

@@ -315,3 +315,134 @@ int oracle_ioms(int layered, int n, int M, const int32_t *rp, const int32_t *ci,
     free(m_old); free(m_new); free(L); free(lq); free(q); free(qf);
     return 0;
 }
+
+/* --------------------------- unrolled weighted offset min-sum and its gradient
+ *
+ * T flooding iterations, no stopping test.  Iteration t (1-based) uses the
+ * weights alpha[t-1][cls], beta[t-1][cls] of the check's degree class
+ * (cls = 0 for checks of the smallest degree in the code, 1 otherwise):
+ *   q_e     = L^{t-1}_{v(e)} - m^{t-1}_e                    (m^0 = 0, L^0 = llr)
+ *   mn_e    = min over the check's other edges of |q|
+ *   m^t_e   = (-1)^{s_c} prod_{other edges} sgn(q) * alpha * max(mn_e - beta, 0)
+ *   L^t_v   = llr_v + sum_{e at v} m^t_e
+ * Loss = mean over frames and variables of the binary cross-entropy of
+ * P(b = 1) = sigma(-L^T_v) against the target bits:
+ *   b softplus(L) + (1 - b) softplus(-L).
+ * Reverse mode with the conventions: the gradient of a minimum goes to its
+ * argmin (ties: the lowest edge index), max(x, 0)' = 0 at x <= 0, sgn(0) = +1;
+ * the signs are piecewise constant and carry no gradient.  All iterations are
+ * stored (no checkpointing).  galpha/gbeta [T][2] are overwritten.
+ */
+static double softplus(double x) { return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
+static double sigmoid(double x) { return x >= 0.0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x)); }
+
+/* lowest-index argmin of |q| over a check's edges, optionally excluding one edge */
+static int32_t argmin_abs(const double *q, int32_t d, int32_t skip) {
+    int32_t best = -1;
+    for (int32_t k = 0; k < d; ++k) {
+        if (k == skip) continue;
+        if (best < 0 || fabs(q[k]) < fabs(q[best])) best = k;
+    }
+    return best;
+}
+
+int oracle_woms(int n, int M, const int32_t *rp, const int32_t *ci, const double *llr,
+                const uint8_t *synd, const uint8_t *target, int F, int T, const double *alpha,
+                const double *beta, double *loss, double *galpha, double *gbeta, double *post) {
+    int32_t E = rp[M];
+    int32_t dmin = 1 << 30, dmax = 0;
+    for (int c = 0; c < M; ++c) {
+        int32_t d = rp[c + 1] - rp[c];
+        if (d < dmin) dmin = d;
+        if (d > dmax) dmax = d;
+    }
+    double *m = (double *)calloc((size_t)(T + 1) * E, sizeof(double));   /* m[t][e] */
+    double *L = (double *)malloc(sizeof(double) * (size_t)(T + 1) * n);  /* L[t][v] */
+    double *q = (double *)malloc(sizeof(double) * (size_t)(dmax + 1));
+    double *gL = (double *)malloc(sizeof(double) * (size_t)n);
+    double *gLn = (double *)malloc(sizeof(double) * (size_t)n);
+    double *gm = (double *)malloc(sizeof(double) * (size_t)E);
+    double *gq = (double *)malloc(sizeof(double) * (size_t)E);
+    if (!m || !L || !q || !gL || !gLn || !gm || !gq) {
+        free(m); free(L); free(q); free(gL); free(gLn); free(gm); free(gq);
+        return -1;
+    }
+    for (int i = 0; i < 2 * T; ++i) { galpha[i] = 0.0; gbeta[i] = 0.0; }
+    double total = 0.0;
+    const double scale = 1.0 / ((double)F * (double)n);
+    for (int f = 0; f < F; ++f) {
+        const double *lf = llr + (size_t)f * n;
+        const uint8_t *sf = synd + (size_t)f * M;
+        const uint8_t *bf = target + (size_t)f * n;
+        memset(m, 0, sizeof(double) * (size_t)E);
+        for (int v = 0; v < n; ++v) L[v] = lf[v];
+        /* forward, every iteration kept */
+        for (int t = 1; t <= T; ++t) {
+            const double *mo = m + (size_t)(t - 1) * E;
+            double *mt = m + (size_t)t * E;
+            const double *Lo = L + (size_t)(t - 1) * n;
+            double *Lt = L + (size_t)t * n;
+            for (int c = 0; c < M; ++c) {
+                int32_t beg = rp[c], d = rp[c + 1] - rp[c];
+                int cls = d == dmin ? 0 : 1;
+                double a = alpha[2 * (t - 1) + cls], b = beta[2 * (t - 1) + cls];
+                for (int32_t k = 0; k < d; ++k) q[k] = Lo[ci[beg + k]] - mo[beg + k];
+                for (int32_t k = 0; k < d; ++k) {
+                    double sign = (sf[c] & 1) ? -1.0 : 1.0;
+                    for (int32_t j = 0; j < d; ++j)
+                        if (j != k) sign *= sgn(q[j]);
+                    double mn = fabs(q[argmin_abs(q, d, k)]);
+                    double r = mn - b;
+                    mt[beg + k] = sign * a * (r > 0.0 ? r : 0.0);
+                }
+            }
+            for (int v = 0; v < n; ++v) Lt[v] = lf[v];
+            for (int32_t e = 0; e < E; ++e) Lt[ci[e]] += mt[e];
+        }
+        const double *LT = L + (size_t)T * n;
+        for (int v = 0; v < n; ++v) {
+            total += bf[v] ? softplus(LT[v]) : softplus(-LT[v]);
+            if (post) post[(size_t)f * n + v] = LT[v];
+            gL[v] = scale * (bf[v] ? sigmoid(LT[v]) : -sigmoid(-LT[v]));
+        }
+        /* reverse */
+        memset(gm, 0, sizeof(double) * (size_t)E);     /* d loss / d m^t through q^{t+1} */
+        for (int t = T; t >= 1; --t) {
+            const double *mo = m + (size_t)(t - 1) * E;
+            const double *Lo = L + (size_t)(t - 1) * n;
+            memset(gq, 0, sizeof(double) * (size_t)E);
+            for (int c = 0; c < M; ++c) {
+                int32_t beg = rp[c], d = rp[c + 1] - rp[c];
+                int cls = d == dmin ? 0 : 1;
+                double a = alpha[2 * (t - 1) + cls], b = beta[2 * (t - 1) + cls];
+                for (int32_t k = 0; k < d; ++k) q[k] = Lo[ci[beg + k]] - mo[beg + k];
+                for (int32_t k = 0; k < d; ++k) {
+                    int32_t e = beg + k;
+                    double g = gm[e] + gL[ci[e]];            /* d loss / d m^t_e */
+                    double sign = (sf[c] & 1) ? -1.0 : 1.0;
+                    for (int32_t j = 0; j < d; ++j)
+                        if (j != k) sign *= sgn(q[j]);
+                    int32_t src = argmin_abs(q, d, k);
+                    double r = fabs(q[src]) - b;
+                    double relu = r > 0.0 ? r : 0.0;
+                    galpha[2 * (t - 1) + cls] += g * sign * relu;
+                    if (r > 0.0) {
+                        double gr = g * sign * a;
+                        gbeta[2 * (t - 1) + cls] -= gr;
+                        gq[beg + src] += gr * sgn(q[src]);
+                    }
+                }
+            }
+            /* q^t = L^{t-1} - m^{t-1};  L^{t-1} = llr + sum m^{t-1} */
+            for (int v = 0; v < n; ++v) gLn[v] = 0.0;
+            for (int32_t e = 0; e < E; ++e) {
+                gLn[ci[e]] += gq[e];
+                gm[e] = -gq[e];
+            }
+            for (int v = 0; v < n; ++v) gL[v] = gLn[v];
+        }
+    }
+    *loss = total * scale;
+    free(m); free(L); free(q); free(gL); free(gLn); free(gm); free(gq);
+    return 0;
+}
