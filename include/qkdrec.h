@@ -200,6 +200,45 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
                                   int32_t *iters_out, uint8_t *conv_out, float *post_out,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------- differentiable weighted min-sum */
+
+/*
+ * Unrolled weighted offset min-sum: T flooding iterations without a stopping
+ * test, iteration t scaling and offsetting the check-to-variable magnitudes with
+ * learnable weights of the check's degree class (class 0 = the smallest check
+ * degree of the code, class 1 = any other):
+ *   m_cv = (-1)^{s_c} prod sgn(q) * alpha[t][cls] * max(min_{v'!=v}|q| - beta[t][cls], 0),
+ * the min-sum form of the BP check rule of Sec. III-C with per-iteration
+ * weights fitted on frames the channel model generates.  Loss = mean over
+ * frames and variables of the binary cross-entropy of P(b = 1) = sigmoid(-L^T)
+ * against target bits b (Bob's slice bits).
+ *   llr     DEVICE float [F][n];  synd DEVICE uint8 [F][M];  target DEVICE uint8 [F][n]
+ *   alpha, beta  DEVICE float [T][2]
+ *   ckpt_every   iterations between stored message checkpoints (K >= 1); the
+ *                backward recomputes each K-iteration segment from them.
+ *   workspace    DEVICE, >= qkdrec_woms_workspace_size bytes, 256-byte aligned;
+ *                qkdrec_woms_backward must get the same workspace (holding the
+ *                forward's checkpoints), inputs and weights as the forward.
+ * Forward: loss_out DEVICE float [1]; post_out DEVICE float [F][n] final
+ * posteriors (may be NULL).
+ * Backward: grad_alpha, grad_beta DEVICE float [T][2], d loss / d weights.  The
+ * gradient of a minimum goes to its argmin (ties: lowest edge index),
+ * max(x, 0)' = 0 at x <= 0, signs carry no gradient.  Gradients are summed in
+ * FP64 over the frames.
+ * Errors: QKDREC_ERR_ARG (NULLs, F/T/ckpt_every < 1, workspace too small),
+ *         QKDREC_ERR_UNSUPPORTED (check degree above 32).
+ */
+qkdrec_status qkdrec_woms_workspace_size(qkdrec_code_t code, int32_t F, int32_t T, int32_t ckpt_every,
+                                         size_t *bytes);
+qkdrec_status qkdrec_woms_forward(qkdrec_code_t code, const float *llr, const uint8_t *synd,
+                                  const uint8_t *target, int32_t F, int32_t T, const float *alpha,
+                                  const float *beta, int32_t ckpt_every, float *loss_out, float *post_out,
+                                  void *workspace, size_t workspace_bytes, void *stream);
+qkdrec_status qkdrec_woms_backward(qkdrec_code_t code, const float *llr, const uint8_t *synd,
+                                   const uint8_t *target, int32_t F, int32_t T, const float *alpha,
+                                   const float *beta, int32_t ckpt_every, float *grad_alpha,
+                                   float *grad_beta, void *workspace, size_t workspace_bytes, void *stream);
+
 /*
  * No-allocation variant of qkdrec_decode_batch.  The paper has no counterpart:
  * this serves callers that cannot allocate device memory when they decode --

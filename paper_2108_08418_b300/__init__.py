@@ -34,6 +34,7 @@ EXPORTED = [
     "qkdrec_slice_capacity", "qkdrec_last_error", "qkdrec_version",
     "qkdrec_profile_begin", "qkdrec_profile_end",
     "qkdrec_decode_static_capacity", "qkdrec_decode_batch_static",
+    "qkdrec_woms_workspace_size", "qkdrec_woms_forward", "qkdrec_woms_backward",
 ]
 SELFTEST = ["qkdrec_selftest_phi"]
 
@@ -82,6 +83,9 @@ def lib():
         "qkdrec_slice_capacity": (U, [D, I32, I32, D, D, U, D, P]),
         "qkdrec_decode_static_capacity": (ctypes.c_size_t, []),
         "qkdrec_decode_batch_static": (U, [P, P, P, I32, P, P, P, P, P, P]),
+        "qkdrec_woms_workspace_size": (U, [P, I32, I32, I32, P]),
+        "qkdrec_woms_forward": (U, [P, P, P, P, I32, I32, P, P, I32, P, P, P, ctypes.c_size_t, P]),
+        "qkdrec_woms_backward": (U, [P, P, P, P, I32, I32, P, P, I32, P, P, P, ctypes.c_size_t, P]),
         "qkdrec_profile_begin": (U, []),
         "qkdrec_selftest_phi": (U, [P, I64, P, P]),
         "qkdrec_profile_end": (U, [P, I32, P]),
@@ -310,6 +314,52 @@ def qkdrec_decode_batch_static(code: Code, llr, synd, opts: DecodeOpts | None = 
                                             ctypes.c_void_p(post.data_ptr()) if post is not None else None,
                                             _stream(llr)))
     return out
+
+
+# ------------------------------------------------ differentiable weighted min-sum
+def qkdrec_woms_workspace_size(code: Code, F: int, T: int, ckpt_every: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().qkdrec_woms_workspace_size(code.handle, int(F), int(T), int(ckpt_every), ctypes.byref(b)))
+    return b.value
+
+
+def _woms_ptrs(code, llr, synd, target, alpha, beta):
+    torch = _torch()
+    llr2 = llr.reshape(-1, code.n)
+    F = llr2.shape[0]
+    if synd.numel() != F * code.M or target.numel() != F * code.n:
+        raise ValueError("synd must be uint8 [F][M] and target uint8 [F][n]")
+    if alpha.shape != beta.shape or alpha.dim() != 2 or alpha.shape[1] != 2:
+        raise ValueError("alpha and beta must be float32 [T][2]")
+    return (F, alpha.shape[0], _dev(llr2, torch.float32, "llr"), _dev(synd, torch.uint8, "synd"),
+            _dev(target, torch.uint8, "target"), _dev(alpha, torch.float32, "alpha"),
+            _dev(beta, torch.float32, "beta"))
+
+
+def qkdrec_woms_forward(code: Code, llr, synd, target, alpha, beta, ckpt_every: int, workspace,
+                        want_post: bool = False):
+    """Loss (float32 [1]) of the unrolled weighted min-sum; `workspace` keeps the checkpoints."""
+    torch = _torch()
+    F, T, lp, sp, tp, ap, bp = _woms_ptrs(code, llr, synd, target, alpha, beta)
+    loss = torch.empty(1, dtype=torch.float32, device=llr.device)
+    post = torch.empty((F, code.n), dtype=torch.float32, device=llr.device) if want_post else None
+    _check(lib().qkdrec_woms_forward(code.handle, lp, sp, tp, F, T, ap, bp, int(ckpt_every),
+                                     ctypes.c_void_p(loss.data_ptr()),
+                                     ctypes.c_void_p(post.data_ptr()) if post is not None else None,
+                                     ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(llr)))
+    return loss, post
+
+
+def qkdrec_woms_backward(code: Code, llr, synd, target, alpha, beta, ckpt_every: int, workspace):
+    """(d loss / d alpha, d loss / d beta), float32 [T][2] each."""
+    torch = _torch()
+    F, T, lp, sp, tp, ap, bp = _woms_ptrs(code, llr, synd, target, alpha, beta)
+    ga = torch.empty_like(alpha)
+    gb = torch.empty_like(beta)
+    _check(lib().qkdrec_woms_backward(code.handle, lp, sp, tp, F, T, ap, bp, int(ckpt_every),
+                                      ctypes.c_void_p(ga.data_ptr()), ctypes.c_void_p(gb.data_ptr()),
+                                      ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(llr)))
+    return ga, gb
 
 
 # ------------------------------------------------------------ host helpers

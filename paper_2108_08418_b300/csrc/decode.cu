@@ -994,3 +994,5 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
 }
 
 }  // extern "C"
+
+#include "decode_woms.cuh"
