@@ -75,6 +75,35 @@ def gaussian_pair(seed: int, count: int, snr: float, va: float = 1.0):
     return x.astype(np.float32), y.astype(np.float32)
 
 
+def uneven_frames(seed: int, count: int, lengths=(4096, 16384, 65536), snr_range=(2.0, 15.0),
+                  snr_step: float | None = None):
+    """Frame lengths drawn uniformly from `lengths` and SNRs uniformly from
+    `snr_range` (Philox key (seed, 2)); with `snr_step` the SNR is drawn uniformly
+    from the grid lo, lo + step, ..., hi instead.  Returns (n int64 [count],
+    snr float64 [count])."""
+    g = np.random.Generator(np.random.Philox(key=[int(seed), 2]))
+    n = np.asarray(lengths, dtype=np.int64)[g.integers(0, len(lengths), size=count)]
+    if snr_step:
+        k = int(round((snr_range[1] - snr_range[0]) / snr_step))
+        snr = snr_range[0] + snr_step * g.integers(0, k + 1, size=count)
+    else:
+        snr = g.uniform(snr_range[0], snr_range[1], size=count)
+    return n, snr
+
+
+def gaussian_frames(seed: int, lengths, snrs, va: float = 1.0):
+    """Concatenated (x, y) float32 of frames with their own SNR: x ~ N(0, va) from key
+    (seed, 0), noise N(0, 1/snr_f) from key (seed, 1) scaled per frame."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    total = int(lengths.sum())
+    gx = np.random.Generator(np.random.Philox(key=[int(seed), 0]))
+    gn = np.random.Generator(np.random.Philox(key=[int(seed), 1]))
+    x = gx.standard_normal(total) * np.sqrt(va)
+    scale = np.repeat(1.0 / np.sqrt(np.asarray(snrs, dtype=np.float64)), lengths)
+    y = x + gn.standard_normal(total) * scale
+    return x.astype(np.float32), y.astype(np.float32)
+
+
 def checks_for_rate(n: int, rate: float) -> int:
     """Number of parity checks M = n (1 - r) of a rate-r code of length n."""
     m = int(round(n * (1.0 - rate)))

@@ -13,7 +13,9 @@
  *   - variable sockets are placed on check sockets by a seeded permutation
  *     (drawn by the caller and passed in), then double edges and edges on
  *     4-cycles are broken by socket swaps with uniformly drawn partner edges
- *     (splitmix64 stream, Steele/Lea/Flood 2014), at most `max_passes` passes.
+ *     (splitmix64 stream, Steele/Lea/Flood 2014), at most `max_passes` passes;
+ *   - repeated (check, variable) pairs still left (dense codes) are then
+ *     swapped away on their own, so H is always a set of distinct pairs.
  * Swapping the variable ends of two edges keeps every node degree.
  */
 #include <stdint.h>
@@ -121,6 +123,26 @@ int64_t synth_break_short_cycles(int32_t n, int32_t M, const int32_t *rp, int32_
             int64_t p = (int64_t)draw_below(&s, (uint64_t)E);
             int32_t t = ci[e]; ci[e] = ci[p]; ci[p] = t;
         }
+    }
+    /* dense codes keep 4-cycles that no swap removes, and the last 4-cycle swaps
+       can leave repeated variables in a check: a parity-check matrix is a set of
+       (check, variable) pairs, so swap those edges alone until none is left */
+    for (int32_t pass = 0; pass < 100 * (max_passes + 1); ++pass) {
+        int64_t nrep = 0;
+        memset(bad, 0, (size_t)E);
+        for (int32_t v = 0; v < n; ++v) stamp[v] = -1;
+        for (int32_t c = 0; c < M; ++c)
+            for (int32_t e = rp[c]; e < rp[c + 1]; ++e) {
+                if (stamp[ci[e]] == c) { bad[e] = 1; nrep++; }
+                stamp[ci[e]] = c;
+            }
+        if (nrep == 0) break;
+        for (int64_t e = 0; e < E; ++e) {
+            if (!bad[e]) continue;
+            int64_t p = (int64_t)draw_below(&s, (uint64_t)E);
+            int32_t t = ci[e]; ci[e] = ci[p]; ci[p] = t;
+        }
+        find_bad(n, M, rp, ci, vptr, vedge, vfill, stamp, stamp_chk, bad, &ncyc);
     }
     free(vptr); free(vedge); free(vfill); free(stamp); free(stamp_chk); free(bad);
     return ncyc;

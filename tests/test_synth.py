@@ -49,3 +49,24 @@ def test_gaussian_pair_prefix_consistent():
     x1, y1 = synth.gaussian_pair(9, 5000, 15.0)
     x2, y2 = synth.gaussian_pair(9, 123, 15.0)
     assert np.array_equal(x1[:123], x2) and np.array_equal(y1[:123], y2)
+
+
+@pytest.mark.parametrize("n,rate", [(512, 60 / 64), (4096, 60 / 64), (2048, 0.9)])
+def test_dense_codes_have_no_repeated_pairs(n, rate):
+    """Dense high-rate codes keep 4-cycles, but H stays a set of distinct
+    (check, variable) pairs with every column of degree 3."""
+    M = synth.checks_for_rate(n, rate)
+    rp, ci, res = synth.make_regular_code(17, n, M)
+    rows = np.repeat(np.arange(M), np.diff(rp))
+    assert np.unique(rows.astype(np.int64) * n + ci).size == ci.size
+    assert np.all(np.bincount(ci, minlength=n) == 3)
+
+
+def test_uneven_frames_and_gaussian_frames():
+    n, snr = synth.uneven_frames(3, 500, (4096, 16384), (2.0, 15.0), snr_step=0.1)
+    assert set(n.tolist()) <= {4096, 16384} and snr.min() >= 2.0 - 1e-12 and snr.max() <= 15.0 + 1e-12
+    assert np.allclose(np.round((snr - 2.0) / 0.1), (snr - 2.0) / 0.1)
+    lengths = np.array([5, 0, 7])
+    x, y = synth.gaussian_frames(4, lengths, np.array([3.0, 5.0, 1e6]))
+    assert x.size == y.size == 12 and x.dtype == np.float32
+    assert np.allclose(x[5:], y[5:], atol=1e-2)          # SNR 1e6: y ~ x
