@@ -188,6 +188,261 @@ def oracle_sample(step, budget_frames, cores):
     return good, wall, len(tasks)
 
 
+# ---------------------------------------------------------- uneven batch
+UNEVEN_FRAMES = 4096
+UNEVEN_LENGTHS = (4096, 16384, 65536)
+UNEVEN_SNR = (2.0, 15.0)
+UNEVEN_SNR_STEP = 0.1
+UNEVEN_MAX_ITER = 50
+UNEVEN_SEED = 11
+UNEVEN_RATE_FRACTION = 0.90     # codes 10% below the slice capacity, as in the paper's Fig. 4 runs
+UNEVEN_WORKLOAD = ("uneven batch: 4096 frames, n in {4096, 16384, 65536}, SNR uniform on the 0.1 grid of 2..15, "
+                   "5 Gray slices, per (frame, slice) rate 0.90 x capacity on the 1/64 grid within [0.10, 0.95] "
+                   "(below 0.10: disclosed), dv=3 codes per (n, rate), layered offset min-sum FP32 (offset 0.5), "
+                   "<= 50 iterations, early stop, whole step replayed as one CUDA graph")
+
+
+def _capacity_row(snr):
+    import paper_2108_08418_b300 as q
+    lo, hi = q.quantiser_range(snr)
+    return snr, [q.qkdrec_slice_capacity(snr, M_SLICES, j, lo, hi) for j in range(M_SLICES)]
+
+
+def uneven_rate(capacity, fraction=UNEVEN_RATE_FRACTION):
+    k = int(np.floor(fraction * capacity * 64 + 0.5))
+    r = min(k, 60) / 64
+    return r if r >= 0.10 else 0.0
+
+
+def uneven_code_seed(n, rate):
+    return 9_000_000 + 1000 * int(n).bit_length() + int(round(rate * 64))
+
+
+def _make_code_nr(key):
+    n, rate = key
+    rp, ci, res = synth.make_regular_code(uneven_code_seed(n, rate), n, synth.checks_for_rate(n, rate))
+    return key, (rp, ci, res)
+
+
+def _pool_map(fn, items, workers):
+    import multiprocessing as mp
+    if workers <= 1:
+        return [fn(i) for i in items]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(fn, items)
+
+
+def uneven_setup(seed, workers):
+    """Frames (sorted by (n, SNR)), per-(slice, frame) rates and the CSR codes (host only)."""
+    n, snr = synth.uneven_frames(seed, UNEVEN_FRAMES, UNEVEN_LENGTHS, UNEVEN_SNR, UNEVEN_SNR_STEP)
+    order = np.lexsort((snr, n))
+    n, snr = n[order], snr[order]
+    caps = dict(_pool_map(_capacity_row, sorted(set(snr.tolist())), workers))
+    rates = np.array([[uneven_rate(caps[s][j]) for s in snr.tolist()] for j in range(M_SLICES)])
+    keys = sorted({(int(n[f]), float(rates[j, f])) for j in range(M_SLICES) for f in range(n.size)
+                   if rates[j, f] > 0}, key=lambda k: -k[0])
+    codes = dict(_pool_map(_make_code_nr, keys, workers))
+    return n, snr, rates, codes
+
+
+def _oracle_uneven_frame(task):
+    """Reverse reconciliation of one frame of the uneven batch by the FP64 oracle."""
+    import oracle
+    x, y, snr, rates, csr = task
+    lo, hi = oracle.quantiser_range(snr)
+    t0 = time.perf_counter()
+    _, bits = oracle.quantise(y, M_SLICES, lo, hi)
+    alice = np.zeros_like(bits)
+    good = 0
+    for j in range(M_SLICES):
+        if rates[j] <= 0:
+            alice[j] = bits[j]
+            continue
+        rp, ci = csr[j]
+        s = oracle.syndrome(rp, ci, bits[j][None])
+        llr = oracle.slice_llr(x.astype(np.float64), alice[:j] if j else None, j, M_SLICES, lo, hi, snr ** -0.5)
+        out = oracle.decode(rp, ci, llr[None], s, "oms_layered", max_iter=UNEVEN_MAX_ITER, offset=0.5)
+        alice[j] = out["bits"][0]
+        good += y.size * int(np.array_equal(out["bits"][0], bits[j]))
+    return good, time.perf_counter() - t0
+
+
+def oracle_uneven_sample(step, per_step, cores, setup=None):
+    """A bounded sample of the uneven batch: `per_step` frames of n = 4096 (spread over
+    the SNR range), each reconciled over all 5 slices by the oracle."""
+    n, snr, rates, codes = setup or uneven_setup(UNEVEN_SEED, max(1, min(cores, 16)))
+    x, y = synth.gaussian_frames(UNEVEN_SEED, n, snr)
+    off = np.concatenate([[0], np.cumsum(n)])
+    small = np.flatnonzero(n == UNEVEN_LENGTHS[0])
+    pick = small[(np.arange(per_step) * 97 + step * per_step * 97) % small.size]
+    tasks = []
+    for f in pick:
+        csr = {j: codes[(int(n[f]), float(rates[j, f]))][:2] for j in range(M_SLICES) if rates[j, f] > 0}
+        tasks.append((x[off[f]:off[f + 1]], y[off[f]:off[f + 1]], float(snr[f]), rates[:, f].copy(), csr))
+    t0 = time.perf_counter()
+    res = _pool_map(_oracle_uneven_frame, tasks, min(cores, len(tasks)))
+    wall = time.perf_counter() - t0
+    return sum(r[0] for r in res), wall, len(tasks)
+
+
+def run_uneven(args):
+    rank, world, local = rank_env()
+    cores = len(os.sched_getaffinity(0))
+    import paper_2108_08418_b300 as q
+    from paper_2108_08418_b300 import build as qbuild
+    qbuild.build()
+    t_setup = time.time()
+    seed = UNEVEN_SEED + 1000 * rank
+    n, snr, rates, codes_h = uneven_setup(seed, max(1, min(cores, 16)))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per = max(1, min(cores, 8))
+        good, wall, nfr = oracle_uneven_sample(0, per, cores, (n, snr, rates, codes_h))
+        cpu = {"value": good / wall, "unit": "bit/s", "cores": min(cores, nfr), "kind": "oracle",
+               "sample": f"{nfr} frames of n=4096 of the batch, each reconciled over all 5 slices (FP64 quantiser, "
+                         f"LLR, syndrome, layered offset min-sum <= {UNEVEN_MAX_ITER} iterations), one process "
+                         f"per frame", "wall_s": wall}
+
+    import torch
+    import torch.distributed as dist
+    from paper_2108_08418_b300.uneven import UnevenBatch
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    codes = {k: q.Code(k[0], v[0], v[1], seed=uneven_code_seed(*k)) for k, v in codes_h.items()}
+    residual = max(v[2] for v in codes_h.values())
+    x, y = synth.gaussian_frames(seed, n, snr)
+    hx, hy = torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()
+    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=UNEVEN_MAX_ITER, device=dev)
+    ub.x.copy_(hx)
+    ub.y.copy_(hy)
+    tunings = ub.autotune(max_iter=10)
+    ub.capture()
+    setup_s = time.time() - t_setup
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ub.replay()
+    barrier()
+    sampler = ClockSampler(smi_index(torch, dev, local))
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ub.replay()
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    good_bits, raw_bits = ub.reconciled_bits(), ub.decoded_bits()
+    ok = ub.frame_ok().cpu().numpy()
+    dec = rates > 0
+    fer = {}
+    for ln in UNEVEN_LENGTHS:
+        sel = n == ln
+        fer[f"n{ln}"] = [round(float(1 - ok[j, sel & dec[j]].mean()), 4) if (sel & dec[j]).any() else None
+                         for j in range(M_SLICES)]
+    iters = ub.iters.cpu().numpy()
+    mean_iters = [round(float(iters[j, dec[j]].mean()), 2) if dec[j].any() else None for j in range(M_SLICES)]
+
+    # per-kernel durations: the same step run eagerly with the profiling hooks
+    q.qkdrec_profile_begin()
+    for _ in range(args.steps):
+        ub.step()
+    barrier()
+    stats = q.qkdrec_profile_end()
+
+    # end to end: pinned host x, y -> device, graph replay, flags back
+    t_e2e = None
+    h2d = hx.numel() * 4 + hy.numel() * 4
+    d2h = ub.conv.numel()
+    if not args.no_e2e:
+        barrier()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(args.steps):
+            ub.x.copy_(hx, non_blocking=True)
+            ub.y.copy_(hy, non_blocking=True)
+            ub.replay()
+            flags = ub.conv.to("cpu", non_blocking=True)
+            stream.synchronize()
+            _ = int(flags.sum())
+        e3.record(stream)
+        barrier()
+        t_e2e = e2.elapsed_time(e3)
+
+    tot = torch.tensor([good_bits, raw_bits], dtype=torch.float64, device=dev)
+    tmax = torch.tensor([ms, t_e2e or 0.0], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    good_bits, raw_bits = float(tot[0]), float(tot[1])
+    ms, t_e2e_max = float(tmax[0]), float(tmax[1])
+    ms_step = ms / args.steps
+    roof, kernels, launches = roofline(stats, args.steps)
+    if rank != 0:
+        return
+    line = {
+        "metric": "reconciled key bits/s", "value": good_bits / (ms_step / 1e3), "unit": "bit/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded Philox Gaussian quadratures and seeded regular dv=3 LDPC codes",
+        "config": {"workload": UNEVEN_WORKLOAD, "frames": int(n.size), "samples": int(n.sum()),
+                   "groups_per_slice": [len(g) for g in ub.groups], "algo": "oms_layered", "prec": "f32",
+                   "max_iter": UNEVEN_MAX_ITER, "tuning_per_slice": [t[0] for t in tunings],
+                   "l2": "inputs larger than L2 (x, y 470 MB each; plan workspace "
+                         f"{ub.ws.numel() / 2**30:.2f} GiB)",
+                   "raw_decoded_bits_per_s": raw_bits / (ms_step / 1e3), "fer_per_slice": fer,
+                   "mean_iters_per_slice": mean_iters, "code_residual_4cycles": residual,
+                   "kernel_times": "per-kernel figures from the same step run eagerly with the profiling hooks",
+                   "setup_s": round(setup_s, 1)},
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": ({"value": good_bits / (t_e2e_max / args.steps / 1e3), "unit": "bit/s",
+                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "ms_per_step": t_e2e_max / args.steps} if t_e2e else None),
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def smi_index(torch, dev, local):
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    return (f"{getattr(props, 'pci_domain_id', 0):08x}:{bus:02x}:{getattr(props, 'pci_device_id', 0):02x}.0"
+            if bus is not None else str(local))
+
+
+def roofline(stats, steps):
+    """Roofline of the dominant kernel class, per-kernel table and our launches per step."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak, peak_src = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6400.0, "fallback")
+    dname, d = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_src,
+            "traffic": load_traffic(dname, d), "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+            "avg_launch_ms": d["ms"] / d["launches"], "launches": d["launches"],
+            "share": round(d["ms"] / sum(v["ms"] for v in stats.values()), 4)}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": round(v["ms"] / steps, 3),
+                   "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None}
+               for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"])}
+    launches = int(sum(v["launches"] for v in stats.values()) / steps)
+    return roof, kernels, launches
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     rank, world, local = rank_env()
@@ -270,11 +525,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step(dx, dy)
     barrier()
-    props = torch.cuda.get_device_properties(dev)
-    bus = getattr(props, "pci_bus_id", None)
-    smi_id = (f"{getattr(props, 'pci_domain_id', 0):08x}:{bus:02x}:{getattr(props, 'pci_device_id', 0):02x}.0"
-              if bus is not None else str(local))
-    sampler = ClockSampler(smi_id)
+    sampler = ClockSampler(smi_index(torch, dev, local))
     sampler.start()
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -335,25 +586,7 @@ def run_ours(args):
     ms_step = ms / args.steps
     value = good_bits / (ms_step / 1e3)
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak, peak_src = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6400.0, "fallback")
-    dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    dname, d = dom
-    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-    traffic = load_traffic(dname, d)
-    roof = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "peak_source": peak_src,
-            "traffic": traffic, "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-            "avg_launch_ms": d["ms"] / d["launches"], "launches": d["launches"],
-            "share": round(d["ms"] / sum(v["ms"] for v in stats.values()), 4)}
-    kernels = {k: {"launches": v["launches"], "ms_per_step": round(v["ms"] / args.steps, 3),
-                   "GB/s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None}
-               for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"])}
-    launches = int(sum(v["launches"] for v in stats.values()) / args.steps)
+    roof, kernels, launches = roofline(stats, args.steps)
     if rank != 0:
         return
     line = {
@@ -405,6 +638,9 @@ def run_reference(args):
     if rank != 0:
         return
     cores = len(os.sched_getaffinity(0))
+    if args.workload == "uneven":
+        run_reference_uneven(args, world, cores)
+        return
     per_snr = max(1, min(cores, 8) // 2)
     for w in range(args.warmup):
         oracle_sample(w, per_snr, cores)
@@ -428,6 +664,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_uneven(args, world, cores):
+    setup = uneven_setup(UNEVEN_SEED, max(1, min(cores, 16)))
+    per = max(1, min(cores, 8))
+    for w in range(args.warmup):
+        oracle_uneven_sample(w, per, cores, setup)
+    goods, walls, nfr = 0, 0.0, 0
+    for s in range(args.steps):
+        g, wall, nfr = oracle_uneven_sample(args.warmup + s, per, cores, setup)
+        goods += g
+        walls += wall
+    value = goods / walls
+    line = {
+        "impl": "reference", "metric": "reconciled key bits/s", "value": value, "unit": "bit/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": walls / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded Philox Gaussian quadratures and seeded regular dv=3 LDPC codes",
+        "config": {"workload": UNEVEN_WORKLOAD, "sample": f"per step: {nfr} frames of n=4096 of the batch"},
+        "cpu_baseline": {"value": value, "unit": "bit/s", "cores": min(cores, nfr), "kind": "oracle",
+                         "sample": f"{nfr} frames of n=4096 per step, each reconciled over all 5 slices"},
+        "e2e": {"value": value, "unit": "bit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------- profiling case
 CASES = {
     # one slice decode of the sweep at n = 2^16 and 512 frames (edge messages 400 MB,
@@ -436,7 +696,35 @@ CASES = {
     "decode_oms_f32": dict(logn=16, frames=512, rate=0.84375, algo="oms_flood", prec="f32", iters=5),
     "decode_layered_f32": dict(logn=16, frames=512, rate=0.84375, algo="oms_layered", prec="f32", iters=5),
     "decode_oms_i8": dict(logn=16, frames=512, rate=0.84375, algo="oms_flood", prec="i8", iters=5),
+    # the plan decoder on a small uneven batch: 96 frames of n = 2^16, 192 of 2^14, 384 of 2^12
+    # (rate 0.84375; ~0.9 GB on the device)
+    "plan_layered": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5),
 }
+
+
+def run_plan_case(args, c):
+    import torch
+    import paper_2108_08418_b300 as q
+    g = synth.philox(78)
+    groups = []
+    for logn, F in c["groups"]:
+        n = 1 << logn
+        rp, ci, _ = synth.make_regular_code(code_seed(logn, 3), n, synth.checks_for_rate(n, c["rate"]))
+        code = q.Code(n, rp, ci)
+        b = g.integers(0, 2, size=(F, n)).astype(np.uint8)
+        llr = ((2 / 0.52 ** 2) * ((1.0 - 2.0 * b) + 0.52 * g.standard_normal((F, n)))).astype(np.float32)
+        bd = torch.from_numpy(b).cuda()
+        groups.append(dict(code=code, llr=torch.from_numpy(llr).cuda(), synd=q.qkdrec_syndrome(code, bd),
+                           bits=torch.empty_like(bd), iters=torch.empty(F, dtype=torch.int32, device="cuda"),
+                           conv=torch.empty(F, dtype=torch.uint8, device="cuda")))
+    opts = q.DecodeOpts(algo="oms_layered", prec="f32", max_iter=c["iters"], early_stop=False)
+    plan = q.Plan(groups, opts, dict(frames_per_cta=8, threads_per_cta=512, stage_depth=4))
+    ws = plan.workspace()
+    for _ in range(args.warmup + args.steps):
+        plan.launch(ws)
+    torch.cuda.synchronize()
+    print(f"case {args.case}: frames={sum(F for _, F in c['groups'])} "
+          f"edge-frames/launch={sum(gr['code'].E * gr['llr'].shape[0] for gr in groups)}", flush=True)
 
 
 def run_case(args):
@@ -446,6 +734,9 @@ def run_case(args):
     from paper_2108_08418_b300 import build as qbuild
     qbuild.build()
     c = CASES[args.case]
+    if "groups" in c:
+        run_plan_case(args, c)
+        return
     n, F = 1 << c["logn"], c["frames"]
     M = synth.checks_for_rate(n, c["rate"])
     rp, ci, _ = synth.make_regular_code(code_seed(c["logn"], 3), n, M)
@@ -472,6 +763,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
     ap.add_argument("--case", choices=sorted(CASES), help="run one small fixed decode (for ncu)")
+    ap.add_argument("--workload", choices=["sweep", "uneven"], default="sweep",
+                    help="sweep: the block-size sweep (default); uneven: the one-graph uneven batch")
     args = ap.parse_args()
     if args.case:
         run_case(args)
@@ -480,6 +773,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -200,6 +200,90 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
                                   int32_t *iters_out, uint8_t *conv_out, float *post_out,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------ uneven batches (one launch) */
+
+/*
+ * Frames whose own SNR sets their quantiser range and noise level: frame f
+ * covers samples [frame_offsets[f], frame_offsets[f+1]) of the concatenated
+ * arrays (frames of different lengths allowed).  Same results, sample by
+ * sample, as qkdrec_quantise_slices / qkdrec_slice_llr called on each frame
+ * with its parameters.
+ *   frame_offsets  DEVICE int64 [F + 1], non-decreasing, last = count.
+ *   frame_ranges   DEVICE double [F][2]: lo, hi of the frame's quantiser.
+ *   frame_params   DEVICE double [F][3]: lo, hi, sigma_n of the frame.
+ *   bits_out / lower_bits are [m][count] / [j][count] planes of the whole batch.
+ *   The per-frame data live on the device and are not validated: ordered
+ *   offsets, lo < hi and sigma_n > 0 are the caller's duty (otherwise the values
+ *   are meaningless; the kernels clamp each frame's range to [0, count), so every
+ *   access stays inside the arrays).
+ */
+qkdrec_status qkdrec_quantise_slices_frames(const float *y, int64_t count, const int64_t *frame_offsets,
+                                            const double *frame_ranges, int32_t F, int32_t m_slices,
+                                            qkdrec_label label, uint8_t *idx_out, uint8_t *bits_out,
+                                            void *stream);
+qkdrec_status qkdrec_slice_llr_frames(const float *x, int64_t count, const int64_t *frame_offsets,
+                                      const double *frame_params, int32_t F, int32_t m_slices, int32_t j,
+                                      qkdrec_label label, const uint8_t *lower_bits, float *llr_out,
+                                      void *stream);
+
+/* One group of an uneven batch: frames that share one code (Sec. III-A: the
+ * sub-blocks of a slice share H_j; here many slices and block lengths at once). */
+typedef struct {
+    qkdrec_code_t code;
+    int32_t frames;          /* F_g >= 0 */
+    const float *llr;        /* DEVICE float [F_g][n] */
+    const uint8_t *synd;     /* DEVICE uint8 [F_g][M] */
+    uint8_t *bits_out;       /* DEVICE uint8 [F_g][n] */
+    int32_t *iters_out;      /* DEVICE int32 [F_g] */
+    uint8_t *conv_out;       /* DEVICE uint8 [F_g] */
+} qkdrec_group;
+
+/* Launch shape of a plan; the autotuner searches all combinations.
+ *   frames_per_cta  8, 16 or 32: frames one CTA decodes together (lanes per check)
+ *   threads_per_cta 128, 256 or 512
+ *   stage_depth     2, 4 or 8: edge loads in flight per lane */
+typedef struct {
+    int32_t frames_per_cta;
+    int32_t threads_per_cta;
+    int32_t stage_depth;
+} qkdrec_tuning;
+
+typedef struct qkdrec_plan_s *qkdrec_plan_t;
+
+/* Defaults: 32 frames, 256 threads, depth 8. */
+void qkdrec_tuning_default(qkdrec_tuning *tuning);
+
+/*
+ * Plan the decode of an uneven batch in ONE persistent launch: work items
+ * (group, tile of frames_per_cta frames), longest first, taken by CTAs from a
+ * device queue (one atomic increment; no CTA waits for another).  Each CTA runs
+ * the full layered offset min-sum decode of its tile with the per-frame
+ * stopping test.  The plan binds the groups' device pointers (the caller keeps
+ * those buffers alive and may refill them between launches).  Synchronous;
+ * allocates the plan's small device tables.  Only opts->algo OMS_LAYERED with
+ * prec F32 is supported (QKDREC_ERR_UNSUPPORTED otherwise).
+ */
+qkdrec_status qkdrec_plan_create(const qkdrec_group *groups, int32_t n_groups, const qkdrec_decode_opts *opts,
+                                 const qkdrec_tuning *tuning, qkdrec_plan_t *out);
+void qkdrec_plan_destroy(qkdrec_plan_t plan);
+/* DEVICE workspace bytes for any tuning of the plan. */
+qkdrec_status qkdrec_plan_workspace_size(qkdrec_plan_t plan, size_t *bytes);
+/*
+ * Enqueue the batch decode on `stream`: a memset of the queue head and one
+ * kernel launch; no allocation and no host synchronisation, so it can be
+ * captured in a CUDA graph.  Launches of one plan must not overlap on the GPU
+ * (they share the queue head).
+ */
+qkdrec_status qkdrec_plan_launch(qkdrec_plan_t plan, void *workspace, size_t workspace_bytes, void *stream);
+qkdrec_status qkdrec_plan_get_tuning(qkdrec_plan_t plan, qkdrec_tuning *out);
+/*
+ * Autotuner: times every tuning on this plan's batch (iterations capped at
+ * max_iter if > 0), keeps the fastest in the plan and returns it (best_ms =
+ * its time).  Synchronous; runs real decodes (the outputs are overwritten).
+ */
+qkdrec_status qkdrec_plan_autotune(qkdrec_plan_t plan, void *workspace, size_t workspace_bytes,
+                                   int32_t max_iter, void *stream, qkdrec_tuning *best_out, float *best_ms);
+
 /* ------------------------------------------- differentiable weighted min-sum */
 
 /*

@@ -35,6 +35,9 @@ EXPORTED = [
     "qkdrec_profile_begin", "qkdrec_profile_end",
     "qkdrec_decode_static_capacity", "qkdrec_decode_batch_static",
     "qkdrec_woms_workspace_size", "qkdrec_woms_forward", "qkdrec_woms_backward",
+    "qkdrec_quantise_slices_frames", "qkdrec_slice_llr_frames", "qkdrec_tuning_default",
+    "qkdrec_plan_create", "qkdrec_plan_destroy", "qkdrec_plan_workspace_size", "qkdrec_plan_launch",
+    "qkdrec_plan_get_tuning", "qkdrec_plan_autotune",
 ]
 SELFTEST = ["qkdrec_selftest_phi"]
 
@@ -48,6 +51,17 @@ class QkdrecError(RuntimeError):
 class KernelStatC(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("units", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class GroupC(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("frames", ctypes.c_int32), ("llr", ctypes.c_void_p),
+                ("synd", ctypes.c_void_p), ("bits_out", ctypes.c_void_p), ("iters_out", ctypes.c_void_p),
+                ("conv_out", ctypes.c_void_p)]
+
+
+class TuningC(ctypes.Structure):
+    _fields_ = [("frames_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("stage_depth", ctypes.c_int32)]
 
 
 class DecodeOptsC(ctypes.Structure):
@@ -86,6 +100,15 @@ def lib():
         "qkdrec_woms_workspace_size": (U, [P, I32, I32, I32, P]),
         "qkdrec_woms_forward": (U, [P, P, P, P, I32, I32, P, P, I32, P, P, P, ctypes.c_size_t, P]),
         "qkdrec_woms_backward": (U, [P, P, P, P, I32, I32, P, P, I32, P, P, P, ctypes.c_size_t, P]),
+        "qkdrec_quantise_slices_frames": (U, [P, I64, P, P, I32, I32, U, P, P, P]),
+        "qkdrec_slice_llr_frames": (U, [P, I64, P, P, I32, I32, I32, U, P, P, P]),
+        "qkdrec_tuning_default": (None, [P]),
+        "qkdrec_plan_create": (U, [P, I32, P, P, P]),
+        "qkdrec_plan_destroy": (None, [P]),
+        "qkdrec_plan_workspace_size": (U, [P, P]),
+        "qkdrec_plan_launch": (U, [P, P, ctypes.c_size_t, P]),
+        "qkdrec_plan_get_tuning": (U, [P, P]),
+        "qkdrec_plan_autotune": (U, [P, P, ctypes.c_size_t, I32, P, P, P]),
         "qkdrec_profile_begin": (U, []),
         "qkdrec_selftest_phi": (U, [P, I64, P, P]),
         "qkdrec_profile_end": (U, [P, I32, P]),
@@ -211,14 +234,18 @@ def qkdrec_slice_llr(x, m_slices: int, j: int, lo: float, hi: float, sigma_n: fl
 
 
 # ---------------------------------------------------------------- syndrome
-def qkdrec_syndrome(code: Code, bits):
-    """Syndromes uint8 [F][M] of bits uint8 [F][n]."""
+def qkdrec_syndrome(code: Code, bits, out=None):
+    """Syndromes uint8 [F][M] of bits uint8 [F][n] (into `out` if given)."""
     torch = _torch()
     bits2 = bits.reshape(-1, code.n)
     F = bits2.shape[0]
     bp = _dev(bits2, torch.uint8, "bits")
-    out = torch.empty((F, code.M), dtype=torch.uint8, device=bits.device)
-    _check(lib().qkdrec_syndrome(code.handle, bp, F, ctypes.c_void_p(out.data_ptr()), _stream(bits)))
+    if out is None:
+        out = torch.empty((F, code.M), dtype=torch.uint8, device=bits.device)
+    elif out.numel() != F * code.M:
+        raise ValueError("out must be uint8 [F][M]")
+    op = _dev(out, torch.uint8, "out")
+    _check(lib().qkdrec_syndrome(code.handle, bp, F, op, _stream(bits)))
     return out
 
 
@@ -314,6 +341,109 @@ def qkdrec_decode_batch_static(code: Code, llr, synd, opts: DecodeOpts | None = 
                                             ctypes.c_void_p(post.data_ptr()) if post is not None else None,
                                             _stream(llr)))
     return out
+
+
+# ------------------------------------------------------------ uneven batches
+def qkdrec_quantise_slices_frames(y, frame_offsets, frame_ranges, m_slices: int, label: str = "gray",
+                                  want_idx: bool = True, bits_out=None):
+    """Quantiser with a range per frame: frame_offsets int64 [F+1], frame_ranges float64 [F][2]."""
+    torch = _torch()
+    count = y.numel()
+    F = frame_offsets.numel() - 1
+    idx = torch.empty(count, dtype=torch.uint8, device=y.device) if want_idx else None
+    bits = bits_out if bits_out is not None else torch.empty((m_slices, count), dtype=torch.uint8, device=y.device)
+    if bits.numel() != m_slices * count:
+        raise ValueError("bits_out must be uint8 [m][count]")
+    _dev(bits, torch.uint8, "bits_out")
+    _check(lib().qkdrec_quantise_slices_frames(_dev(y, torch.float32, "y"), count,
+                                               _dev(frame_offsets, torch.int64, "frame_offsets"),
+                                               _dev(frame_ranges, torch.float64, "frame_ranges"), F,
+                                               int(m_slices), _LABELS[label],
+                                               ctypes.c_void_p(idx.data_ptr()) if idx is not None else None,
+                                               ctypes.c_void_p(bits.data_ptr()), _stream(y)))
+    return idx, bits
+
+
+def qkdrec_slice_llr_frames(x, frame_offsets, frame_params, m_slices: int, j: int, lower_bits=None,
+                            label: str = "gray", out=None):
+    """Slice LLRs with (lo, hi, sigma_n) per frame: frame_params float64 [F][3]."""
+    torch = _torch()
+    count = x.numel()
+    F = frame_offsets.numel() - 1
+    if out is None:
+        out = torch.empty(count, dtype=torch.float32, device=x.device)
+    lb = _dev(lower_bits, torch.uint8, "lower_bits") if j > 0 else None
+    _check(lib().qkdrec_slice_llr_frames(_dev(x, torch.float32, "x"), count,
+                                         _dev(frame_offsets, torch.int64, "frame_offsets"),
+                                         _dev(frame_params, torch.float64, "frame_params"), F, int(m_slices),
+                                         int(j), _LABELS[label], lb, _dev(out, torch.float32, "out"), _stream(x)))
+    return out
+
+
+class Plan:
+    """One-launch decode of an uneven batch (groups of frames with their own codes).
+
+    groups: list of dicts with keys code (Code), llr float32 [F][n], synd uint8 [F][M],
+    bits uint8 [F][n], iters int32 [F], conv uint8 [F] -- CUDA tensors the plan binds
+    (kept alive here; refill them in place between launches)."""
+
+    def __init__(self, groups, opts: DecodeOpts, tuning: dict | None = None):
+        torch = _torch()
+        self._keep = groups
+        arr = (GroupC * max(len(groups), 1))()
+        for i, g in enumerate(groups):
+            c = g["code"]
+            F = g["llr"].numel() // c.n
+            arr[i] = GroupC(c.handle.value, F, _dev(g["llr"], torch.float32, "llr").value,
+                            _dev(g["synd"], torch.uint8, "synd").value, _dev(g["bits"], torch.uint8, "bits").value,
+                            _dev(g["iters"], torch.int32, "iters").value, _dev(g["conv"], torch.uint8, "conv").value)
+        o = opts.c()
+        t = None
+        if tuning is not None:
+            t = TuningC(tuning["frames_per_cta"], tuning["threads_per_cta"], tuning["stage_depth"])
+        self._h = ctypes.c_void_p()
+        _check(lib().qkdrec_plan_create(arr, len(groups), ctypes.byref(o), ctypes.byref(t) if t else None,
+                                        ctypes.byref(self._h)))
+
+    def workspace_size(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().qkdrec_plan_workspace_size(self._h, ctypes.byref(b)))
+        return b.value
+
+    def workspace(self, device="cuda"):
+        return _torch().empty(self.workspace_size(), dtype=_torch().uint8, device=device)
+
+    def launch(self, workspace, stream=None):
+        torch = _torch()
+        st = stream if stream is not None else torch.cuda.current_stream(workspace.device)
+        _check(lib().qkdrec_plan_launch(self._h, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                        ctypes.c_void_p(st.cuda_stream)))
+
+    def tuning(self) -> dict:
+        t = TuningC()
+        _check(lib().qkdrec_plan_get_tuning(self._h, ctypes.byref(t)))
+        return dict(frames_per_cta=t.frames_per_cta, threads_per_cta=t.threads_per_cta, stage_depth=t.stage_depth)
+
+    def autotune(self, workspace, max_iter: int = 10):
+        torch = _torch()
+        t = TuningC()
+        ms = ctypes.c_float()
+        _check(lib().qkdrec_plan_autotune(self._h, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                          int(max_iter), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                          ctypes.byref(t), ctypes.byref(ms)))
+        return dict(frames_per_cta=t.frames_per_cta, threads_per_cta=t.threads_per_cta,
+                    stage_depth=t.stage_depth), ms.value
+
+    def destroy(self):
+        if self._h:
+            lib().qkdrec_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------ differentiable weighted min-sum

@@ -996,3 +996,4 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
 }  // extern "C"
 
 #include "decode_woms.cuh"
+#include "decode_plan.cuh"

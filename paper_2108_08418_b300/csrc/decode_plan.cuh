@@ -1,0 +1,460 @@
+// Batched decoding of an uneven batch: many groups of frames, each group with
+// its own code (length n, rate), in one persistent launch (included by decode.cu).
+//
+// The batch is cut into work items (group, tile of FT frames), ordered longest
+// first.  Each CTA takes the next item with one atomic increment of a queue
+// head -- CTAs never wait for each other -- and runs the whole layered offset
+// min-sum decode of its tile: all layers of all iterations with a block
+// barrier between layers, the stopping test after every iteration, frames
+// retiring one by one, the tile leaving early once all its frames are done.
+// Lane layout: lane = slot * FT + frame, so a warp serves 32/FT checks at a
+// time; the q values of a check stay in shared memory between the two passes.
+//
+// Per tile the workspace holds L [n][FT] and m [E][FT] (frame fastest) and the
+// tile's syndrome bits, one word per check.  The q values of the first kStash
+// edges of a check wait in shared memory between the two passes; the rest are
+// recomputed from L and m, which no other check of the layer touches.
+
+namespace qkd {
+
+struct PlanGroup {
+    const int32_t *rp, *ci, *lptr, *lchk;
+    const float *llr;       // [F][n]
+    const uint8_t *synd;    // [F][M]
+    uint8_t *bits;          // [F][n]
+    int32_t *iters;         // [F]
+    uint8_t *conv;          // [F]
+    int64_t ws_off;         // byte offset of the group's first tile
+    int64_t tile_bytes;
+    int64_t E;
+    int32_t n, M, n_layers, F, dc_max;
+};
+
+struct PlanItem {
+    int32_t g, tile;
+};
+
+struct PlanArgs {
+    const PlanGroup *groups;
+    const PlanItem *items;
+    int32_t n_items;
+    int32_t *head;
+    char *ws;
+    int32_t FT, max_iter, early_stop;
+    float beta;
+    unsigned long long *prof;
+};
+
+static int64_t plan_tile_bytes(int64_t n, int64_t E, int64_t M, int FT) {
+    return (int64_t)align_up((size_t)n * FT * 4, 256) + (int64_t)align_up((size_t)E * FT * 4, 256) +
+           (int64_t)align_up((size_t)M * 4, 256);
+}
+
+template <int CH>
+__global__ void __launch_bounds__(512)
+plan_layered_kernel(PlanArgs a) {
+    extern __shared__ float qst[];  // [warps][kStash][32]
+    __shared__ int s_item;
+    __shared__ uint32_t s_unsat, s_active;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int FT = a.FT, slots = 32 / FT, slot = lane / FT, fl = lane - slot * FT;
+    float *my = qst + (warp * kStash) * 32 + lane;
+    unsigned long long units = 0;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.head, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.n_items) break;
+        const PlanItem itm = a.items[item];
+        const PlanGroup &G = a.groups[itm.g];
+        const int n = G.n, M = G.M;
+        const int64_t E = G.E;
+        const int f0 = itm.tile * FT, nf = min(FT, G.F - f0);
+        char *tb = a.ws + G.ws_off + (int64_t)itm.tile * G.tile_bytes;
+        float *L = reinterpret_cast<float *>(tb);
+        float *msg = reinterpret_cast<float *>(tb + align_up((size_t)n * FT * 4, 256));
+        uint32_t *sw = reinterpret_cast<uint32_t *>(tb + align_up((size_t)n * FT * 4, 256) +
+                                                    align_up((size_t)E * FT * 4, 256));
+        // ---- load the tile: posteriors = channel LLRs, messages = 0, syndrome words
+        for (int64_t idx = tid; idx < (int64_t)FT * n; idx += blockDim.x) {
+            const int i = (int)(idx / n), v = (int)(idx - (int64_t)i * n);
+            L[(int64_t)v * FT + i] = i < nf ? __ldg(G.llr + (int64_t)(f0 + i) * n + v) : kLlrClip;
+        }
+        for (int64_t idx = tid; idx < E * FT; idx += blockDim.x) msg[idx] = 0.0f;
+        for (int c = tid; c < M; c += blockDim.x) {
+            uint32_t w = 0;
+            for (int i = 0; i < nf; ++i) w |= (uint32_t)(__ldg(G.synd + (int64_t)(f0 + i) * M + c) & 1) << i;
+            sw[c] = w;
+        }
+        if (tid == 0) {
+            s_active = nf == 32 ? 0xffffffffu : ((1u << nf) - 1u);
+            s_unsat = 0;
+        }
+        __syncthreads();
+        // ---- stopping test of the tile's current posteriors: bit i of s_unsat
+        auto parity = [&]() {
+            uint32_t bad = 0;
+            if (fl < nf) {
+                for (int c = warp * slots + slot; c < M; c += nwarps * slots) {
+                    uint32_t par = (sw[c] >> fl) & 1u;
+                    for (int32_t e = __ldg(G.rp + c), ee = __ldg(G.rp + c + 1); e < ee; ++e)
+                        par ^= (uint32_t)(L[(int64_t)__ldg(G.ci + e) * FT + fl] < 0.0f);
+                    bad |= par;
+                }
+            }
+            if (bad) atomicOr(&s_unsat, 1u << fl);
+        };
+        // retire the frames whose test passed (iterations executed: t)
+        auto retire = [&](int t) {
+            __syncthreads();
+            if (tid < nf) {
+                const bool was = (s_active >> tid) & 1u;
+                const bool ok = !((s_unsat >> tid) & 1u);
+                if (was && ok) G.iters[f0 + tid] = t;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_active &= s_unsat;   // still decoding: active and unsatisfied
+                s_unsat = 0;
+            }
+            __syncthreads();
+        };
+        if (a.early_stop) {
+            parity();
+            retire(0);
+        }
+        for (int t = 1; t <= a.max_iter; ++t) {
+            if (s_active == 0) break;
+            for (int ly = 0; ly < G.n_layers; ++ly) {
+                const int32_t lb = __ldg(G.lptr + ly), le = __ldg(G.lptr + ly + 1);
+                const bool live = fl < nf && ((s_active >> fl) & 1u);
+                for (int32_t kk = lb + warp * slots + slot; live && kk < le; kk += nwarps * slots) {
+                    const int32_t c = __ldg(G.lchk + kk);
+                    const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
+                    uint32_t neg = (sw[c] >> fl) & 1u;
+                    float mn1 = INFINITY, mn2 = INFINITY;
+                    int32_t arg = -1;
+                    units += d;
+                    for (int k0 = 0; k0 < d; k0 += CH) {
+                        float Lv[CH], mo[CH];
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) {
+                            const int32_t e = beg + min(k0 + j, d - 1);
+                            Lv[j] = L[(int64_t)__ldg(G.ci + e) * FT + fl];
+                            mo[j] = msg[(int64_t)e * FT + fl];
+                        }
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) {
+                            const int k = k0 + j;
+                            if (k >= d) break;
+                            const float q = Lv[j] - mo[j];
+                            if (k < kStash) my[k * 32] = q;
+                            neg ^= (uint32_t)(q < 0.0f);
+                            const float m = fabsf(q);
+                            if (m < mn1) { mn2 = mn1; mn1 = m; arg = k; }
+                            else if (m < mn2) mn2 = m;
+                        }
+                    }
+                    for (int k = 0; k < d; ++k) {
+                        const int32_t e = beg + k;
+                        const int32_t col = __ldg(G.ci + e);
+                        // edges beyond the stash: L and m of this edge are still unchanged
+                        const float q = k < kStash ? my[k * 32] : L[(int64_t)col * FT + fl] - msg[(int64_t)e * FT + fl];
+                        const float mag = fmaxf(((k == arg) ? mn2 : mn1) - a.beta, 0.0f);
+                        const float mn = ((neg ^ (uint32_t)(q < 0.0f)) & 1u) ? -mag : mag;
+                        msg[(int64_t)e * FT + fl] = mn;
+                        L[(int64_t)col * FT + fl] = q + mn;
+                    }
+                }
+                __syncthreads();
+            }
+            if (a.early_stop || t == a.max_iter) {
+                parity();
+                retire(t);
+            }
+        }
+        if (!a.early_stop && a.max_iter == 0) {
+            parity();
+            retire(0);
+        }
+        // ---- outputs: frames still active never satisfied the syndrome
+        if (tid < nf) {
+            const bool act = (s_active >> tid) & 1u;
+            G.conv[f0 + tid] = act ? 0 : 1;
+            if (act) G.iters[f0 + tid] = a.max_iter;
+        }
+        for (int64_t idx = tid; idx < (int64_t)nf * n; idx += blockDim.x) {
+            const int i = (int)(idx / n), v = (int)(idx - (int64_t)i * n);
+            G.bits[(int64_t)(f0 + i) * n + v] = L[(int64_t)v * FT + i] < 0.0f ? 1 : 0;
+        }
+        __syncthreads();
+    }
+    prof_add(a.prof, units, units * 16);
+}
+
+}  // namespace qkd
+
+// ------------------------------------------------------------------ host side
+struct qkdrec_plan_s {
+    std::vector<qkdrec_group> groups;
+    qkdrec_decode_opts opts;
+    qkdrec_tuning tuning;
+    int32_t *d_head = nullptr;
+    qkd::PlanGroup *d_groups = nullptr;
+    qkd::PlanItem *d_items = nullptr;
+    int32_t n_items = 0;
+    size_t ws_needed = 0;      // for the current tuning
+    size_t ws_max = 0;         // over every tuning the autotuner may pick
+};
+
+namespace qkd {
+
+static const int kPlanFT[] = {8, 16, 32};
+static const int kPlanThreads[] = {128, 256, 512};
+static const int kPlanDepth[] = {2, 4, 8};
+
+static bool tuning_ok(const qkdrec_tuning &t) {
+    auto in = [](int v, const int *set) { return v == set[0] || v == set[1] || v == set[2]; };
+    return in(t.frames_per_cta, kPlanFT) && in(t.threads_per_cta, kPlanThreads) && in(t.stage_depth, kPlanDepth);
+}
+
+static size_t plan_ws_bytes(const std::vector<qkdrec_group> &gs, int FT) {
+    size_t total = 0;
+    for (const qkdrec_group &g : gs) {
+        const CodeDev &d = g.code->d;
+        total += (size_t)ceil_div(g.frames, FT) * (size_t)plan_tile_bytes(d.n, d.E, d.M, FT);
+    }
+    return total;
+}
+
+// (Re)build the device tables for the plan's current tuning (synchronous).
+static qkdrec_status plan_build(qkdrec_plan_s &p) {
+    const int FT = p.tuning.frames_per_cta;
+    std::vector<PlanGroup> hg(p.groups.size());
+    std::vector<PlanItem> items;
+    std::vector<double> cost;
+    int64_t off = 0;
+    for (size_t i = 0; i < p.groups.size(); ++i) {
+        const qkdrec_group &g = p.groups[i];
+        const CodeDev &d = g.code->d;
+        PlanGroup &G = hg[i];
+        G.rp = d.rp;
+        G.ci = d.ci;
+        G.lptr = d.layer_ptr;
+        G.lchk = d.layer_chk;
+        G.llr = g.llr;
+        G.synd = g.synd;
+        G.bits = g.bits_out;
+        G.iters = g.iters_out;
+        G.conv = g.conv_out;
+        G.ws_off = off;
+        G.tile_bytes = plan_tile_bytes(d.n, d.E, d.M, FT);
+        G.E = d.E;
+        G.n = d.n;
+        G.M = d.M;
+        G.n_layers = d.n_layers;
+        G.F = g.frames;
+        G.dc_max = d.dc_max;
+        const int tiles = (int)ceil_div(g.frames, FT);
+        for (int t = 0; t < tiles; ++t) {
+            items.push_back(PlanItem{(int32_t)i, t});
+            cost.push_back((double)d.E * (double)std::min(FT, g.frames - t * FT) + 1e-3 * (double)d.n_layers);
+        }
+        off += (int64_t)tiles * G.tile_bytes;
+    }
+    // longest first: the queue hands out the expensive tiles early
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<PlanItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    cudaFree(p.d_groups);
+    cudaFree(p.d_items);
+    p.d_groups = nullptr;
+    p.d_items = nullptr;
+    QKD_CUDA(cudaMalloc(&p.d_groups, sizeof(PlanGroup) * std::max<size_t>(hg.size(), 1)));
+    QKD_CUDA(cudaMalloc(&p.d_items, sizeof(PlanItem) * std::max<size_t>(sorted.size(), 1)));
+    if (!hg.empty())
+        QKD_CUDA(cudaMemcpy(p.d_groups, hg.data(), sizeof(PlanGroup) * hg.size(), cudaMemcpyHostToDevice));
+    if (!sorted.empty())
+        QKD_CUDA(cudaMemcpy(p.d_items, sorted.data(), sizeof(PlanItem) * sorted.size(), cudaMemcpyHostToDevice));
+    p.n_items = (int32_t)sorted.size();
+    p.ws_needed = (size_t)off;
+    return QKDREC_OK;
+}
+
+static qkdrec_status plan_launch(const qkdrec_plan_s &p, void *ws, size_t bytes, cudaStream_t st) {
+    if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) QKD_FAIL(QKDREC_ERR_ARG, "workspace NULL or not 256-byte aligned");
+    if (bytes < p.ws_needed) QKD_FAIL(QKDREC_ERR_ARG, "workspace %zu < %zu bytes", bytes, p.ws_needed);
+    if (p.n_items == 0) return QKDREC_OK;
+    PlanArgs a;
+    a.groups = p.d_groups;
+    a.items = p.d_items;
+    a.n_items = p.n_items;
+    a.head = p.d_head;
+    a.ws = reinterpret_cast<char *>(ws);
+    a.FT = p.tuning.frames_per_cta;
+    a.max_iter = p.opts.max_iter;
+    a.early_stop = p.opts.early_stop ? 1 : 0;
+    a.beta = p.opts.offset;
+    a.prof = prof::counters(prof::kPlan);
+    QKD_CUDA(cudaMemsetAsync(p.d_head, 0, sizeof(int32_t), st));
+    const int threads = p.tuning.threads_per_cta;
+    const size_t stash = (size_t)(threads / 32) * kStash * 32 * sizeof(float);
+    // 512 threads need 64 KB of dynamic shared memory (above the default 48 KB)
+    static bool attr_set = false;
+    if (!attr_set) {
+        const int lim = (int)((size_t)(512 / 32) * kStash * 32 * sizeof(float));
+        cudaFuncSetAttribute(plan_layered_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(plan_layered_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(plan_layered_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        attr_set = true;
+    }
+    int per_sm = 0;
+    switch (p.tuning.stage_depth) {
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<2>, threads, stash); break;
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<4>, threads, stash); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<8>, threads, stash); break;
+    }
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, p.n_items);
+    prof::Scope ps(prof::kPlan, st);
+    switch (p.tuning.stage_depth) {
+        case 2: plan_layered_kernel<2><<<grid, threads, stash, st>>>(a); break;
+        case 4: plan_layered_kernel<4><<<grid, threads, stash, st>>>(a); break;
+        default: plan_layered_kernel<8><<<grid, threads, stash, st>>>(a); break;
+    }
+    QKD_LAUNCHED("plan_layered_kernel");
+    return QKDREC_OK;
+}
+
+}  // namespace qkd
+
+extern "C" {
+
+void qkdrec_tuning_default(qkdrec_tuning *t) {
+    if (!t) return;
+    t->frames_per_cta = 32;
+    t->threads_per_cta = 256;
+    t->stage_depth = 8;
+}
+
+qkdrec_status qkdrec_plan_create(const qkdrec_group *groups, int32_t n_groups, const qkdrec_decode_opts *opts,
+                                 const qkdrec_tuning *tuning, qkdrec_plan_t *out) {
+    clear_error();
+    if (!out) QKD_FAIL(QKDREC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_groups < 0 || (n_groups > 0 && !groups)) QKD_FAIL(QKDREC_ERR_ARG, "bad group list");
+    if (!opts_ok(opts)) QKD_FAIL(QKDREC_ERR_ARG, "bad decode options");
+    if (opts->algo != QKDREC_OMS_LAYERED || opts->prec != QKDREC_F32)
+        QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "batched plans decode with FP32 layered offset min-sum");
+    qkdrec_tuning tu;
+    qkdrec_tuning_default(&tu);
+    if (tuning) tu = *tuning;
+    if (!tuning_ok(tu)) QKD_FAIL(QKDREC_ERR_ARG, "tuning outside the supported sets");
+    for (int32_t i = 0; i < n_groups; ++i) {
+        const qkdrec_group &g = groups[i];
+        if (!g.code || g.frames < 0) QKD_FAIL(QKDREC_ERR_ARG, "group %d: NULL code or frames < 0", i);
+        if (g.frames > 0 && (!g.llr || !g.synd || !g.bits_out || !g.iters_out || !g.conv_out))
+            QKD_FAIL(QKDREC_ERR_ARG, "group %d: NULL input/output", i);
+    }
+    qkdrec_plan_s *p = new (std::nothrow) qkdrec_plan_s();
+    if (!p) QKD_FAIL(QKDREC_ERR_NOMEM, "host allocation");
+    p->groups.assign(groups, groups + n_groups);
+    p->opts = *opts;
+    p->tuning = tu;
+    cudaError_t e = cudaMalloc(&p->d_head, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        delete p;
+        QKD_FAIL(QKDREC_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    for (int ft : kPlanFT) p->ws_max = std::max(p->ws_max, plan_ws_bytes(p->groups, ft));
+    qkdrec_status s = plan_build(*p);
+    if (s != QKDREC_OK) {
+        cudaFree(p->d_head);
+        cudaFree(p->d_groups);
+        cudaFree(p->d_items);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return QKDREC_OK;
+}
+
+void qkdrec_plan_destroy(qkdrec_plan_t p) {
+    if (!p) return;
+    cudaFree(p->d_head);
+    cudaFree(p->d_groups);
+    cudaFree(p->d_items);
+    delete p;
+}
+
+qkdrec_status qkdrec_plan_workspace_size(qkdrec_plan_t p, size_t *bytes) {
+    clear_error();
+    if (!p || !bytes) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    *bytes = std::max<size_t>(p->ws_max, 256);
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_plan_launch(qkdrec_plan_t p, void *workspace, size_t workspace_bytes, void *stream) {
+    clear_error();
+    if (!p) QKD_FAIL(QKDREC_ERR_ARG, "plan is NULL");
+    return plan_launch(*p, workspace, workspace_bytes, as_stream(stream));
+}
+
+qkdrec_status qkdrec_plan_get_tuning(qkdrec_plan_t p, qkdrec_tuning *out) {
+    clear_error();
+    if (!p || !out) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    *out = p->tuning;
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_plan_autotune(qkdrec_plan_t p, void *workspace, size_t workspace_bytes, int32_t max_iter,
+                                   void *stream, qkdrec_tuning *best_out, float *best_ms) {
+    clear_error();
+    if (!p) QKD_FAIL(QKDREC_ERR_ARG, "plan is NULL");
+    if (workspace_bytes < p->ws_max) QKD_FAIL(QKDREC_ERR_ARG, "workspace %zu < %zu bytes", workspace_bytes, p->ws_max);
+    cudaStream_t st = as_stream(stream);
+    const qkdrec_decode_opts keep = p->opts;
+    if (max_iter > 0) p->opts.max_iter = std::min(max_iter, keep.max_iter);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QKD_CUDA(cudaEventCreate(&e0));
+    QKD_CUDA(cudaEventCreate(&e1));
+    qkdrec_tuning best = p->tuning;
+    float best_t = INFINITY;
+    qkdrec_status s = QKDREC_OK;
+    for (int ft : kPlanFT) {
+        p->tuning.frames_per_cta = ft;
+        if ((s = plan_build(*p)) != QKDREC_OK) break;
+        for (int th : kPlanThreads)
+            for (int dep : kPlanDepth) {
+                p->tuning.threads_per_cta = th;
+                p->tuning.stage_depth = dep;
+                if ((s = plan_launch(*p, workspace, workspace_bytes, st)) != QKDREC_OK) break;  // warm-up
+                cudaEventRecord(e0, st);
+                if ((s = plan_launch(*p, workspace, workspace_bytes, st)) != QKDREC_OK) break;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_t) {
+                    best_t = ms;
+                    best = p->tuning;
+                }
+            }
+        if (s != QKDREC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->opts = keep;
+    p->tuning = best;
+    qkdrec_status s2 = plan_build(*p);
+    if (s != QKDREC_OK) return s;
+    if (s2 != QKDREC_OK) return s2;
+    QKD_CUDA(cudaStreamSynchronize(st));
+    if (best_out) *best_out = best;
+    if (best_ms) *best_ms = best_t;
+    return QKDREC_OK;
+}
+
+}  // extern "C"

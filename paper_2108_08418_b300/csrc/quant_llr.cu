@@ -110,6 +110,67 @@ __device__ __forceinline__ double lp_interval64(const LlrParams &p, int k, doubl
     return logp64((p.td[k] - x) * p.inv_sigma_d, (p.td[k + 1] - x) * p.inv_sigma_d);
 }
 
+// LLR of one sample (x, reconciled lower bits `low`) with the tables of p.
+__device__ __forceinline__ float llr_one(const LlrParams &p, float x, int low) {
+    const int nc = p.K >> p.j;  // candidates consistent with the lower bits
+    const float lg_half_n = logf(0.5f * (float)nc);   // log |K_b|
+    // nearest candidate of each set
+    float dmin[2] = {INFINITY, INFINITY};
+    int kmin[2] = {0, 0};
+    for (int u = 0; u < nc; ++u) {
+        const int k = p.k_of_label[(u << p.j) | low];
+        const float d = interval_dist(p, k, x);
+        const int b = u & 1;
+        if (d < dmin[b]) { dmin[b] = d; kmin[b] = k; }
+    }
+    const float lpn0 = lp_interval32(p, kmin[0], x), lpn1 = lp_interval32(p, kmin[1], x);
+    // a set whose whole mass is provably more than the clip below the other's
+    // nearest term cannot move the clipped result
+    const float ub0 = lg_half_n + (dmin[0] > 0.0f ? kLn05 - 0.5f * dmin[0] * dmin[0] : 0.0f);
+    const float ub1 = lg_half_n + (dmin[1] > 0.0f ? kLn05 - 0.5f * dmin[1] * dmin[1] : 0.0f);
+    float llr;
+    if (ub1 < lpn0 - kLlrClip) {
+        llr = kLlrClip;
+    } else if (ub0 < lpn1 - kLlrClip) {
+        llr = -kLlrClip;
+    } else if (fmaxf(lpn0, lpn1) >= -kFarNats) {
+        // FP32: sums relative to each set's nearest term
+        float s0 = 1.0f, s1 = 1.0f;
+        for (int u = 0; u < nc; ++u) {
+            const int k = p.k_of_label[(u << p.j) | low];
+            const int b = u & 1;
+            if (k == kmin[b]) continue;
+            const float d = interval_dist(p, k, x);
+            const float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
+            const float ref = b ? lpn1 : lpn0;
+            if (bound < ref - kSkipNats) continue;
+            const float t = expf(lp_interval32(p, k, x) - ref);
+            if (b) s1 += t;
+            else s0 += t;
+        }
+        llr = (lpn0 + logf(s0)) - (lpn1 + logf(s1));
+    } else {
+        // far Gaussian tails of both sets (x beyond e^-50 of every candidate):
+        // the log-probabilities are large, so the difference is formed in FP64
+        const double xd = (double)x;
+        const double r0 = lp_interval64(p, kmin[0], xd), r1 = lp_interval64(p, kmin[1], xd);
+        double s0 = 1.0, s1 = 1.0;
+        for (int u = 0; u < nc; ++u) {
+            const int k = p.k_of_label[(u << p.j) | low];
+            const int b = u & 1;
+            if (k == kmin[b]) continue;
+            const float d = interval_dist(p, k, x);
+            const float bound = kLn05 - 0.5f * d * d;
+            if (bound < (b ? lpn1 : lpn0) - kSkipNats) continue;
+            const double t = exp(lp_interval64(p, k, xd) - (b ? r1 : r0));
+            if (b) s1 += t;
+            else s0 += t;
+        }
+        llr = (float)((r0 + log(s0)) - (r1 + log(s1)));
+    }
+    return fminf(fmaxf(llr, -kLlrClip), kLlrClip);
+}
+
 __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
                                  const uint8_t *__restrict__ lower, const LlrParams p_in,
                                  float *__restrict__ out, unsigned long long *prof) {
@@ -124,72 +185,83 @@ __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
     __syncthreads();
     const LlrParams &p = sp;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int nc = p.K >> p.j;  // candidates consistent with the lower bits
-    const float lg_half_n = logf(0.5f * (float)nc);   // log |K_b|
     unsigned long long units = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
         ++units;
-        const float x = xs[i];
         int low = 0;
         for (int b = 0; b < p.j; ++b) low |= (int)(lower[(int64_t)b * count + i] & 1) << b;
-        // nearest candidate of each set
-        float dmin[2] = {INFINITY, INFINITY};
-        int kmin[2] = {0, 0};
-        for (int u = 0; u < nc; ++u) {
-            const int k = p.k_of_label[(u << p.j) | low];
-            const float d = interval_dist(p, k, x);
-            const int b = u & 1;
-            if (d < dmin[b]) { dmin[b] = d; kmin[b] = k; }
-        }
-        const float lpn0 = lp_interval32(p, kmin[0], x), lpn1 = lp_interval32(p, kmin[1], x);
-        // a set whose whole mass is provably more than the clip below the other's
-        // nearest term cannot move the clipped result
-        const float ub0 = lg_half_n + (dmin[0] > 0.0f ? kLn05 - 0.5f * dmin[0] * dmin[0] : 0.0f);
-        const float ub1 = lg_half_n + (dmin[1] > 0.0f ? kLn05 - 0.5f * dmin[1] * dmin[1] : 0.0f);
-        float llr;
-        if (ub1 < lpn0 - kLlrClip) {
-            llr = kLlrClip;
-        } else if (ub0 < lpn1 - kLlrClip) {
-            llr = -kLlrClip;
-        } else if (fmaxf(lpn0, lpn1) >= -kFarNats) {
-            // FP32: sums relative to each set's nearest term
-            float s0 = 1.0f, s1 = 1.0f;
-            for (int u = 0; u < nc; ++u) {
-                const int k = p.k_of_label[(u << p.j) | low];
-                const int b = u & 1;
-                if (k == kmin[b]) continue;
-                const float d = interval_dist(p, k, x);
-                const float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
-                const float ref = b ? lpn1 : lpn0;
-                if (bound < ref - kSkipNats) continue;
-                const float t = expf(lp_interval32(p, k, x) - ref);
-                if (b) s1 += t;
-                else s0 += t;
-            }
-            llr = (lpn0 + logf(s0)) - (lpn1 + logf(s1));
-        } else {
-            // far Gaussian tails of both sets (x beyond e^-50 of every candidate):
-            // the log-probabilities are large, so the difference is formed in FP64
-            const double xd = (double)x;
-            const double r0 = lp_interval64(p, kmin[0], xd), r1 = lp_interval64(p, kmin[1], xd);
-            double s0 = 1.0, s1 = 1.0;
-            for (int u = 0; u < nc; ++u) {
-                const int k = p.k_of_label[(u << p.j) | low];
-                const int b = u & 1;
-                if (k == kmin[b]) continue;
-                const float d = interval_dist(p, k, x);
-                const float bound = kLn05 - 0.5f * d * d;
-                if (bound < (b ? lpn1 : lpn0) - kSkipNats) continue;
-                const double t = exp(lp_interval64(p, k, xd) - (b ? r1 : r0));
-                if (b) s1 += t;
-                else s0 += t;
-            }
-            llr = (float)((r0 + log(s0)) - (r1 + log(s1)));
-        }
-        out[i] = fminf(fmaxf(llr, -kLlrClip), kLlrClip);
+        out[i] = llr_one(p, xs[i], low);
     }
     // x and the lower bits read, the LLR written
     prof_add(prof, units, units * (8 + p.j));
+}
+
+// ------------------------------------------- frames with their own parameters
+// One block per frame: the block builds the frame's tables (thresholds from its
+// quantiser range, its noise level) in shared memory, then walks its samples.
+__global__ void quantise_frames_kernel(const float *__restrict__ y, const int64_t *__restrict__ off,
+                                       const double *__restrict__ par, int64_t count, int32_t m, int32_t gray,
+                                       uint8_t *__restrict__ idx_out, uint8_t *__restrict__ bits_out,
+                                       unsigned long long *prof) {
+    __shared__ float tf[kMaxK];
+    __shared__ uint8_t lab_s[kMaxK];
+    const int K = 1 << m;
+    unsigned long long units = 0;
+    const int64_t f = blockIdx.x;
+    const double lo = par[2 * f], hi = par[2 * f + 1], delta = (hi - lo) / K;
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        // rounded like the host tables (no fused multiply-add): smallest float >= t_k
+        if (t >= 1) tf[t - 1] = __double2float_ru(__dadd_rn(lo, __dmul_rn(delta, (double)t)));
+        lab_s[t] = (uint8_t)(gray ? (t ^ (t >> 1)) : t);
+    }
+    __syncthreads();
+    const int64_t ib = max(off[f], (int64_t)0), ie = min(off[f + 1], count);
+    for (int64_t i = ib + threadIdx.x; i < ie; i += blockDim.x) {
+        ++units;
+        const float v = y[i];
+        int k = 0;
+        for (int s = K >> 1; s >= 1; s >>= 1)
+            if (!(v < tf[k + s - 1])) k += s;
+        if (idx_out) idx_out[i] = (uint8_t)k;
+        if (bits_out) {
+            const int lab = lab_s[k];
+            for (int j = 0; j < m; ++j) bits_out[(int64_t)j * count + i] = (uint8_t)((lab >> j) & 1);
+        }
+    }
+    prof_add(prof, units, units * (4 + (idx_out ? 1 : 0) + (bits_out ? m : 0)));
+}
+
+__global__ void slice_llr_frames_kernel(const float *__restrict__ xs, const int64_t *__restrict__ off,
+                                        const double *__restrict__ par, int64_t count, int32_t m, int32_t j,
+                                        int32_t gray, const uint8_t *__restrict__ lower, float *__restrict__ out,
+                                        unsigned long long *prof) {
+    __shared__ LlrParams sp;
+    const int64_t f = blockIdx.x;
+    const int K = 1 << m;
+    const double lo = par[3 * f], hi = par[3 * f + 1], sn = par[3 * f + 2], delta = (hi - lo) / K;
+    for (int t = threadIdx.x; t <= K; t += blockDim.x) {
+        const double td = t == 0 ? -INFINITY : (t == K ? INFINITY : __dadd_rn(lo, __dmul_rn(delta, (double)t)));
+        sp.td[t] = td;
+        sp.tf[t] = (float)td;
+        if (t < K) sp.k_of_label[gray ? (t ^ (t >> 1)) : t] = (uint8_t)t;
+    }
+    if (threadIdx.x == 0) {
+        sp.inv_sigma = (float)(1.0 / sn);
+        sp.inv_sigma_d = 1.0 / sn;
+        sp.m = m;
+        sp.K = K;
+        sp.j = j;
+    }
+    __syncthreads();
+    unsigned long long units = 0;
+    const int64_t ib = max(off[f], (int64_t)0), ie = min(off[f + 1], count);
+    for (int64_t i = ib + threadIdx.x; i < ie; i += blockDim.x) {
+        ++units;
+        int low = 0;
+        for (int b = 0; b < j; ++b) low |= (int)(lower[(int64_t)b * count + i] & 1) << b;
+        out[i] = llr_one(sp, xs[i], low);
+    }
+    prof_add(prof, units, units * (8 + j));
 }
 
 static int label_of(int k, qkdrec_label lab) { return lab == QKDREC_LABEL_BINARY ? k : (k ^ (k >> 1)); }
@@ -265,6 +337,44 @@ qkdrec_status qkdrec_slice_llr(const float *x, int64_t count, int32_t m, int32_t
     slice_llr_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(x, count, lower_bits, p, llr_out,
                                                                               prof::counters(prof::kSliceLlr));
     QKD_LAUNCHED("slice_llr_kernel");
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_quantise_slices_frames(const float *y, int64_t count, const int64_t *frame_offsets,
+                                            const double *frame_ranges, int32_t F, int32_t m, qkdrec_label label,
+                                            uint8_t *idx_out, uint8_t *bits_out, void *stream) {
+    clear_error();
+    if (count < 0 || F < 0) QKD_FAIL(QKDREC_ERR_ARG, "count/F < 0");
+    if (m < 1 || m > kMaxM) QKD_FAIL(QKDREC_ERR_ARG, "m_slices=%d outside [1, %d]", m, kMaxM);
+    if (label != QKDREC_LABEL_GRAY && label != QKDREC_LABEL_BINARY) QKD_FAIL(QKDREC_ERR_ARG, "bad label");
+    if (F == 0 || count == 0) return QKDREC_OK;
+    if (!y || !frame_offsets || !frame_ranges) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    if (F > 2147483647) QKD_FAIL(QKDREC_ERR_ARG, "too many frames");
+    prof::Scope ps(prof::kQuantise, as_stream(stream));
+    quantise_frames_kernel<<<(unsigned)F, 256, 0, as_stream(stream)>>>(
+        y, frame_offsets, frame_ranges, count, m, label == QKDREC_LABEL_GRAY, idx_out, bits_out,
+        prof::counters(prof::kQuantise));
+    QKD_LAUNCHED("quantise_frames_kernel");
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_slice_llr_frames(const float *x, int64_t count, const int64_t *frame_offsets,
+                                      const double *frame_params, int32_t F, int32_t m, int32_t j,
+                                      qkdrec_label label, const uint8_t *lower_bits, float *llr_out,
+                                      void *stream) {
+    clear_error();
+    if (count < 0 || F < 0) QKD_FAIL(QKDREC_ERR_ARG, "count/F < 0");
+    if (m < 1 || m > kMaxM) QKD_FAIL(QKDREC_ERR_ARG, "m_slices=%d outside [1, %d]", m, kMaxM);
+    if (j < 0 || j >= m) QKD_FAIL(QKDREC_ERR_ARG, "slice j=%d outside [0, %d)", j, m);
+    if (label != QKDREC_LABEL_GRAY && label != QKDREC_LABEL_BINARY) QKD_FAIL(QKDREC_ERR_ARG, "bad label");
+    if (F == 0 || count == 0) return QKDREC_OK;
+    if (!x || !frame_offsets || !frame_params || !llr_out) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    if (j > 0 && !lower_bits) QKD_FAIL(QKDREC_ERR_ARG, "lower_bits NULL for j=%d", j);
+    prof::Scope ps(prof::kSliceLlr, as_stream(stream));
+    slice_llr_frames_kernel<<<(unsigned)F, 256, 0, as_stream(stream)>>>(
+        x, frame_offsets, frame_params, count, m, j, label == QKDREC_LABEL_GRAY, lower_bits, llr_out,
+        prof::counters(prof::kSliceLlr));
+    QKD_LAUNCHED("slice_llr_frames_kernel");
     return QKDREC_OK;
 }
 

@@ -1,0 +1,187 @@
+"""Reverse reconciliation of an uneven batch of frames as one CUDA graph.
+
+Each frame f has its own length n_f and SNR, hence its own quantiser range
+[-4 sigma_y, 4 sigma_y], noise level sigma_n = SNR^-1/2 and per-slice code
+rates (Sec. III-A: the rate of slice j follows its conditional capacity; a
+slice whose rate is 0 is disclosed).  One step of the batch:
+
+  Bob    quantise every frame with its range into m slices (Sec. III-A), then
+         the syndrome of every decoded (frame, slice) with the code of its
+         (n_f, rate) (Sec. II, step 5);
+  Alice  for j = 0 .. m-1: the slice-j LLRs of every frame from x and the
+         already reconciled slices 0..j-1 (Sec. III-B, multi-stage decoding),
+         then ONE persistent plan launch decoding every frame of slice j
+         (layered offset min-sum, per-frame stopping test), then the
+         disclosed frames of slice j copied in the clear.
+
+Groups of a slice's plan are runs of consecutive frames sharing (n, rate):
+order the frames by (n, SNR) so that the runs are long.  All buffers are
+allocated once here, so `step` allocates nothing and the whole step can be
+captured in a CUDA graph (`capture`) and replayed with new x, y written into
+the `x` and `y` tensors in place.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import DecodeOpts, Plan, qkdrec_quantise_slices_frames, qkdrec_slice_llr_frames, qkdrec_syndrome
+from . import quantiser_range
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class UnevenBatch:
+    """lengths int [F] (samples per frame, in sample order); snrs float [F];
+    rates float [m][F] (0 = the slice of that frame is disclosed); codes: dict
+    (n, rate) -> Code for every decoded (n_f, rates[j][f]) pair."""
+
+    def __init__(self, lengths, snrs, rates, codes, m_slices: int = 5, label: str = "gray",
+                 max_iter: int = 50, offset: float = 0.5, tuning: dict | None = None, device="cuda",
+                 va: float = 1.0):
+        torch = _torch()
+        self.lengths = np.asarray(lengths, dtype=np.int64)
+        self.snrs = np.asarray(snrs, dtype=np.float64)
+        self.rates = np.asarray(rates, dtype=np.float64).reshape(m_slices, -1)
+        F = self.F = self.lengths.size
+        if self.snrs.size != F or self.rates.shape[1] != F:
+            raise ValueError("lengths, snrs and rates[j] must have one entry per frame")
+        self.m, self.label = int(m_slices), label
+        self.device = torch.device(device)
+        off = np.concatenate([[0], np.cumsum(self.lengths)]).astype(np.int64)
+        self.offsets = off
+        self.count = int(off[-1])
+        rng = np.array([quantiser_range(s, va) for s in self.snrs], dtype=np.float64).reshape(F, 2)
+        par = np.concatenate([rng, (self.snrs ** -0.5)[:, None]], axis=1)
+        dev = self.device
+        self.d_off = torch.from_numpy(off).to(dev)
+        self.d_ranges = torch.from_numpy(np.ascontiguousarray(rng)).to(dev)
+        self.d_params = torch.from_numpy(np.ascontiguousarray(par)).to(dev)
+        self.x = torch.zeros(self.count, dtype=torch.float32, device=dev)
+        self.y = torch.zeros(self.count, dtype=torch.float32, device=dev)
+        self.bob = torch.zeros((self.m, self.count), dtype=torch.uint8, device=dev)
+        self.alice = torch.zeros((self.m, self.count), dtype=torch.uint8, device=dev)
+        self.llr = torch.zeros(self.count, dtype=torch.float32, device=dev)
+        self.iters = torch.zeros((self.m, F), dtype=torch.int32, device=dev)
+        self.conv = torch.ones((self.m, F), dtype=torch.uint8, device=dev)
+        self.opts = DecodeOpts(algo="oms_layered", prec="f32", max_iter=max_iter, offset=offset, early_stop=True)
+        self.codes = codes
+        # per slice: groups (runs of frames with one code) and disclosed sample ranges
+        self.groups, self.disclosed, self.synd, self.plans = [], [], [], []
+        for j in range(self.m):
+            runs, opened = [], []
+            f = 0
+            while f < F:
+                key = (int(self.lengths[f]), float(self.rates[j, f]))
+                g = f + 1
+                while g < F and (int(self.lengths[g]), float(self.rates[j, g])) == key:
+                    g += 1
+                if key[1] <= 0:
+                    opened.append((int(off[f]), int(off[g])))
+                else:
+                    if key not in codes:
+                        raise KeyError(f"no code for (n, rate) = {key}")
+                    runs.append((f, g, codes[key]))
+                f = g
+            total = sum((g - f) * c.M for f, g, c in runs)
+            synd = torch.zeros(max(total, 1), dtype=torch.uint8, device=dev)
+            groups, so = [], 0
+            for f, g, c in runs:
+                nf = g - f
+                a, b = int(off[f]), int(off[g])
+                groups.append(dict(code=c, f0=f, f1=g, a=a, b=b,
+                                   llr=self.llr[a:b].view(nf, c.n), bits=self.alice[j, a:b].view(nf, c.n),
+                                   synd=synd[so:so + nf * c.M].view(nf, c.M),
+                                   iters=self.iters[j, f:g], conv=self.conv[j, f:g]))
+                so += nf * c.M
+            self.groups.append(groups)
+            self.disclosed.append(opened)
+            self.synd.append(synd)
+            self.plans.append(Plan(groups, self.opts, tuning))
+        self.ws = torch.empty(max(p.workspace_size() for p in self.plans), dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    # ------------------------------------------------------------------ run
+    def step(self):
+        """Enqueue one reconciliation of the batch in `x`, `y` on the current stream."""
+        qkdrec_quantise_slices_frames(self.y, self.d_off, self.d_ranges, self.m, self.label, want_idx=False,
+                                      bits_out=self.bob)
+        for j in range(self.m):
+            for g in self.groups[j]:
+                nf, n = g["f1"] - g["f0"], g["code"].n
+                qkdrec_syndrome(g["code"], self.bob[j, g["a"]:g["b"]].view(nf, n), out=g["synd"])
+        for j in range(self.m):
+            qkdrec_slice_llr_frames(self.x, self.d_off, self.d_params, self.m, j,
+                                    self.alice[:j] if j else None, self.label, out=self.llr)
+            self.plans[j].launch(self.ws)
+            for a, b in self.disclosed[j]:
+                self.alice[j, a:b].copy_(self.bob[j, a:b])
+
+    def autotune(self, max_iter: int = 10):
+        """Pick each slice plan's fastest tuning on the batch now in x, y (synchronous)."""
+        torch = _torch()
+        out = []
+        self.step()
+        torch.cuda.synchronize(self.device)
+        for j, p in enumerate(self.plans):
+            # the plan of slice j decodes the LLRs of slice j: recompute them first
+            qkdrec_slice_llr_frames(self.x, self.d_off, self.d_params, self.m, j, self.alice[:j] if j else None,
+                                    self.label, out=self.llr)
+            out.append(p.autotune(self.ws, max_iter))
+            p.launch(self.ws)
+        torch.cuda.synchronize(self.device)
+        self.graph = None
+        return out
+
+    def capture(self):
+        """Capture `step` in a CUDA graph (after one eager step that sets kernel attributes)."""
+        torch = _torch()
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.step()
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step()
+        return self.graph
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    # --------------------------------------------------------------- results
+    def frame_ok(self):
+        """bool [m][F]: Alice's slice equals Bob's (disclosed slices count as equal)."""
+        torch = _torch()
+        ok = torch.ones((self.m, self.F), dtype=torch.bool, device=self.device)
+        f = 0
+        while f < self.F:                       # runs of frames with one length
+            n = int(self.lengths[f])
+            g = f + 1
+            while g < self.F and int(self.lengths[g]) == n:
+                g += 1
+            a, b = int(self.offsets[f]), int(self.offsets[g])
+            if n > 0:
+                ok[:, f:g] = (self.alice[:, a:b] == self.bob[:, a:b]).view(self.m, g - f, n).all(dim=2)
+            f = g
+        return ok
+
+    def reconciled_bits(self):
+        """Bits of decoded (non-disclosed) slices in frames reconciled correctly."""
+        ok = self.frame_ok().cpu().numpy()
+        dec = self.rates > 0
+        return int(np.sum(ok * dec * self.lengths[None, :]))
+
+    def decoded_bits(self):
+        return int(np.sum((self.rates > 0) * self.lengths[None, :]))
+
+    def destroy(self):
+        for p in self.plans:
+            p.destroy()
+        self.plans = []
+        self.graph = None
