@@ -718,7 +718,7 @@ def run_plan_case(args, c):
                            bits=torch.empty_like(bd), iters=torch.empty(F, dtype=torch.int32, device="cuda"),
                            conv=torch.empty(F, dtype=torch.uint8, device="cuda")))
     opts = q.DecodeOpts(algo="oms_layered", prec="f32", max_iter=c["iters"], early_stop=False)
-    plan = q.Plan(groups, opts, dict(frames_per_cta=8, threads_per_cta=512, stage_depth=4))
+    plan = q.Plan(groups, opts, dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=4))
     ws = plan.workspace()
     for _ in range(args.warmup + args.steps):
         plan.launch(ws)

@@ -239,26 +239,31 @@ typedef struct {
 } qkdrec_group;
 
 /* Launch shape of a plan; the autotuner searches all combinations.
- *   frames_per_cta  8, 16 or 32: frames one CTA decodes together (lanes per check)
- *   threads_per_cta 128, 256 or 512
- *   stage_depth     2, 4 or 8: edge loads in flight per lane */
+ *   frames_per_tile 8, 16 or 32: frames decoded together (lanes per check)
+ *   threads_per_cta 256, 512 or 1024
+ *   stage_depth     4 or 8: edge loads in flight per lane
+ *   ctas_per_tile   1, 2, 4 or 8: CTAs of a thread-block cluster sharing one
+ *                   tile (they split each layer's checks and meet at the
+ *                   cluster barrier after every layer) */
 typedef struct {
-    int32_t frames_per_cta;
+    int32_t frames_per_tile;
     int32_t threads_per_cta;
     int32_t stage_depth;
+    int32_t ctas_per_tile;
 } qkdrec_tuning;
 
 typedef struct qkdrec_plan_s *qkdrec_plan_t;
 
-/* Defaults: 32 frames, 256 threads, depth 8. */
+/* Defaults: 32 frames per tile, 512 threads, depth 8, 4 CTAs per tile. */
 void qkdrec_tuning_default(qkdrec_tuning *tuning);
 
 /*
  * Plan the decode of an uneven batch in ONE persistent launch: work items
- * (group, tile of frames_per_cta frames), longest first, taken by CTAs from a
- * device queue (one atomic increment; no CTA waits for another).  Each CTA runs
- * the full layered offset min-sum decode of its tile with the per-frame
- * stopping test.  The plan binds the groups' device pointers (the caller keeps
+ * (group, tile of frames_per_tile frames), longest first, taken from a device
+ * queue (one atomic increment per item) by thread-block clusters of
+ * ctas_per_tile CTAs; no cluster waits for another.  A cluster runs the full
+ * layered offset min-sum decode of its tile (Sec. III-C, layered schedule) with
+ * the per-frame stopping test, its CTAs splitting each layer's checks.  The plan binds the groups' device pointers (the caller keeps
  * those buffers alive and may refill them between launches).  Synchronous;
  * allocates the plan's small device tables.  Only opts->algo OMS_LAYERED with
  * prec F32 is supported (QKDREC_ERR_UNSUPPORTED otherwise).

@@ -60,8 +60,11 @@ class GroupC(ctypes.Structure):
 
 
 class TuningC(ctypes.Structure):
-    _fields_ = [("frames_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("stage_depth", ctypes.c_int32)]
+    _fields_ = [("frames_per_tile", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("stage_depth", ctypes.c_int32), ("ctas_per_tile", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class DecodeOptsC(ctypes.Structure):
@@ -400,7 +403,9 @@ class Plan:
         o = opts.c()
         t = None
         if tuning is not None:
-            t = TuningC(tuning["frames_per_cta"], tuning["threads_per_cta"], tuning["stage_depth"])
+            d = TuningC()
+            lib().qkdrec_tuning_default(ctypes.byref(d))
+            t = TuningC(**{**d.as_dict(), **tuning})
         self._h = ctypes.c_void_p()
         _check(lib().qkdrec_plan_create(arr, len(groups), ctypes.byref(o), ctypes.byref(t) if t else None,
                                         ctypes.byref(self._h)))
@@ -422,7 +427,7 @@ class Plan:
     def tuning(self) -> dict:
         t = TuningC()
         _check(lib().qkdrec_plan_get_tuning(self._h, ctypes.byref(t)))
-        return dict(frames_per_cta=t.frames_per_cta, threads_per_cta=t.threads_per_cta, stage_depth=t.stage_depth)
+        return t.as_dict()
 
     def autotune(self, workspace, max_iter: int = 10):
         torch = _torch()
@@ -431,8 +436,7 @@ class Plan:
         _check(lib().qkdrec_plan_autotune(self._h, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                           int(max_iter), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
                                           ctypes.byref(t), ctypes.byref(ms)))
-        return dict(frames_per_cta=t.frames_per_cta, threads_per_cta=t.threads_per_cta,
-                    stage_depth=t.stage_depth), ms.value
+        return t.as_dict(), ms.value
 
     def destroy(self):
         if self._h:

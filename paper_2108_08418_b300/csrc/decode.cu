@@ -25,6 +25,7 @@
 // Check kernels keep the per-edge state of pass 1 (phi values, or the v->c
 // signs) in registers for checks of degree <= DCMAX, so pass 2 only computes
 // and stores the outgoing messages; larger degrees use a variant that reloads.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include <algorithm>
@@ -257,7 +258,7 @@ __device__ __forceinline__ void publish_unsat(uint32_t bits, int64_t f0, int64_t
 constexpr int kStash = 32;
 
 template <int ALGO, typename MsgT, int V, bool CACHED>
-__global__ void __launch_bounds__(kCheckWarps * 32, 3)
+__global__ void __launch_bounds__(kCheckWarps * 32, (ALGO == kSP && V == 1) ? 4 : 3)
 check_flood_f(DecArgs a) {
     extern __shared__ float stash[];  // SP cached: [kCheckWarps][kStash][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

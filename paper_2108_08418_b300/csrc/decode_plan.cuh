@@ -2,20 +2,30 @@
 // its own code (length n, rate), in one persistent launch (included by decode.cu).
 //
 // The batch is cut into work items (group, tile of FT frames), ordered longest
-// first.  Each CTA takes the next item with one atomic increment of a queue
-// head -- CTAs never wait for each other -- and runs the whole layered offset
-// min-sum decode of its tile: all layers of all iterations with a block
-// barrier between layers, the stopping test after every iteration, frames
-// retiring one by one, the tile leaving early once all its frames are done.
-// Lane layout: lane = slot * FT + frame, so a warp serves 32/FT checks at a
-// time; the q values of a check stay in shared memory between the two passes.
+// first.  A tile is decoded by a thread-block cluster of CS CTAs (CS = 1: one
+// CTA): the cluster's leader takes the next item with one atomic increment of
+// a queue head and hands it to the other CTAs through distributed shared
+// memory; clusters never wait for each other.  The CTAs of the cluster split
+// every layer's checks between their warps and meet at the hardware cluster
+// barrier (release/acquire) after each layer, so one large tile runs on up to
+// 8 SMs while small tiles run on one.  The cluster runs the whole layered
+// offset min-sum decode of its tile: all layers of all iterations, the
+// stopping test after every iteration (per-CTA partial results OR-ed into the
+// leader's shared word), frames retiring one by one, the tile leaving early
+// once all its frames are done.
 //
-// Per tile the workspace holds L [n][FT] and m [E][FT] (frame fastest) and the
-// tile's syndrome bits, one word per check.  The q values of the first kStash
-// edges of a check wait in shared memory between the two passes; the rest are
-// recomputed from L and m, which no other check of the layer touches.
+// Lane layout: lane = slot * FT + frame, so a warp serves 32/FT checks at a
+// time; with FT = 32 every posterior gather and message access of a warp is one
+// 128-byte line.  Per tile the workspace holds L [n][FT] and m [E][FT] (frame
+// fastest) and the tile's syndrome bits, one word per check.  Messages are not
+// cleared: the first iteration reads m = 0 without loading it.  The q values of
+// the first kStash edges of a check wait in shared memory between the two
+// passes; the rest are recomputed from L and m, which no other check of the
+// layer touches.  All posterior and message accesses go through L2 only
+// (ld/st .cg), so what one SM of the cluster wrote is what the others read.
 
 namespace qkd {
+namespace cg = cooperative_groups;
 
 struct PlanGroup {
     const int32_t *rp, *ci, *lptr, *lchk;
@@ -40,7 +50,7 @@ struct PlanArgs {
     int32_t n_items;
     int32_t *head;
     char *ws;
-    int32_t FT, max_iter, early_stop;
+    int32_t FT, CS, max_iter, early_stop;
     float beta;
     unsigned long long *prof;
 };
@@ -50,98 +60,119 @@ static int64_t plan_tile_bytes(int64_t n, int64_t E, int64_t M, int FT) {
            (int64_t)align_up((size_t)M * 4, 256);
 }
 
+// barrier over the CTAs that share a tile
+__device__ __forceinline__ void plan_sync(int CS) {
+    if (CS > 1) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
 template <int CH>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024, 1)
 plan_layered_kernel(PlanArgs a) {
-    extern __shared__ float qst[];  // [warps][kStash][32]
+    extern __shared__ float qst[];  // [warps][kStash][32]: q stash; 32 x 32 transposes
     __shared__ int s_item;
-    __shared__ uint32_t s_unsat, s_active;
+    __shared__ uint32_t s_unsat;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int CS = a.CS;
+    const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    volatile int *item_src = CS > 1 ? cg::this_cluster().map_shared_rank(&s_item, 0) : &s_item;
+    uint32_t *unsat_dst = CS > 1 ? cg::this_cluster().map_shared_rank(&s_unsat, 0) : &s_unsat;
     const int FT = a.FT, slots = 32 / FT, slot = lane / FT, fl = lane - slot * FT;
+    const int gw = rank * nwarps + warp, TW = CS * nwarps;            // warp within the cluster
+    const int64_t gt = (int64_t)rank * blockDim.x + tid, TT = (int64_t)CS * blockDim.x;
     float *my = qst + (warp * kStash) * 32 + lane;
-    unsigned long long units = 0;
+    float *tr = qst + (warp * kStash) * 32;                           // this warp's 32 x 32 tile
+    unsigned long long units = 0, units_first = 0, punits = 0;   // per launch
+    if (tid == 0) s_unsat = 0;
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.head, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= a.n_items) break;
+        if (rank == 0 && tid == 0) s_item = atomicAdd(a.head, 1);
+        plan_sync(CS);
+        const int item = *item_src;
+        if (item >= a.n_items) {
+            plan_sync(CS);   // no CTA leaves while another may still read the leader's word
+            break;
+        }
         const PlanItem itm = a.items[item];
         const PlanGroup &G = a.groups[itm.g];
         const int n = G.n, M = G.M;
-        const int64_t E = G.E;
         const int f0 = itm.tile * FT, nf = min(FT, G.F - f0);
         char *tb = a.ws + G.ws_off + (int64_t)itm.tile * G.tile_bytes;
         float *L = reinterpret_cast<float *>(tb);
         float *msg = reinterpret_cast<float *>(tb + align_up((size_t)n * FT * 4, 256));
         uint32_t *sw = reinterpret_cast<uint32_t *>(tb + align_up((size_t)n * FT * 4, 256) +
-                                                    align_up((size_t)E * FT * 4, 256));
-        // ---- load the tile: posteriors = channel LLRs, messages = 0, syndrome words
-        for (int64_t idx = tid; idx < (int64_t)FT * n; idx += blockDim.x) {
-            const int i = (int)(idx / n), v = (int)(idx - (int64_t)i * n);
-            L[(int64_t)v * FT + i] = i < nf ? __ldg(G.llr + (int64_t)(f0 + i) * n + v) : kLlrClip;
+                                                    align_up((size_t)G.E * FT * 4, 256));
+        // ---- load the tile: L[v][i] = llr[f0 + i][v] through a per-warp transpose
+        // (swizzled columns, conflict-free), padding frames get a confident 0
+        for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
+            const int64_t v = v0 + lane;
+            for (int i = 0; i < FT; ++i)
+                tr[i * 32 + (lane ^ i)] = (i < nf && v < n) ? __ldg(G.llr + (int64_t)(f0 + i) * n + v) : kLlrClip;
+            __syncwarp();
+            for (int idx = lane; idx < 32 * FT; idx += 32) {
+                const int j = idx / FT, fi = idx - j * FT;
+                if (v0 + j < n) __stcg(L + (v0 + j) * FT + fi, tr[fi * 32 + (j ^ fi)]);
+            }
+            __syncwarp();
         }
-        for (int64_t idx = tid; idx < E * FT; idx += blockDim.x) msg[idx] = 0.0f;
-        for (int c = tid; c < M; c += blockDim.x) {
+        for (int64_t c = gt; c < M; c += TT) {
             uint32_t w = 0;
             for (int i = 0; i < nf; ++i) w |= (uint32_t)(__ldg(G.synd + (int64_t)(f0 + i) * M + c) & 1) << i;
-            sw[c] = w;
+            __stcg(sw + c, w);
         }
-        if (tid == 0) {
-            s_active = nf == 32 ? 0xffffffffu : ((1u << nf) - 1u);
-            s_unsat = 0;
-        }
-        __syncthreads();
-        // ---- stopping test of the tile's current posteriors: bit i of s_unsat
+        uint32_t active = nf == 32 ? 0xffffffffu : ((1u << nf) - 1u);   // same value in every thread
+        plan_sync(CS);
+        // ---- stopping test of the tile's current posteriors: frames failing a
+        // check are OR-ed into the leader's word
         auto parity = [&]() {
             uint32_t bad = 0;
-            if (fl < nf) {
-                for (int c = warp * slots + slot; c < M; c += nwarps * slots) {
-                    uint32_t par = (sw[c] >> fl) & 1u;
-                    for (int32_t e = __ldg(G.rp + c), ee = __ldg(G.rp + c + 1); e < ee; ++e)
-                        par ^= (uint32_t)(L[(int64_t)__ldg(G.ci + e) * FT + fl] < 0.0f);
-                    bad |= par;
+            if (fl < nf && ((active >> fl) & 1u)) {
+                for (int c = gw * slots + slot; c < M; c += TW * slots) {
+                    uint32_t par = (__ldcg(sw + c) >> fl) & 1u;
+                    const int32_t beg = __ldg(G.rp + c), end = __ldg(G.rp + c + 1);
+                    for (int32_t e = beg; e < end; ++e)
+                        par ^= (uint32_t)(__ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl)) < 0.0f);
+                    bad |= par << fl;
+                    punits += end - beg;
                 }
             }
-            if (bad) atomicOr(&s_unsat, 1u << fl);
+            bad = __reduce_or_sync(0xffffffffu, bad);
+            if (lane == 0 && bad) atomicOr(unsat_dst, bad);
         };
         // retire the frames whose test passed (iterations executed: t)
         auto retire = [&](int t) {
-            __syncthreads();
-            if (tid < nf) {
-                const bool was = (s_active >> tid) & 1u;
-                const bool ok = !((s_unsat >> tid) & 1u);
-                if (was && ok) G.iters[f0 + tid] = t;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                s_active &= s_unsat;   // still decoding: active and unsatisfied
-                s_unsat = 0;
-            }
-            __syncthreads();
+            plan_sync(CS);
+            const uint32_t u = *reinterpret_cast<volatile uint32_t *>(unsat_dst);
+            const uint32_t done = active & ~u;
+            if (rank == 0 && tid < nf && ((done >> tid) & 1u)) G.iters[f0 + tid] = t;
+            active &= u;
+            plan_sync(CS);   // every CTA has read the word before it is cleared
+            if (rank == 0 && tid == 0) s_unsat = 0;
         };
         if (a.early_stop) {
             parity();
             retire(0);
         }
-        for (int t = 1; t <= a.max_iter; ++t) {
-            if (s_active == 0) break;
+        for (int t = 1; t <= a.max_iter && active; ++t) {
+            const bool first = t == 1;
             for (int ly = 0; ly < G.n_layers; ++ly) {
                 const int32_t lb = __ldg(G.lptr + ly), le = __ldg(G.lptr + ly + 1);
-                const bool live = fl < nf && ((s_active >> fl) & 1u);
-                for (int32_t kk = lb + warp * slots + slot; live && kk < le; kk += nwarps * slots) {
+                const bool live = fl < nf && ((active >> fl) & 1u);
+                for (int32_t kk = lb + gw * slots + slot; live && kk < le; kk += TW * slots) {
                     const int32_t c = __ldg(G.lchk + kk);
                     const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
-                    uint32_t neg = (sw[c] >> fl) & 1u;
+                    uint32_t neg = (__ldcg(sw + c) >> fl) & 1u;
                     float mn1 = INFINITY, mn2 = INFINITY;
                     int32_t arg = -1;
                     units += d;
+                    if (first) units_first += d;
+                    // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
                     for (int k0 = 0; k0 < d; k0 += CH) {
                         float Lv[CH], mo[CH];
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
                             const int32_t e = beg + min(k0 + j, d - 1);
-                            Lv[j] = L[(int64_t)__ldg(G.ci + e) * FT + fl];
-                            mo[j] = msg[(int64_t)e * FT + fl];
+                            Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl));
+                            mo[j] = first ? 0.0f : __ldcg(msg + ((uint32_t)e * FT + fl));
                         }
 #pragma unroll
                         for (int j = 0; j < CH; ++j) {
@@ -155,18 +186,20 @@ plan_layered_kernel(PlanArgs a) {
                             else if (m < mn2) mn2 = m;
                         }
                     }
+                    // pass 2: new messages and posteriors L = q + m
                     for (int k = 0; k < d; ++k) {
                         const int32_t e = beg + k;
-                        const int32_t col = __ldg(G.ci + e);
+                        float *Lp = L + ((uint32_t)__ldg(G.ci + e) * FT + fl);
+                        float *mp = msg + ((uint32_t)e * FT + fl);
                         // edges beyond the stash: L and m of this edge are still unchanged
-                        const float q = k < kStash ? my[k * 32] : L[(int64_t)col * FT + fl] - msg[(int64_t)e * FT + fl];
+                        const float q = k < kStash ? my[k * 32] : __ldcg(Lp) - (first ? 0.0f : __ldcg(mp));
                         const float mag = fmaxf(((k == arg) ? mn2 : mn1) - a.beta, 0.0f);
                         const float mn = ((neg ^ (uint32_t)(q < 0.0f)) & 1u) ? -mag : mag;
-                        msg[(int64_t)e * FT + fl] = mn;
-                        L[(int64_t)col * FT + fl] = q + mn;
+                        __stcg(mp, mn);
+                        __stcg(Lp, q + mn);
                     }
                 }
-                __syncthreads();
+                plan_sync(CS);
             }
             if (a.early_stop || t == a.max_iter) {
                 parity();
@@ -178,18 +211,29 @@ plan_layered_kernel(PlanArgs a) {
             retire(0);
         }
         // ---- outputs: frames still active never satisfied the syndrome
-        if (tid < nf) {
-            const bool act = (s_active >> tid) & 1u;
+        if (rank == 0 && tid < nf) {
+            const bool act = (active >> tid) & 1u;
             G.conv[f0 + tid] = act ? 0 : 1;
             if (act) G.iters[f0 + tid] = a.max_iter;
         }
-        for (int64_t idx = tid; idx < (int64_t)nf * n; idx += blockDim.x) {
-            const int i = (int)(idx / n), v = (int)(idx - (int64_t)i * n);
-            G.bits[(int64_t)(f0 + i) * n + v] = L[(int64_t)v * FT + i] < 0.0f ? 1 : 0;
+        for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
+            for (int idx = lane; idx < 32 * FT; idx += 32) {
+                const int j = idx / FT, fi = idx - j * FT;
+                tr[fi * 32 + (j ^ fi)] = v0 + j < n ? __ldcg(L + (v0 + j) * FT + fi) : 0.0f;
+            }
+            __syncwarp();
+            const int64_t v = v0 + lane;
+            if (v < n)
+                for (int i = 0; i < nf; ++i)
+                    G.bits[(int64_t)(f0 + i) * n + v] = tr[i * 32 + (lane ^ i)] < 0.0f ? 1 : 0;
+            __syncwarp();
         }
-        __syncthreads();
+        plan_sync(CS);   // the tile is finished in every CTA before the leader takes the next
     }
-    prof_add(a.prof, units, units * 16);
+    // per edge-frame update: posterior and message read and written (16 B; the
+    // first iteration reads no message); per edge-frame of a stopping test: the
+    // posterior gathered (4 B)
+    prof_add(a.prof, units, units * 16 - units_first * 4 + punits * 4);
 }
 
 }  // namespace qkd
@@ -210,12 +254,20 @@ struct qkdrec_plan_s {
 namespace qkd {
 
 static const int kPlanFT[] = {8, 16, 32};
-static const int kPlanThreads[] = {128, 256, 512};
-static const int kPlanDepth[] = {2, 4, 8};
+static const int kPlanThreads[] = {256, 512, 1024};
+static const int kPlanDepth[] = {4, 8};
+static const int kPlanCS[] = {1, 2, 4, 8};
+
+template <size_t N>
+static bool in_set(int v, const int (&set)[N]) {
+    for (size_t i = 0; i < N; ++i)
+        if (v == set[i]) return true;
+    return false;
+}
 
 static bool tuning_ok(const qkdrec_tuning &t) {
-    auto in = [](int v, const int *set) { return v == set[0] || v == set[1] || v == set[2]; };
-    return in(t.frames_per_cta, kPlanFT) && in(t.threads_per_cta, kPlanThreads) && in(t.stage_depth, kPlanDepth);
+    return in_set(t.frames_per_tile, kPlanFT) && in_set(t.threads_per_cta, kPlanThreads) &&
+           in_set(t.stage_depth, kPlanDepth) && in_set(t.ctas_per_tile, kPlanCS);
 }
 
 static size_t plan_ws_bytes(const std::vector<qkdrec_group> &gs, int FT) {
@@ -229,7 +281,7 @@ static size_t plan_ws_bytes(const std::vector<qkdrec_group> &gs, int FT) {
 
 // (Re)build the device tables for the plan's current tuning (synchronous).
 static qkdrec_status plan_build(qkdrec_plan_s &p) {
-    const int FT = p.tuning.frames_per_cta;
+    const int FT = p.tuning.frames_per_tile;
     std::vector<PlanGroup> hg(p.groups.size());
     std::vector<PlanItem> items;
     std::vector<double> cost;
@@ -283,6 +335,44 @@ static qkdrec_status plan_build(qkdrec_plan_s &p) {
     return QKDREC_OK;
 }
 
+template <int CH>
+static qkdrec_status plan_launch_ch(const PlanArgs &a, int threads, int CS, int n_items, cudaStream_t st) {
+    // up to 1024 threads x 128 B of stash: above the default 48 KB of dynamic shared memory
+    static bool attr_set = false;
+    const size_t stash = (size_t)(threads / 32) * kStash * 32 * sizeof(float);
+    if (!attr_set) {
+        QKD_CUDA(cudaFuncSetAttribute(plan_layered_kernel<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((size_t)(1024 / 32) * kStash * 32 * sizeof(float))));
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = stash;
+    cfg.stream = st;
+    int groups_resident = 0;
+    if (CS > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(CS);
+        QKD_CUDA(cudaOccupancyMaxActiveClusters(&groups_resident, plan_layered_kernel<CH>, &cfg));
+    } else {
+        int per_sm = 0;
+        QKD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<CH>, threads, stash));
+        groups_resident = per_sm * sm_count();
+    }
+    if (groups_resident < 1)
+        QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "launch shape %d threads x %d CTAs does not fit", threads, CS);
+    const int groups = std::min(groups_resident, n_items);
+    cfg.gridDim = dim3((unsigned)(groups * CS));
+    QKD_CUDA(cudaLaunchKernelEx(&cfg, plan_layered_kernel<CH>, a));
+    return QKDREC_OK;
+}
+
 static qkdrec_status plan_launch(const qkdrec_plan_s &p, void *ws, size_t bytes, cudaStream_t st) {
     if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) QKD_FAIL(QKDREC_ERR_ARG, "workspace NULL or not 256-byte aligned");
     if (bytes < p.ws_needed) QKD_FAIL(QKDREC_ERR_ARG, "workspace %zu < %zu bytes", bytes, p.ws_needed);
@@ -293,37 +383,18 @@ static qkdrec_status plan_launch(const qkdrec_plan_s &p, void *ws, size_t bytes,
     a.n_items = p.n_items;
     a.head = p.d_head;
     a.ws = reinterpret_cast<char *>(ws);
-    a.FT = p.tuning.frames_per_cta;
+    a.FT = p.tuning.frames_per_tile;
+    a.CS = p.tuning.ctas_per_tile;
     a.max_iter = p.opts.max_iter;
     a.early_stop = p.opts.early_stop ? 1 : 0;
     a.beta = p.opts.offset;
     a.prof = prof::counters(prof::kPlan);
     QKD_CUDA(cudaMemsetAsync(p.d_head, 0, sizeof(int32_t), st));
     const int threads = p.tuning.threads_per_cta;
-    const size_t stash = (size_t)(threads / 32) * kStash * 32 * sizeof(float);
-    // 512 threads need 64 KB of dynamic shared memory (above the default 48 KB)
-    static bool attr_set = false;
-    if (!attr_set) {
-        const int lim = (int)((size_t)(512 / 32) * kStash * 32 * sizeof(float));
-        cudaFuncSetAttribute(plan_layered_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(plan_layered_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(plan_layered_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        attr_set = true;
-    }
-    int per_sm = 0;
-    switch (p.tuning.stage_depth) {
-        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<2>, threads, stash); break;
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<4>, threads, stash); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<8>, threads, stash); break;
-    }
-    if (per_sm < 1) per_sm = 1;
-    const int grid = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, p.n_items);
     prof::Scope ps(prof::kPlan, st);
-    switch (p.tuning.stage_depth) {
-        case 2: plan_layered_kernel<2><<<grid, threads, stash, st>>>(a); break;
-        case 4: plan_layered_kernel<4><<<grid, threads, stash, st>>>(a); break;
-        default: plan_layered_kernel<8><<<grid, threads, stash, st>>>(a); break;
-    }
+    qkdrec_status s = p.tuning.stage_depth == 4 ? plan_launch_ch<4>(a, threads, a.CS, p.n_items, st)
+                                                : plan_launch_ch<8>(a, threads, a.CS, p.n_items, st);
+    if (s != QKDREC_OK) return s;
     QKD_LAUNCHED("plan_layered_kernel");
     return QKDREC_OK;
 }
@@ -334,9 +405,10 @@ extern "C" {
 
 void qkdrec_tuning_default(qkdrec_tuning *t) {
     if (!t) return;
-    t->frames_per_cta = 32;
-    t->threads_per_cta = 256;
+    t->frames_per_tile = 32;
+    t->threads_per_cta = 512;
     t->stage_depth = 8;
+    t->ctas_per_tile = 4;
 }
 
 qkdrec_status qkdrec_plan_create(const qkdrec_group *groups, int32_t n_groups, const qkdrec_decode_opts *opts,
@@ -357,6 +429,9 @@ qkdrec_status qkdrec_plan_create(const qkdrec_group *groups, int32_t n_groups, c
         if (!g.code || g.frames < 0) QKD_FAIL(QKDREC_ERR_ARG, "group %d: NULL code or frames < 0", i);
         if (g.frames > 0 && (!g.llr || !g.synd || !g.bits_out || !g.iters_out || !g.conv_out))
             QKD_FAIL(QKDREC_ERR_ARG, "group %d: NULL input/output", i);
+        // tile offsets are 32-bit: edges x 32 frames must stay below 2^32
+        if ((uint64_t)g.code->d.E * 32u > 0xffffffffull)
+            QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "group %d: %lld edges, above 2^27", i, (long long)g.code->d.E);
     }
     qkdrec_plan_s *p = new (std::nothrow) qkdrec_plan_s();
     if (!p) QKD_FAIL(QKDREC_ERR_NOMEM, "host allocation");
@@ -422,26 +497,38 @@ qkdrec_status qkdrec_plan_autotune(qkdrec_plan_t p, void *workspace, size_t work
     QKD_CUDA(cudaEventCreate(&e1));
     qkdrec_tuning best = p->tuning;
     float best_t = INFINITY;
+    // time one shape: 1 = timed, 0 = does not fit on the device (skipped), < 0 = error
+    auto trial = [&]() -> int {
+        if (plan_launch(*p, workspace, workspace_bytes, st) != QKDREC_OK) {   // warm-up
+            cudaGetLastError();
+            clear_error();
+            return 0;
+        }
+        cudaEventRecord(e0, st);
+        if (plan_launch(*p, workspace, workspace_bytes, st) != QKDREC_OK) return -1;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_t) {
+            best_t = ms;
+            best = p->tuning;
+        }
+        return 1;
+    };
     qkdrec_status s = QKDREC_OK;
     for (int ft : kPlanFT) {
-        p->tuning.frames_per_cta = ft;
+        p->tuning.frames_per_tile = ft;
         if ((s = plan_build(*p)) != QKDREC_OK) break;
-        for (int th : kPlanThreads)
-            for (int dep : kPlanDepth) {
-                p->tuning.threads_per_cta = th;
-                p->tuning.stage_depth = dep;
-                if ((s = plan_launch(*p, workspace, workspace_bytes, st)) != QKDREC_OK) break;  // warm-up
-                cudaEventRecord(e0, st);
-                if ((s = plan_launch(*p, workspace, workspace_bytes, st)) != QKDREC_OK) break;
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_t) {
-                    best_t = ms;
-                    best = p->tuning;
+        for (int cs : kPlanCS)
+            for (int th : kPlanThreads)
+                for (int dep : kPlanDepth) {
+                    if (s != QKDREC_OK) continue;
+                    p->tuning.ctas_per_tile = cs;
+                    p->tuning.threads_per_cta = th;
+                    p->tuning.stage_depth = dep;
+                    if (trial() < 0) s = QKDREC_ERR_CUDA;
                 }
-            }
         if (s != QKDREC_OK) break;
     }
     cudaEventDestroy(e0);

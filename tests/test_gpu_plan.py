@@ -90,9 +90,10 @@ def test_frames_empty_batch_is_a_no_op():
 
 # ------------------------------------------------------------------ plan decoder
 TUNINGS = [None,
-           dict(frames_per_cta=8, threads_per_cta=128, stage_depth=2),
-           dict(frames_per_cta=16, threads_per_cta=512, stage_depth=4),
-           dict(frames_per_cta=32, threads_per_cta=128, stage_depth=8)]
+           dict(frames_per_tile=8, threads_per_cta=256, stage_depth=4, ctas_per_tile=1),
+           dict(frames_per_tile=16, threads_per_cta=512, stage_depth=4, ctas_per_tile=2),
+           dict(frames_per_tile=32, threads_per_cta=1024, stage_depth=8, ctas_per_tile=8),
+           dict(frames_per_tile=32, threads_per_cta=256, stage_depth=8, ctas_per_tile=1)]
 
 
 def make_groups(spec, seed=800):
@@ -146,7 +147,7 @@ def test_plan_identical_to_batch_decoder(tuning, early_stop, max_iter):
 def test_plan_vs_oracle_after_fixed_iterations(iters):
     groups = make_groups([(1024, 0.5, 13, 0.85), (720, 40 / 90, 9, 0.9)], seed=850)
     opts = q.DecodeOpts(algo="oms_layered", prec="f32", max_iter=iters, early_stop=False)
-    plan = q.Plan(groups, opts, dict(frames_per_cta=8, threads_per_cta=256, stage_depth=4))
+    plan = q.Plan(groups, opts, dict(frames_per_tile=8, threads_per_cta=256, stage_depth=4, ctas_per_tile=4))
     plan.launch(plan.workspace())
     torch.cuda.synchronize()
     for g in groups:
@@ -213,9 +214,10 @@ def test_plan_autotune_picks_a_supported_tuning_and_keeps_results():
     plan = q.Plan(groups, opts)
     ws = plan.workspace()
     best, ms = plan.autotune(ws, max_iter=5)
-    assert best["frames_per_cta"] in (8, 16, 32)
-    assert best["threads_per_cta"] in (128, 256, 512)
-    assert best["stage_depth"] in (2, 4, 8)
+    assert best["frames_per_tile"] in (8, 16, 32)
+    assert best["threads_per_cta"] in (256, 512, 1024)
+    assert best["stage_depth"] in (4, 8)
+    assert best["ctas_per_tile"] in (1, 2, 4, 8)
     assert ms > 0 and plan.tuning() == best
     plan.launch(ws)
     torch.cuda.synchronize()
@@ -231,8 +233,9 @@ def test_plan_rejects_unsupported_options_and_small_workspace():
     with pytest.raises(RuntimeError):
         q.Plan(groups, q.DecodeOpts(algo="oms_layered", prec="f16"))
     with pytest.raises(RuntimeError):
-        q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(frames_per_cta=4, threads_per_cta=256,
-                                                                  stage_depth=8))
+        q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(frames_per_tile=4))
+    with pytest.raises(RuntimeError):
+        q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(ctas_per_tile=3))
     plan = q.Plan(groups, q.DecodeOpts(algo="oms_layered"))
     small = torch.empty(256, dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError):

@@ -46,11 +46,11 @@ def frame_rates(snrs, fraction=0.75):
     return r
 
 
-def make_batch(seed, F, lengths=(1024, 2048, 4096)):
+def make_batch(seed, F, lengths=(1024, 2048, 4096), fraction=0.75):
     n, snr = synth.uneven_frames(seed, F, lengths, (2.0, 15.0))
     order = np.lexsort((snr, n))
     n, snr = n[order], snr[order]
-    rates = frame_rates(snr)
+    rates = frame_rates(snr, fraction)
     keys = {(int(n[f]), float(rates[j, f])) for j in range(M_SLICES) for f in range(F) if rates[j, f] > 0}
     csr, codes = {}, {}
     for i, (nn, r) in enumerate(sorted(keys)):
@@ -123,7 +123,7 @@ def test_uneven_graph_equals_per_group_calls_and_replays():
 
 
 def test_uneven_frames_vs_oracle_reconciliation():
-    n, snr, rates, codes, csr, x, y = make_batch(43, 18, lengths=(512, 1024))
+    n, snr, rates, codes, csr, x, y = make_batch(43, 18, lengths=(1024, 2048), fraction=0.6)
     ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=30)
     ub.x.copy_(torch.from_numpy(x))
     ub.y.copy_(torch.from_numpy(y))
@@ -142,6 +142,8 @@ def test_uneven_frames_vs_oracle_reconciliation():
             if rates[j, f] <= 0:
                 mine[j] = bits[j]
                 continue
+            if not np.array_equal(alice[:j, a:b], mine[:j]):
+                break      # one side failed a lower slice: its later LLRs differ
             rp, ci = csr[(int(n[f]), float(rates[j, f]))]
             s = oracle.syndrome(rp, ci, bits[j][None])
             llr = oracle.slice_llr(x[a:b].astype(np.float64), mine[:j] if j else None, j, M_SLICES, lo, hi,
@@ -151,6 +153,4 @@ def test_uneven_frames_vs_oracle_reconciliation():
             if out["converged"][0] and conv[j, f]:
                 agreed += 1
                 assert np.array_equal(alice[j, a:b], mine[j]), (f, j)
-            else:
-                break      # the lower slices now differ; later slices are not comparable
-    assert agreed > 0
+    assert agreed >= 3
