@@ -195,10 +195,13 @@ UNEVEN_SNR = (2.0, 15.0)
 UNEVEN_SNR_STEP = 0.1
 UNEVEN_MAX_ITER = 50
 UNEVEN_SEED = 11
-UNEVEN_RATE_FRACTION = 0.90     # codes 10% below the slice capacity, as in the paper's Fig. 4 runs
+UNEVEN_SNR_BIN = 1.0            # rates are set per (n, slice, SNR bin [2,3), [3,4), ..., [14,15])
+UNEVEN_RATES = os.path.join(ROOT, "uneven_rates.json")
 UNEVEN_WORKLOAD = ("uneven batch: 4096 frames, n in {4096, 16384, 65536}, SNR uniform on the 0.1 grid of 2..15, "
-                   "5 Gray slices, per (frame, slice) rate 0.90 x capacity on the 1/64 grid within [0.10, 0.95] "
-                   "(below 0.10: disclosed), dv=3 codes per (n, rate), layered offset min-sum FP32 (offset 0.5), "
+                   "5 Gray slices, per (n, slice, SNR bin of width 1) rate from the Sec. V-B back-off (start 0.95 x "
+                   "capacity at the bin's lowest SNR, minus 3/64 while > 1 of 32 trial frames fail; below 0.10: "
+                   "disclosed; table in uneven_rates.json), dv=3 codes per (n, rate), layered offset min-sum FP32 "
+                   "(offset 0.5), "
                    "<= 50 iterations, early stop, whole step replayed as one CUDA graph")
 
 
@@ -208,10 +211,26 @@ def _capacity_row(snr):
     return snr, [q.qkdrec_slice_capacity(snr, M_SLICES, j, lo, hi) for j in range(M_SLICES)]
 
 
-def uneven_rate(capacity, fraction=UNEVEN_RATE_FRACTION):
-    k = int(np.floor(fraction * capacity * 64 + 0.5))
-    r = min(k, 60) / 64
-    return r if r >= 0.10 else 0.0
+def uneven_start_rate(capacity):
+    """First rate the back-off tries: 0.95 x capacity on the 1/64 grid, at most 60/64."""
+    return min(int(np.floor(0.95 * capacity * 64 + 0.5)), 60) / 64
+
+
+def uneven_bin(snr):
+    k = int((UNEVEN_SNR[1] - UNEVEN_SNR[0]) / UNEVEN_SNR_BIN)
+    return np.minimum(((np.asarray(snr) - UNEVEN_SNR[0]) / UNEVEN_SNR_BIN + 1e-9).astype(np.int64), k - 1)
+
+
+def uneven_bin_low(b):
+    return UNEVEN_SNR[0] + UNEVEN_SNR_BIN * int(b)
+
+
+def load_uneven_rates():
+    try:
+        t = json.load(open(UNEVEN_RATES))
+    except OSError:
+        raise SystemExit(f"{UNEVEN_RATES} missing: run python bench.py --workload uneven --calibrate")
+    return {(int(r[0]), int(r[1]), int(r[2])): float(r[3]) for r in t["rates"]}
 
 
 def uneven_code_seed(n, rate):
@@ -232,17 +251,75 @@ def _pool_map(fn, items, workers):
         return pool.map(fn, items)
 
 
-def uneven_setup(seed, workers):
-    """Frames (sorted by (n, SNR)), per-(slice, frame) rates and the CSR codes (host only)."""
+def uneven_setup(seed, workers, rule="backoff"):
+    """Frames (sorted by (n, SNR)), per-(slice, frame) rates and the CSR codes (host only).
+    rule "backoff": the committed back-off table per (n, slice, SNR bin);
+    rule "capacity": 0.95 x capacity at the frame's SNR, 1/64 grid, at most 60/64,
+    below 0.10 disclosed."""
     n, snr = synth.uneven_frames(seed, UNEVEN_FRAMES, UNEVEN_LENGTHS, UNEVEN_SNR, UNEVEN_SNR_STEP)
     order = np.lexsort((snr, n))
     n, snr = n[order], snr[order]
-    caps = dict(_pool_map(_capacity_row, sorted(set(snr.tolist())), workers))
-    rates = np.array([[uneven_rate(caps[s][j]) for s in snr.tolist()] for j in range(M_SLICES)])
+    if rule == "backoff":
+        table = load_uneven_rates()
+        bins = uneven_bin(snr)
+        rates = np.array([[table[(int(n[f]), int(bins[f]), j)] for f in range(n.size)] for j in range(M_SLICES)])
+    else:
+        caps = dict(_pool_map(_capacity_row, sorted(set(snr.tolist())), workers))
+        start = np.array([[uneven_start_rate(caps[s_][j]) for s_ in snr.tolist()] for j in range(M_SLICES)])
+        rates = np.where(start >= 0.10, start, 0.0)
     keys = sorted({(int(n[f]), float(rates[j, f])) for j in range(M_SLICES) for f in range(n.size)
                    if rates[j, f] > 0}, key=lambda k: -k[0])
     codes = dict(_pool_map(_make_code_nr, keys, workers))
     return n, snr, rates, codes
+
+
+def _trial_sample(point):
+    n, snr, j = point
+    b = int(uneven_bin(snr))
+    x, y = synth.gaussian_pair(600_000 + 100 * b + int(n).bit_length(), 32 * n, snr)
+    return x, y
+
+
+def run_calibrate(args):
+    """Sec. V-B back-off for every (n, slice, SNR bin) of the uneven workload on
+    32 trial frames at the bin's lowest SNR; writes the rate table."""
+    cores = len(os.sched_getaffinity(0))
+    workers = max(1, min(cores, 16))
+    import paper_2108_08418_b300 as q
+    from paper_2108_08418_b300 import build as qbuild
+    qbuild.build()
+    nbins = int((UNEVEN_SNR[1] - UNEVEN_SNR[0]) / UNEVEN_SNR_BIN)
+    lows = [uneven_bin_low(b) for b in range(nbins)]
+    caps = dict(_pool_map(_capacity_row, lows, workers))
+    points = [(n, s, j) for n in UNEVEN_LENGTHS for s in lows for j in range(M_SLICES)]
+    start = {p: uneven_start_rate(caps[p[1]][p[2]]) for p in points}
+    import torch
+    from paper_2108_08418_b300.uneven import backoff_rates
+    torch.cuda.set_device(0)
+    cache = {}
+
+    def codes_for(keys):
+        new = sorted(k for k in keys if k not in cache)
+        for k, v in _pool_map(_make_code_nr, new, workers):
+            cache[k] = q.Code(k[0], v[0], v[1], seed=uneven_code_seed(*k))
+        return cache
+
+    t0 = time.time()
+    got = backoff_rates(points, start, codes_for, _trial_sample, trial_frames=32, max_fail=1, step=3 / 64,
+                        min_rate=0.10, m_slices=M_SLICES, max_iter=UNEVEN_MAX_ITER, offset=0.5)
+    rows = [[p[0], int(uneven_bin(p[1])), p[2], got[p][0], got[p][1], start[p]] for p in points]
+    out = {"procedure": "Sec. V-B back-off: start at 0.95 x slice capacity (1/64 grid, <= 60/64) at the bin's "
+                        "lowest SNR; 32 trial frames (seed 600000 + 100 bin + bitlength(n)), Bob's lower slices; "
+                        "layered offset min-sum <= 50 iterations; lower the rate by 3/64 while more than 1 frame "
+                        "fails; below 0.10 the slice is disclosed (rate 0)",
+           "command": "python bench.py --workload uneven --calibrate",
+           "columns": ["n", "snr_bin", "slice", "rate", "trial_frame_errors", "start_rate"],
+           "snr_bins": [[lo, lo + UNEVEN_SNR_BIN] for lo in lows],
+           "seconds": round(time.time() - t0, 1), "rates": rows}
+    with open(args.rates_out or UNEVEN_RATES, "w") as fh:
+        json.dump(out, fh, indent=0)
+    print(json.dumps({"calibrated_points": len(rows), "seconds": out["seconds"],
+                      "disclosed": sum(1 for r in rows if r[3] == 0.0)}), flush=True)
 
 
 def _oracle_uneven_frame(task):
@@ -293,10 +370,10 @@ def run_uneven(args):
     qbuild.build()
     t_setup = time.time()
     seed = UNEVEN_SEED + 1000 * rank
-    n, snr, rates, codes_h = uneven_setup(seed, max(1, min(cores, 16)))
+    n, snr, rates, codes_h = uneven_setup(seed, max(1, min(cores, 16)), args.rate_rule)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        per = max(1, min(cores, 8))
+        per = 3 * max(1, min(cores, 8))
         good, wall, nfr = oracle_uneven_sample(0, per, cores, (n, snr, rates, codes_h))
         cpu = {"value": good / wall, "unit": "bit/s", "cores": min(cores, nfr), "kind": "oracle",
                "sample": f"{nfr} frames of n=4096 of the batch, each reconciled over all 5 slices (FP64 quantiser, "
@@ -396,6 +473,7 @@ def run_uneven(args):
         "config": {"workload": UNEVEN_WORKLOAD, "frames": int(n.size), "samples": int(n.sum()),
                    "groups_per_slice": [len(g) for g in ub.groups], "algo": "oms_layered", "prec": "f32",
                    "max_iter": UNEVEN_MAX_ITER, "tuning_per_slice": [t[0] for t in tunings],
+                   "rate_rule": args.rate_rule,
                    "l2": "inputs larger than L2 (x, y 470 MB each; plan workspace "
                          f"{ub.ws.numel() / 2**30:.2f} GiB)",
                    "raw_decoded_bits_per_s": raw_bits / (ms_step / 1e3), "fer_per_slice": fer,
@@ -665,8 +743,8 @@ def run_reference(args):
 
 
 def run_reference_uneven(args, world, cores):
-    setup = uneven_setup(UNEVEN_SEED, max(1, min(cores, 16)))
-    per = max(1, min(cores, 8))
+    setup = uneven_setup(UNEVEN_SEED, max(1, min(cores, 16)), args.rate_rule)
+    per = 3 * max(1, min(cores, 8))
     for w in range(args.warmup):
         oracle_uneven_sample(w, per, cores, setup)
     goods, walls, nfr = 0, 0.0, 0
@@ -698,7 +776,10 @@ CASES = {
     "decode_oms_i8": dict(logn=16, frames=512, rate=0.84375, algo="oms_flood", prec="i8", iters=5),
     # the plan decoder on a small uneven batch: 96 frames of n = 2^16, 192 of 2^14, 384 of 2^12
     # (rate 0.84375; ~0.9 GB on the device)
-    "plan_layered": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5),
+    "plan_layered": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
+                         tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=6, ctas_per_tile=8)),
+    "plan_layered_ft32": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
+                              tuning=dict(frames_per_tile=32, threads_per_cta=1024, stage_depth=6, ctas_per_tile=8)),
 }
 
 
@@ -718,7 +799,7 @@ def run_plan_case(args, c):
                            bits=torch.empty_like(bd), iters=torch.empty(F, dtype=torch.int32, device="cuda"),
                            conv=torch.empty(F, dtype=torch.uint8, device="cuda")))
     opts = q.DecodeOpts(algo="oms_layered", prec="f32", max_iter=c["iters"], early_stop=False)
-    plan = q.Plan(groups, opts, dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=4))
+    plan = q.Plan(groups, opts, c["tuning"])
     ws = plan.workspace()
     for _ in range(args.warmup + args.steps):
         plan.launch(ws)
@@ -765,6 +846,11 @@ def main():
     ap.add_argument("--case", choices=sorted(CASES), help="run one small fixed decode (for ncu)")
     ap.add_argument("--workload", choices=["sweep", "uneven"], default="sweep",
                     help="sweep: the block-size sweep (default); uneven: the one-graph uneven batch")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="with --workload uneven: run the rate back-off and write uneven_rates.json")
+    ap.add_argument("--rates-out", help="where --calibrate writes the table (default: uneven_rates.json)")
+    ap.add_argument("--rate-rule", choices=["backoff", "capacity"], default="backoff",
+                    help="uneven workload: back-off table (default) or 0.95 x capacity per frame")
     args = ap.parse_args()
     if args.case:
         run_case(args)
@@ -773,6 +859,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven" and args.calibrate:
+        run_calibrate(args)
     elif args.workload == "uneven":
         run_uneven(args)
     else:

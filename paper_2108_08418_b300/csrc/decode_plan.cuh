@@ -7,8 +7,9 @@
 // a queue head and hands it to the other CTAs through distributed shared
 // memory; clusters never wait for each other.  The CTAs of the cluster split
 // every layer's checks between their warps and meet at the hardware cluster
-// barrier (release/acquire) after each layer, so one large tile runs on up to
-// 8 SMs while small tiles run on one.  The cluster runs the whole layered
+// barrier (release/acquire) after each layer, so one tile runs on up to 8 SMs:
+// the tile that holds the batch's slowest frame (the one that needs every
+// iteration) finishes up to 8 times sooner.  The cluster runs the whole layered
 // offset min-sum decode of its tile: all layers of all iterations, the
 // stopping test after every iteration (per-CTA partial results OR-ed into the
 // leader's shared word), frames retiring one by one, the tile leaving early
@@ -66,23 +67,187 @@ __device__ __forceinline__ void plan_sync(int CS) {
     else __syncthreads();
 }
 
+// Per-launch work counters of one CTA.
+struct PlanCount {
+    unsigned long long units = 0, units_first = 0, punits = 0;
+};
+
+// Decode one work item with a team of tcs CTAs (trank = this CTA's place in the
+// team; unsat_dst = the team leader's shared stopping-test word).
+template <int CH>
+__device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, int trank, uint32_t *unsat_dst,
+                                          uint32_t *s_unsat, float *qst, PlanCount &cnt) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int FT = a.FT, slots = 32 / FT, slot = lane / FT, fl = lane - slot * FT;
+    const int gw = trank * nwarps + warp, TW = tcs * nwarps;          // warp within the team
+    const int64_t gt = (int64_t)trank * blockDim.x + tid, TT = (int64_t)tcs * blockDim.x;
+    float *my = qst + (warp * kStash) * 32 + lane;
+    float *tr = qst + (warp * kStash) * 32;                           // this warp's 32 x 32 tile
+    uint32_t units = 0, units_first = 0, punits = 0;   // this item's share (added to cnt at the end)
+    const PlanItem itm = a.items[item];
+    const PlanGroup &G = a.groups[itm.g];
+    const int n = G.n, M = G.M;
+    const int f0 = itm.tile * FT, nf = min(FT, G.F - f0);
+    char *tb = a.ws + G.ws_off + (int64_t)itm.tile * G.tile_bytes;
+    float *L = reinterpret_cast<float *>(tb);
+    float *msg = reinterpret_cast<float *>(tb + align_up((size_t)n * FT * 4, 256));
+    uint32_t *sw = reinterpret_cast<uint32_t *>(tb + align_up((size_t)n * FT * 4, 256) +
+                                                align_up((size_t)G.E * FT * 4, 256));
+    // ---- load the tile: L[v][i] = llr[f0 + i][v] through a per-warp transpose
+    // (swizzled columns, conflict-free), padding frames get a confident 0
+    for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
+        const int64_t v = v0 + lane;
+        for (int i = 0; i < FT; ++i)
+            tr[i * 32 + (lane ^ i)] = (i < nf && v < n) ? __ldg(G.llr + (int64_t)(f0 + i) * n + v) : kLlrClip;
+        __syncwarp();
+        for (int idx = lane; idx < 32 * FT; idx += 32) {
+            const int j = idx / FT, fi = idx - j * FT;
+            if (v0 + j < n) __stcg(L + (v0 + j) * FT + fi, tr[fi * 32 + (j ^ fi)]);
+        }
+        __syncwarp();
+    }
+    for (int64_t c = gt; c < M; c += TT) {
+        uint32_t w = 0;
+#pragma unroll 8
+        for (int i = 0; i < nf; ++i) w |= (uint32_t)(__ldg(G.synd + (int64_t)(f0 + i) * M + c) & 1) << i;
+        __stcg(sw + c, w);
+    }
+    uint32_t active = nf == 32 ? 0xffffffffu : ((1u << nf) - 1u);   // same value in every thread
+    plan_sync(tcs);
+    // ---- stopping test of the tile's current posteriors: frames failing a
+    // check are OR-ed into the leader's word
+    auto parity = [&]() {
+        uint32_t bad = 0;
+        if (fl < nf && ((active >> fl) & 1u)) {
+            for (int c = gw * slots + slot; c < M; c += TW * slots) {
+                uint32_t par = (__ldcg(sw + c) >> fl) & 1u;
+                const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
+                // CH gathers in flight (indices past the last edge clamped to it)
+                for (int k0 = 0; k0 < d; k0 += CH) {
+                    float Lv[CH];
+#pragma unroll
+                    for (int j = 0; j < CH; ++j)
+                        Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + beg + min(k0 + j, d - 1)) * FT + fl));
+#pragma unroll
+                    for (int j = 0; j < CH; ++j)
+                        if (k0 + j < d) par ^= (uint32_t)(Lv[j] < 0.0f);
+                }
+                bad |= par << fl;
+                punits += d;
+            }
+        }
+        bad = __reduce_or_sync(0xffffffffu, bad);
+        if (lane == 0 && bad) atomicOr(unsat_dst, bad);
+    };
+    // retire the frames whose test passed (iterations executed: t)
+    auto retire = [&](int t) {
+        plan_sync(tcs);
+        const uint32_t u = *reinterpret_cast<volatile uint32_t *>(unsat_dst);
+        const uint32_t done = active & ~u;
+        if (trank == 0 && tid < nf && ((done >> tid) & 1u)) G.iters[f0 + tid] = t;
+        active &= u;
+        plan_sync(tcs);   // every CTA has read the word before it is cleared
+        if (trank == 0 && tid == 0) *s_unsat = 0;
+    };
+    if (a.early_stop) {
+        parity();
+        retire(0);
+    }
+    for (int t = 1; t <= a.max_iter && active; ++t) {
+        const bool first = t == 1;
+        for (int ly = 0; ly < G.n_layers; ++ly) {
+            const int32_t lb = __ldg(G.lptr + ly), le = __ldg(G.lptr + ly + 1);
+            const bool live = fl < nf && ((active >> fl) & 1u);
+            for (int32_t kk = lb + gw * slots + slot; live && kk < le; kk += TW * slots) {
+                const int32_t c = __ldg(G.lchk + kk);
+                const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
+                uint32_t neg = (__ldcg(sw + c) >> fl) & 1u;
+                float mn1 = INFINITY, mn2 = INFINITY;
+                int32_t arg = -1;
+                units += d;
+                if (first) units_first += d;
+                // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
+                for (int k0 = 0; k0 < d; k0 += CH) {
+                    float Lv[CH], mo[CH];
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        const int32_t e = beg + min(k0 + j, d - 1);
+                        Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl));
+                        mo[j] = first ? 0.0f : __ldcg(msg + ((uint32_t)e * FT + fl));
+                    }
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        const int k = k0 + j;
+                        if (k >= d) break;
+                        const float q = Lv[j] - mo[j];
+                        if (k < kStash) my[k * 32] = q;
+                        neg ^= (uint32_t)(q < 0.0f);
+                        const float m = fabsf(q);
+                        if (m < mn1) { mn2 = mn1; mn1 = m; arg = k; }
+                        else if (m < mn2) mn2 = m;
+                    }
+                }
+                // pass 2: new messages and posteriors L = q + m
+                for (int k = 0; k < d; ++k) {
+                    const int32_t e = beg + k;
+                    float *Lp = L + ((uint32_t)__ldg(G.ci + e) * FT + fl);
+                    float *mp = msg + ((uint32_t)e * FT + fl);
+                    // edges beyond the stash: L and m of this edge are still unchanged
+                    const float q = k < kStash ? my[k * 32] : __ldcg(Lp) - (first ? 0.0f : __ldcg(mp));
+                    const float mag = fmaxf(((k == arg) ? mn2 : mn1) - a.beta, 0.0f);
+                    const float mn = ((neg ^ (uint32_t)(q < 0.0f)) & 1u) ? -mag : mag;
+                    __stcg(mp, mn);
+                    __stcg(Lp, q + mn);
+                }
+            }
+            plan_sync(tcs);
+        }
+        if (a.early_stop || t == a.max_iter) {
+            parity();
+            retire(t);
+        }
+    }
+    if (!a.early_stop && a.max_iter == 0) {
+        parity();
+        retire(0);
+    }
+    // ---- outputs: frames still active never satisfied the syndrome
+    if (trank == 0 && tid < nf) {
+        const bool act = (active >> tid) & 1u;
+        G.conv[f0 + tid] = act ? 0 : 1;
+        if (act) G.iters[f0 + tid] = a.max_iter;
+    }
+    for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
+        for (int idx = lane; idx < 32 * FT; idx += 32) {
+            const int j = idx / FT, fi = idx - j * FT;
+            tr[fi * 32 + (j ^ fi)] = v0 + j < n ? __ldcg(L + (v0 + j) * FT + fi) : 0.0f;
+        }
+        __syncwarp();
+        const int64_t v = v0 + lane;
+        if (v < n)
+            for (int i = 0; i < nf; ++i)
+                G.bits[(int64_t)(f0 + i) * n + v] = tr[i * 32 + (lane ^ i)] < 0.0f ? 1 : 0;
+        __syncwarp();
+    }
+    cnt.units += units;
+    cnt.units_first += units_first;
+    cnt.punits += punits;
+}
+
+// Persistent loop: the team (the whole cluster, or the CTA when CS = 1) takes
+// items from the queue until it is empty.
 template <int CH>
 __global__ void __launch_bounds__(1024, 1)
 plan_layered_kernel(PlanArgs a) {
     extern __shared__ float qst[];  // [warps][kStash][32]: q stash; 32 x 32 transposes
     __shared__ int s_item;
     __shared__ uint32_t s_unsat;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     const int CS = a.CS;
     const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
     volatile int *item_src = CS > 1 ? cg::this_cluster().map_shared_rank(&s_item, 0) : &s_item;
     uint32_t *unsat_dst = CS > 1 ? cg::this_cluster().map_shared_rank(&s_unsat, 0) : &s_unsat;
-    const int FT = a.FT, slots = 32 / FT, slot = lane / FT, fl = lane - slot * FT;
-    const int gw = rank * nwarps + warp, TW = CS * nwarps;            // warp within the cluster
-    const int64_t gt = (int64_t)rank * blockDim.x + tid, TT = (int64_t)CS * blockDim.x;
-    float *my = qst + (warp * kStash) * 32 + lane;
-    float *tr = qst + (warp * kStash) * 32;                           // this warp's 32 x 32 tile
-    unsigned long long units = 0, units_first = 0, punits = 0;   // per launch
+    PlanCount cnt;
     if (tid == 0) s_unsat = 0;
     for (;;) {
         if (rank == 0 && tid == 0) s_item = atomicAdd(a.head, 1);
@@ -92,148 +257,13 @@ plan_layered_kernel(PlanArgs a) {
             plan_sync(CS);   // no CTA leaves while another may still read the leader's word
             break;
         }
-        const PlanItem itm = a.items[item];
-        const PlanGroup &G = a.groups[itm.g];
-        const int n = G.n, M = G.M;
-        const int f0 = itm.tile * FT, nf = min(FT, G.F - f0);
-        char *tb = a.ws + G.ws_off + (int64_t)itm.tile * G.tile_bytes;
-        float *L = reinterpret_cast<float *>(tb);
-        float *msg = reinterpret_cast<float *>(tb + align_up((size_t)n * FT * 4, 256));
-        uint32_t *sw = reinterpret_cast<uint32_t *>(tb + align_up((size_t)n * FT * 4, 256) +
-                                                    align_up((size_t)G.E * FT * 4, 256));
-        // ---- load the tile: L[v][i] = llr[f0 + i][v] through a per-warp transpose
-        // (swizzled columns, conflict-free), padding frames get a confident 0
-        for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
-            const int64_t v = v0 + lane;
-            for (int i = 0; i < FT; ++i)
-                tr[i * 32 + (lane ^ i)] = (i < nf && v < n) ? __ldg(G.llr + (int64_t)(f0 + i) * n + v) : kLlrClip;
-            __syncwarp();
-            for (int idx = lane; idx < 32 * FT; idx += 32) {
-                const int j = idx / FT, fi = idx - j * FT;
-                if (v0 + j < n) __stcg(L + (v0 + j) * FT + fi, tr[fi * 32 + (j ^ fi)]);
-            }
-            __syncwarp();
-        }
-        for (int64_t c = gt; c < M; c += TT) {
-            uint32_t w = 0;
-            for (int i = 0; i < nf; ++i) w |= (uint32_t)(__ldg(G.synd + (int64_t)(f0 + i) * M + c) & 1) << i;
-            __stcg(sw + c, w);
-        }
-        uint32_t active = nf == 32 ? 0xffffffffu : ((1u << nf) - 1u);   // same value in every thread
-        plan_sync(CS);
-        // ---- stopping test of the tile's current posteriors: frames failing a
-        // check are OR-ed into the leader's word
-        auto parity = [&]() {
-            uint32_t bad = 0;
-            if (fl < nf && ((active >> fl) & 1u)) {
-                for (int c = gw * slots + slot; c < M; c += TW * slots) {
-                    uint32_t par = (__ldcg(sw + c) >> fl) & 1u;
-                    const int32_t beg = __ldg(G.rp + c), end = __ldg(G.rp + c + 1);
-                    for (int32_t e = beg; e < end; ++e)
-                        par ^= (uint32_t)(__ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl)) < 0.0f);
-                    bad |= par << fl;
-                    punits += end - beg;
-                }
-            }
-            bad = __reduce_or_sync(0xffffffffu, bad);
-            if (lane == 0 && bad) atomicOr(unsat_dst, bad);
-        };
-        // retire the frames whose test passed (iterations executed: t)
-        auto retire = [&](int t) {
-            plan_sync(CS);
-            const uint32_t u = *reinterpret_cast<volatile uint32_t *>(unsat_dst);
-            const uint32_t done = active & ~u;
-            if (rank == 0 && tid < nf && ((done >> tid) & 1u)) G.iters[f0 + tid] = t;
-            active &= u;
-            plan_sync(CS);   // every CTA has read the word before it is cleared
-            if (rank == 0 && tid == 0) s_unsat = 0;
-        };
-        if (a.early_stop) {
-            parity();
-            retire(0);
-        }
-        for (int t = 1; t <= a.max_iter && active; ++t) {
-            const bool first = t == 1;
-            for (int ly = 0; ly < G.n_layers; ++ly) {
-                const int32_t lb = __ldg(G.lptr + ly), le = __ldg(G.lptr + ly + 1);
-                const bool live = fl < nf && ((active >> fl) & 1u);
-                for (int32_t kk = lb + gw * slots + slot; live && kk < le; kk += TW * slots) {
-                    const int32_t c = __ldg(G.lchk + kk);
-                    const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
-                    uint32_t neg = (__ldcg(sw + c) >> fl) & 1u;
-                    float mn1 = INFINITY, mn2 = INFINITY;
-                    int32_t arg = -1;
-                    units += d;
-                    if (first) units_first += d;
-                    // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
-                    for (int k0 = 0; k0 < d; k0 += CH) {
-                        float Lv[CH], mo[CH];
-#pragma unroll
-                        for (int j = 0; j < CH; ++j) {
-                            const int32_t e = beg + min(k0 + j, d - 1);
-                            Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl));
-                            mo[j] = first ? 0.0f : __ldcg(msg + ((uint32_t)e * FT + fl));
-                        }
-#pragma unroll
-                        for (int j = 0; j < CH; ++j) {
-                            const int k = k0 + j;
-                            if (k >= d) break;
-                            const float q = Lv[j] - mo[j];
-                            if (k < kStash) my[k * 32] = q;
-                            neg ^= (uint32_t)(q < 0.0f);
-                            const float m = fabsf(q);
-                            if (m < mn1) { mn2 = mn1; mn1 = m; arg = k; }
-                            else if (m < mn2) mn2 = m;
-                        }
-                    }
-                    // pass 2: new messages and posteriors L = q + m
-                    for (int k = 0; k < d; ++k) {
-                        const int32_t e = beg + k;
-                        float *Lp = L + ((uint32_t)__ldg(G.ci + e) * FT + fl);
-                        float *mp = msg + ((uint32_t)e * FT + fl);
-                        // edges beyond the stash: L and m of this edge are still unchanged
-                        const float q = k < kStash ? my[k * 32] : __ldcg(Lp) - (first ? 0.0f : __ldcg(mp));
-                        const float mag = fmaxf(((k == arg) ? mn2 : mn1) - a.beta, 0.0f);
-                        const float mn = ((neg ^ (uint32_t)(q < 0.0f)) & 1u) ? -mag : mag;
-                        __stcg(mp, mn);
-                        __stcg(Lp, q + mn);
-                    }
-                }
-                plan_sync(CS);
-            }
-            if (a.early_stop || t == a.max_iter) {
-                parity();
-                retire(t);
-            }
-        }
-        if (!a.early_stop && a.max_iter == 0) {
-            parity();
-            retire(0);
-        }
-        // ---- outputs: frames still active never satisfied the syndrome
-        if (rank == 0 && tid < nf) {
-            const bool act = (active >> tid) & 1u;
-            G.conv[f0 + tid] = act ? 0 : 1;
-            if (act) G.iters[f0 + tid] = a.max_iter;
-        }
-        for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
-            for (int idx = lane; idx < 32 * FT; idx += 32) {
-                const int j = idx / FT, fi = idx - j * FT;
-                tr[fi * 32 + (j ^ fi)] = v0 + j < n ? __ldcg(L + (v0 + j) * FT + fi) : 0.0f;
-            }
-            __syncwarp();
-            const int64_t v = v0 + lane;
-            if (v < n)
-                for (int i = 0; i < nf; ++i)
-                    G.bits[(int64_t)(f0 + i) * n + v] = tr[i * 32 + (lane ^ i)] < 0.0f ? 1 : 0;
-            __syncwarp();
-        }
+        plan_item<CH>(a, item, CS, rank, unsat_dst, &s_unsat, qst, cnt);
         plan_sync(CS);   // the tile is finished in every CTA before the leader takes the next
     }
     // per edge-frame update: posterior and message read and written (16 B; the
     // first iteration reads no message); per edge-frame of a stopping test: the
     // posterior gathered (4 B)
-    prof_add(a.prof, units, units * 16 - units_first * 4 + punits * 4);
+    prof_add(a.prof, cnt.units, cnt.units * 16 - cnt.units_first * 4 + cnt.punits * 4);
 }
 
 }  // namespace qkd
@@ -255,7 +285,7 @@ namespace qkd {
 
 static const int kPlanFT[] = {8, 16, 32};
 static const int kPlanThreads[] = {256, 512, 1024};
-static const int kPlanDepth[] = {4, 8};
+static const int kPlanDepth[] = {4, 6};
 static const int kPlanCS[] = {1, 2, 4, 8};
 
 template <size_t N>
@@ -309,8 +339,9 @@ static qkdrec_status plan_build(qkdrec_plan_s &p) {
         G.dc_max = d.dc_max;
         const int tiles = (int)ceil_div(g.frames, FT);
         for (int t = 0; t < tiles; ++t) {
+            const double c = (double)d.E * (double)std::min(FT, g.frames - t * FT);
             items.push_back(PlanItem{(int32_t)i, t});
-            cost.push_back((double)d.E * (double)std::min(FT, g.frames - t * FT) + 1e-3 * (double)d.n_layers);
+            cost.push_back(c + 1e-3 * (double)d.n_layers);
         }
         off += (int64_t)tiles * G.tile_bytes;
     }
@@ -393,7 +424,7 @@ static qkdrec_status plan_launch(const qkdrec_plan_s &p, void *ws, size_t bytes,
     const int threads = p.tuning.threads_per_cta;
     prof::Scope ps(prof::kPlan, st);
     qkdrec_status s = p.tuning.stage_depth == 4 ? plan_launch_ch<4>(a, threads, a.CS, p.n_items, st)
-                                                : plan_launch_ch<8>(a, threads, a.CS, p.n_items, st);
+                                                : plan_launch_ch<6>(a, threads, a.CS, p.n_items, st);
     if (s != QKDREC_OK) return s;
     QKD_LAUNCHED("plan_layered_kernel");
     return QKDREC_OK;
@@ -407,7 +438,7 @@ void qkdrec_tuning_default(qkdrec_tuning *t) {
     if (!t) return;
     t->frames_per_tile = 32;
     t->threads_per_cta = 512;
-    t->stage_depth = 8;
+    t->stage_depth = 6;
     t->ctas_per_tile = 4;
 }
 

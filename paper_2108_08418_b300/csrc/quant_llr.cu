@@ -59,6 +59,8 @@ struct __align__(8) LlrParams {
 };
 
 constexpr float kSkipNats = 25.0f;   // terms below e^-25 of the set's nearest term are dropped
+constexpr float kSkipLinNats = 16.0f;  // same, in the linear-domain sums (<= 2^m e^-16 relative)
+constexpr float kLinDist = 9.0f;     // nearest terms within 9 sigma: P >= ~1e-19, sums in linear FP32
 constexpr float kFarNats = 50.0f;    // both sets below e^-50: the set sums are redone in FP64
 constexpr float kLn05 = -0.69314718055994531f;
 
@@ -96,6 +98,16 @@ __device__ __forceinline__ double logp64(double a, double b) {
     return ln + log(-expm1(log_q64(df) - ln));
 }
 
+// P(k | x) in linear FP32 for standardised bounds a < b, from the complementary
+// error function on the side away from x (no cancellation except inside the
+// containing interval, where P is at least the interval's width-scaled mass).
+__device__ __forceinline__ float p_lin32(float a, float b) {
+    const float r2 = 0.70710678118654752f;
+    if (a >= 0.0f) return 0.5f * (erfcf(a * r2) - erfcf(b * r2));
+    if (b <= 0.0f) return 0.5f * (erfcf(-b * r2) - erfcf(-a * r2));
+    return 1.0f - 0.5f * (erfcf(-a * r2) + erfcf(b * r2));
+}
+
 // standardised distance from x to interval k (0 if x lies inside)
 __device__ __forceinline__ float interval_dist(const LlrParams &p, int k, float x) {
     float a = (p.tf[k] - x) * p.inv_sigma;
@@ -122,6 +134,26 @@ __device__ __forceinline__ float llr_one(const LlrParams &p, float x, int low) {
         const float d = interval_dist(p, k, x);
         const int b = u & 1;
         if (d < dmin[b]) { dmin[b] = d; kmin[b] = k; }
+    }
+    if (fmaxf(dmin[0], dmin[1]) <= kLinDist) {
+        // both nearest terms are ordinary floats: plain sums of P(k | x), terms
+        // below e^-16 of their set's nearest term dropped
+        const float pn0 = p_lin32((p.tf[kmin[0]] - x) * p.inv_sigma, (p.tf[kmin[0] + 1] - x) * p.inv_sigma);
+        const float pn1 = p_lin32((p.tf[kmin[1]] - x) * p.inv_sigma, (p.tf[kmin[1] + 1] - x) * p.inv_sigma);
+        const float cut0 = logf(pn0) - kSkipLinNats, cut1 = logf(pn1) - kSkipLinNats;
+        float s0 = pn0, s1 = pn1;
+        for (int u = 0; u < nc; ++u) {
+            const int k = p.k_of_label[(u << p.j) | low];
+            const int b = u & 1;
+            if (k == kmin[b]) continue;
+            const float d = interval_dist(p, k, x);
+            const float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
+            if (bound < (b ? cut1 : cut0)) continue;
+            const float t = p_lin32((p.tf[k] - x) * p.inv_sigma, (p.tf[k + 1] - x) * p.inv_sigma);
+            if (b) s1 += t;
+            else s0 += t;
+        }
+        return fminf(fmaxf(logf(s0) - logf(s1), -kLlrClip), kLlrClip);
     }
     const float lpn0 = lp_interval32(p, kmin[0], x), lpn1 = lp_interval32(p, kmin[1], x);
     // a set whose whole mass is provably more than the clip below the other's

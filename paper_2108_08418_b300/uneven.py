@@ -25,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import DecodeOpts, Plan, qkdrec_quantise_slices_frames, qkdrec_slice_llr_frames, qkdrec_syndrome
-from . import quantiser_range
+from . import qkdrec_quantise_slices, qkdrec_slice_llr, quantiser_range
 
 
 def _torch():
@@ -69,7 +69,7 @@ class UnevenBatch:
         self.opts = DecodeOpts(algo="oms_layered", prec="f32", max_iter=max_iter, offset=offset, early_stop=True)
         self.codes = codes
         # per slice: groups (runs of frames with one code) and disclosed sample ranges
-        self.groups, self.disclosed, self.synd, self.plans = [], [], [], []
+        self.groups, self.disclosed, self.synd, self.plans, self.llr_runs = [], [], [], [], []
         for j in range(self.m):
             runs, opened = [], []
             f = 0
@@ -97,6 +97,14 @@ class UnevenBatch:
                                    iters=self.iters[j, f:g], conv=self.conv[j, f:g]))
                 so += nf * c.M
             self.groups.append(groups)
+            # runs of consecutive decoded frames: the only frames that need slice-j LLRs
+            runs_j = []
+            for f, g, _ in runs:
+                if runs_j and runs_j[-1][1] == f:
+                    runs_j[-1][1] = g
+                else:
+                    runs_j.append([f, g])
+            self.llr_runs.append(runs_j)
             self.disclosed.append(opened)
             self.synd.append(synd)
             self.plans.append(Plan(groups, self.opts, tuning))
@@ -113,9 +121,11 @@ class UnevenBatch:
                 nf, n = g["f1"] - g["f0"], g["code"].n
                 qkdrec_syndrome(g["code"], self.bob[j, g["a"]:g["b"]].view(nf, n), out=g["synd"])
         for j in range(self.m):
-            qkdrec_slice_llr_frames(self.x, self.d_off, self.d_params, self.m, j,
-                                    self.alice[:j] if j else None, self.label, out=self.llr)
-            self.plans[j].launch(self.ws)
+            for f, g in self.llr_runs[j]:
+                qkdrec_slice_llr_frames(self.x, self.d_off[f:g + 1], self.d_params[f:g], self.m, j,
+                                        self.alice[:j] if j else None, self.label, out=self.llr)
+            if self.groups[j]:
+                self.plans[j].launch(self.ws)
             for a, b in self.disclosed[j]:
                 self.alice[j, a:b].copy_(self.bob[j, a:b])
 
@@ -127,8 +137,12 @@ class UnevenBatch:
         torch.cuda.synchronize(self.device)
         for j, p in enumerate(self.plans):
             # the plan of slice j decodes the LLRs of slice j: recompute them first
-            qkdrec_slice_llr_frames(self.x, self.d_off, self.d_params, self.m, j, self.alice[:j] if j else None,
-                                    self.label, out=self.llr)
+            for f, g in self.llr_runs[j]:
+                qkdrec_slice_llr_frames(self.x, self.d_off[f:g + 1], self.d_params[f:g], self.m, j,
+                                        self.alice[:j] if j else None, self.label, out=self.llr)
+            if not self.groups[j]:
+                out.append((None, 0.0))
+                continue
             out.append(p.autotune(self.ws, max_iter))
             p.launch(self.ws)
         torch.cuda.synchronize(self.device)
@@ -185,3 +199,73 @@ class UnevenBatch:
             p.destroy()
         self.plans = []
         self.graph = None
+
+
+# ------------------------------------------------------------- rate back-off
+def backoff_rates(points, start_rate, codes_for, sample, trial_frames: int = 32, max_fail: int = 1,
+                  step: float = 3 / 64, min_rate: float = 0.10, m_slices: int = 5, label: str = "gray",
+                  max_iter: int = 50, offset: float = 0.5, tuning: dict | None = None, device="cuda",
+                  va: float = 1.0):
+    """Code-rate back-off on trial frames (Sec. V-B: pick the rate closest to
+    capacity, test whether the code fails too often, else lower the rate by a
+    fixed step and test again).
+
+    points      list of (n, snr, j): block length, SNR, slice
+    start_rate  dict point -> first rate tried (on the 1/64 grid)
+    codes_for   callable: set of (n, rate) -> dict (n, rate) -> Code
+    sample      callable: point -> (x, y) float32 arrays of trial_frames * n samples
+    Each point's trial frames are quantised and their slice-j LLRs formed with
+    Bob's own lower slices (lower slices reconciled); every round decodes all
+    pending points in one plan launch (layered offset min-sum) and lowers the
+    rate of each point with more than `max_fail` frame errors by `step`
+    (rounded to 1/64).  A rate below `min_rate` means the slice is disclosed.
+    Returns dict point -> (rate, frame errors of the accepted rate); rate 0.0
+    = disclosed.
+    """
+    torch = _torch()
+    dev = torch.device(device)
+    opts = DecodeOpts(algo="oms_layered", prec="f32", max_iter=max_iter, offset=offset, early_stop=True)
+    trial = {}
+    for p in points:
+        n, snr, j = p
+        x, y = sample(p)
+        lo, hi = quantiser_range(snr, va)
+        xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
+        yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).to(dev)
+        _, bits = qkdrec_quantise_slices(yd, m_slices, lo, hi, label, want_idx=False)
+        llr = qkdrec_slice_llr(xd, m_slices, j, lo, hi, snr ** -0.5, bits[:j] if j else None, label)
+        trial[p] = (llr.view(trial_frames, n), bits[j].reshape(trial_frames, n).contiguous())
+    rate = {p: float(start_rate[p]) for p in points}
+    done = {}
+    for p in points:
+        if rate[p] < min_rate:
+            done[p] = (0.0, 0)
+    pending = [p for p in points if p not in done]
+    while pending:
+        codes = codes_for({(p[0], rate[p]) for p in pending})
+        groups = []
+        for p in pending:
+            c = codes[(p[0], rate[p])]
+            llr, bob = trial[p]
+            groups.append(dict(code=c, llr=llr, synd=qkdrec_syndrome(c, bob),
+                               bits=torch.empty_like(bob),
+                               iters=torch.empty(trial_frames, dtype=torch.int32, device=dev),
+                               conv=torch.empty(trial_frames, dtype=torch.uint8, device=dev)))
+        plan = Plan(groups, opts, tuning)
+        plan.launch(plan.workspace(dev))
+        torch.cuda.synchronize(dev)
+        fails = [int((g["bits"] != trial[p][1]).any(dim=1).sum().item()) for p, g in zip(pending, groups)]
+        plan.destroy()
+        nxt = []
+        for p, f in zip(pending, fails):
+            if f <= max_fail:
+                done[p] = (rate[p], f)
+                continue
+            r = np.floor((rate[p] - step) * 64 + 0.5) / 64
+            if r < min_rate:
+                done[p] = (0.0, f)
+            else:
+                rate[p] = float(r)
+                nxt.append(p)
+        pending = nxt
+    return done

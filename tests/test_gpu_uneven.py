@@ -154,3 +154,45 @@ def test_uneven_frames_vs_oracle_reconciliation():
                 agreed += 1
                 assert np.array_equal(alice[j, a:b], mine[j]), (f, j)
     assert agreed >= 3
+
+
+def test_backoff_rates_accept_only_rates_whose_trials_pass():
+    from paper_2108_08418_b300.uneven import backoff_rates
+    T = 16
+    points = [(1024, 3.0, 2), (1024, 3.0, 3), (2048, 12.0, 4), (1024, 2.0, 0)]
+    start = {}
+    for p in points:
+        lo, hi = q.quantiser_range(p[1])
+        start[p] = min(int(np.floor(0.95 * q.qkdrec_slice_capacity(p[1], M_SLICES, p[2], lo, hi) * 64 + 0.5)), 60) / 64
+    cache, csr = {}, {}
+
+    def codes_for(keys):
+        for i, (n, r) in enumerate(sorted(keys)):
+            if (n, r) not in cache:
+                rp, ci, _ = synth.make_regular_code(7000 + int(r * 64), n, synth.checks_for_rate(n, r))
+                csr[(n, r)] = (rp, ci)
+                cache[(n, r)] = q.Code(n, rp, ci)
+        return cache
+
+    def sample(p):
+        return synth.gaussian_pair(8000 + p[0] // 1024 + int(p[1]), T * p[0], p[1])
+
+    got = backoff_rates(points, start, codes_for, sample, trial_frames=T, max_fail=1)
+    for p in points:
+        rate, fails = got[p]
+        assert rate <= start[p]
+        assert rate == 0.0 or (rate >= 0.10 and fails <= 1)
+        if rate > 0:
+            # the accepted code decodes the trial frames with at most one frame error
+            n, snr, j = p
+            x, y = sample(p)
+            lo, hi = q.quantiser_range(snr)
+            _, bits = q.qkdrec_quantise_slices(torch.from_numpy(y).cuda(), M_SLICES, lo, hi, want_idx=False)
+            llr = q.qkdrec_slice_llr(torch.from_numpy(x).cuda(), M_SLICES, j, lo, hi, snr ** -0.5,
+                                     bits[:j] if j else None)
+            c = cache[(n, rate)]
+            bob = bits[j].reshape(T, n).contiguous()
+            out = q.qkdrec_decode_batch(c, llr.view(T, n), q.qkdrec_syndrome(c, bob),
+                                        q.DecodeOpts(algo="oms_layered", max_iter=50))
+            assert int((out["bits"] != bob).any(dim=1).sum()) == fails
+    assert got[(1024, 2.0, 0)][0] == 0.0          # the LSB at SNR 2 carries almost nothing: disclosed
