@@ -64,17 +64,19 @@ def slice_rates(snr, capacity_fn):
 
 
 def _make_code(args):
-    logn, j, rate = args
+    logn, j, rate, by_rate = args
     n = 1 << logn
     M = synth.checks_for_rate(n, rate)
-    rp, ci, res = synth.make_regular_code(code_seed(logn, j), n, M)
-    return (logn, j, rate), (rp, ci, res)
+    seed = uneven_code_seed(n, rate) if by_rate else code_seed(logn, j)
+    rp, ci, res = synth.make_regular_code(seed, n, M)
+    return (logn, j, rate), (rp, ci, res, seed)
 
 
-def build_codes(jobs, workers):
+def build_codes(jobs, workers, by_rate=False):
     """Construct the parity-check matrices in a spawn pool (before any CUDA use)."""
     import multiprocessing as mp
     out = {}
+    jobs = [(*jb, by_rate) for jb in sorted(jobs, key=lambda t: -t[0])]
     if workers <= 1:
         for jb in jobs:
             k, v = _make_code(jb)
@@ -82,7 +84,7 @@ def build_codes(jobs, workers):
         return out
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        for k, v in pool.imap_unordered(_make_code, sorted(jobs, key=lambda t: -t[0])):
+        for k, v in pool.imap_unordered(_make_code, jobs):
             out[k] = v
     return out
 
@@ -161,19 +163,32 @@ def _oracle_frame(task):
     return good, time.perf_counter() - t0
 
 
-def oracle_sample(step, budget_frames, cores):
+def load_sweep_rates():
+    try:
+        t = json.load(open(SWEEP_RATES))
+    except OSError:
+        raise SystemExit(f"{SWEEP_RATES} missing: run python bench.py --calibrate")
+    return {(float(r[0]), int(r[1]), int(r[2])): float(r[3]) for r in t["rates"]}
+
+
+def oracle_sample(step, budget_frames, cores, rate_of=None):
     """A bounded sample of the sweep: `budget_frames` sub-blocks of n = 2^12 per SNR
-    (frames step*budget .. ), each reconciled over all 5 slices by the oracle."""
+    (frames step*budget .. ), each reconciled over all 5 slices by the oracle
+    (rates: 0.95 x capacity, or the back-off table `rate_of`)."""
     import multiprocessing as mp
     import oracle
     tasks = []
     for snr in SNRS:
-        _, rates = slice_rates(snr, lambda s, m, j, lo, hi: oracle.slice_capacity(s, m, j))
+        if rate_of is None:
+            _, rates = slice_rates(snr, lambda s, m, j, lo, hi: oracle.slice_capacity(s, m, j))
+        else:
+            rates = [rate_of[(snr, 12, j)] for j in range(M_SLICES)]
         codes = {}
         for j in range(M_SLICES):
             if rates[j] > 0:
                 M = synth.checks_for_rate(1 << 12, rates[j])
-                rp, ci, _ = synth.make_regular_code(code_seed(12, j), 1 << 12, M)
+                seed = code_seed(12, j) if rate_of is None else uneven_code_seed(1 << 12, rates[j])
+                rp, ci, _ = synth.make_regular_code(seed, 1 << 12, M)
                 codes[j] = (rp, ci)
         for f in range(budget_frames):
             tasks.append((snr, 12, step * budget_frames + f, rates, codes))
@@ -197,6 +212,7 @@ UNEVEN_MAX_ITER = 50
 UNEVEN_SEED = 11
 UNEVEN_SNR_BIN = 1.0            # rates are set per (n, slice, SNR bin [2,3), [3,4), ..., [14,15])
 UNEVEN_RATES = os.path.join(ROOT, "uneven_rates.json")
+SWEEP_RATES = os.path.join(ROOT, "sweep_rates.json")
 UNEVEN_WORKLOAD = ("uneven batch: 4096 frames, n in {4096, 16384, 65536}, SNR uniform on the 0.1 grid of 2..15, "
                    "5 Gray slices, per (n, slice, SNR bin of width 1) rate from the Sec. V-B back-off (start 0.95 x "
                    "capacity at the bin's lowest SNR, minus 3/64 while > 1 of 32 trial frames fail; below 0.10: "
@@ -280,19 +296,32 @@ def _trial_sample(point):
     return x, y
 
 
+def _sweep_trial_sample(point):
+    n, snr, j = point
+    return synth.gaussian_pair(700_000 + 100 * int(n).bit_length() + int(snr), 32 * n, snr)
+
+
 def run_calibrate(args):
-    """Sec. V-B back-off for every (n, slice, SNR bin) of the uneven workload on
-    32 trial frames at the bin's lowest SNR; writes the rate table."""
+    """Sec. V-B back-off on 32 trial frames per point; writes the rate table.
+    uneven: every (n, slice, SNR bin), trial frames at the bin's lowest SNR;
+    sweep: every (SNR, n, slice) of the block-size sweep."""
     cores = len(os.sched_getaffinity(0))
     workers = max(1, min(cores, 16))
     import paper_2108_08418_b300 as q
     from paper_2108_08418_b300 import build as qbuild
     qbuild.build()
-    nbins = int((UNEVEN_SNR[1] - UNEVEN_SNR[0]) / UNEVEN_SNR_BIN)
-    lows = [uneven_bin_low(b) for b in range(nbins)]
-    caps = dict(_pool_map(_capacity_row, lows, workers))
-    points = [(n, s, j) for n in UNEVEN_LENGTHS for s in lows for j in range(M_SLICES)]
-    start = {p: uneven_start_rate(caps[p[1]][p[2]]) for p in points}
+    if args.workload == "sweep":
+        points = [(1 << ln, snr, j) for snr in SNRS for ln in LOGNS for j in range(M_SLICES)]
+        rates0 = {snr: slice_rates(snr, q.qkdrec_slice_capacity)[1] for snr in SNRS}
+        start = {p: rates0[p[1]][p[2]] for p in points}
+        sample, lows = _sweep_trial_sample, None
+    else:
+        nbins = int((UNEVEN_SNR[1] - UNEVEN_SNR[0]) / UNEVEN_SNR_BIN)
+        lows = [uneven_bin_low(b) for b in range(nbins)]
+        caps = dict(_pool_map(_capacity_row, lows, workers))
+        points = [(n, s, j) for n in UNEVEN_LENGTHS for s in lows for j in range(M_SLICES)]
+        start = {p: uneven_start_rate(caps[p[1]][p[2]]) for p in points}
+        sample = _trial_sample
     import torch
     from paper_2108_08418_b300.uneven import backoff_rates
     torch.cuda.set_device(0)
@@ -305,18 +334,27 @@ def run_calibrate(args):
         return cache
 
     t0 = time.time()
-    got = backoff_rates(points, start, codes_for, _trial_sample, trial_frames=32, max_fail=1, step=3 / 64,
+    got = backoff_rates(points, start, codes_for, sample, trial_frames=32, max_fail=1, step=3 / 64,
                         min_rate=0.10, m_slices=M_SLICES, max_iter=UNEVEN_MAX_ITER, offset=0.5)
-    rows = [[p[0], int(uneven_bin(p[1])), p[2], got[p][0], got[p][1], start[p]] for p in points]
-    out = {"procedure": "Sec. V-B back-off: start at 0.95 x slice capacity (1/64 grid, <= 60/64) at the bin's "
-                        "lowest SNR; 32 trial frames (seed 600000 + 100 bin + bitlength(n)), Bob's lower slices; "
-                        "layered offset min-sum <= 50 iterations; lower the rate by 3/64 while more than 1 frame "
-                        "fails; below 0.10 the slice is disclosed (rate 0)",
-           "command": "python bench.py --workload uneven --calibrate",
-           "columns": ["n", "snr_bin", "slice", "rate", "trial_frame_errors", "start_rate"],
-           "snr_bins": [[lo, lo + UNEVEN_SNR_BIN] for lo in lows],
-           "seconds": round(time.time() - t0, 1), "rates": rows}
-    with open(args.rates_out or UNEVEN_RATES, "w") as fh:
+    if args.workload == "sweep":
+        rows = [[p[1], p[0].bit_length() - 1, p[2], got[p][0], got[p][1], start[p]] for p in points]
+        out = {"procedure": "Sec. V-B back-off: start at the sweep's rate (0.95 x slice capacity, 1/64 grid, "
+                            "<= 63/64); 32 trial frames (seed 700000 + 100 bitlength(n) + SNR), Bob's lower "
+                            "slices; layered offset min-sum <= 50 iterations; lower the rate by 3/64 while more "
+                            "than 1 frame fails; below 0.10 the slice is disclosed (rate 0)",
+               "command": "python bench.py --calibrate",
+               "columns": ["snr", "log2_n", "slice", "rate", "trial_frame_errors", "start_rate"]}
+    else:
+        rows = [[p[0], int(uneven_bin(p[1])), p[2], got[p][0], got[p][1], start[p]] for p in points]
+        out = {"procedure": "Sec. V-B back-off: start at 0.95 x slice capacity (1/64 grid, <= 60/64) at the "
+                            "bin's lowest SNR; 32 trial frames (seed 600000 + 100 bin + bitlength(n)), Bob's "
+                            "lower slices; layered offset min-sum <= 50 iterations; lower the rate by 3/64 while "
+                            "more than 1 frame fails; below 0.10 the slice is disclosed (rate 0)",
+               "command": "python bench.py --workload uneven --calibrate",
+               "columns": ["n", "snr_bin", "slice", "rate", "trial_frame_errors", "start_rate"],
+               "snr_bins": [[lo, lo + UNEVEN_SNR_BIN] for lo in lows]}
+    out.update({"seconds": round(time.time() - t0, 1), "rates": rows})
+    with open(args.rates_out or (SWEEP_RATES if args.workload == "sweep" else UNEVEN_RATES), "w") as fh:
         json.dump(out, fh, indent=0)
     print(json.dumps({"calibrated_points": len(rows), "seconds": out["seconds"],
                       "disclosed": sum(1 for r in rows if r[3] == 0.0)}), flush=True)
@@ -522,6 +560,12 @@ def roofline(stats, steps):
 
 
 # ------------------------------------------------------------------ GPU arm
+# --decoder: the block-size sweep decoded with another form (the precision study)
+DECODERS = {"sp_f32": ("sp_flood", "f32"), "sp_f16": ("sp_flood", "f16"), "oms_f32": ("oms_flood", "f32"),
+            "oms_f16": ("oms_flood", "f16"), "oms_i8": ("oms_flood", "i8"), "layered_f32": ("oms_layered", "f32"),
+            "layered_f16": ("oms_layered", "f16"), "layered_i8": ("oms_layered", "i8")}
+
+
 def run_ours(args):
     rank, world, local = rank_env()
     cores = len(os.sched_getaffinity(0))
@@ -529,14 +573,19 @@ def run_ours(args):
     import paper_2108_08418_b300 as q
     from paper_2108_08418_b300 import build as qbuild
     qbuild.build()
-    rates = {snr: slice_rates(snr, q.qkdrec_slice_capacity)[1] for snr in SNRS}
-    jobs = {(logn, j, rates[snr][j]) for snr in SNRS for logn in LOGNS for j in range(M_SLICES)
-            if rates[snr][j] > 0}
+    if args.rate_rule == "backoff":
+        # the sweep's frames at the Sec. V-B back-off rates (table written by --calibrate)
+        rate_of = load_sweep_rates()
+    else:
+        base = {snr: slice_rates(snr, q.qkdrec_slice_capacity)[1] for snr in SNRS}
+        rate_of = {(snr, ln, j): base[snr][j] for snr in SNRS for ln in LOGNS for j in range(M_SLICES)}
+    jobs = {(ln, j, r) for (snr, ln, j), r in rate_of.items() if r > 0}
     t_setup = time.time()
-    codes_h = build_codes(jobs, max(1, min(cores, 16)))
+    codes_h = build_codes(jobs, max(1, min(cores, 16)), args.rate_rule == "backoff")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        good, wall, nfr = oracle_sample(0, max(1, min(cores, 8) // 2), cores)
+        good, wall, nfr = oracle_sample(0, max(1, min(cores, 8) // 2), cores,
+                                        rate_of if args.rate_rule == "backoff" else None)
         cpu = {"value": good / wall, "unit": "bit/s", "cores": min(cores, nfr), "kind": "oracle",
                "sample": f"{nfr} sub-blocks of n=4096 ({nfr // 2} per SNR), each reconciled over all 5 slices "
                          f"(FP64 quantiser, LLR, syndrome, sum-product <= 100 iterations), one process per sub-block",
@@ -548,7 +597,7 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    codes = {k: q.Code(1 << k[0], v[0], v[1], seed=code_seed(k[0], k[1])) for k, v in codes_h.items()}
+    codes = {k: q.Code(1 << k[0], v[0], v[1], seed=v[3]) for k, v in codes_h.items()}
     residual = max(v[2] for v in codes_h.values())
 
     # data: rank r reconciles its own block (weak scaling)
@@ -559,7 +608,10 @@ def run_ours(args):
         host_y[snr] = torch.from_numpy(y).pin_memory()
         dx[snr] = host_x[snr].to(dev)
         dy[snr] = host_y[snr].to(dev)
-    opts = q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=MAX_ITER, early_stop=True)
+    algo, prec = DECODERS[args.decoder]
+    # low-precision forms re-decode the frames they leave unsatisfied in FP32
+    opts = q.DecodeOpts(algo=algo, prec=prec, max_iter=MAX_ITER, early_stop=True,
+                        fallback_f32=(args.fallback if prec != "f32" else False))
     ws_bytes = max(q.qkdrec_decode_workspace_size(c, N_SAMPLES >> k[0], opts) for k, c in codes.items())
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     # per point: Alice's reconciled planes and decoder side outputs
@@ -584,7 +636,7 @@ def run_ours(args):
                 n, F = 1 << ln, N_SAMPLES >> ln
                 a = alice[(snr, ln)]
                 for j in range(M_SLICES):
-                    r = rates[snr][j]
+                    r = rate_of[(snr, ln, j)]
                     if r <= 0:
                         a[j].copy_(bits[j])          # disclosed slice: Bob's bits in the clear
                         continue
@@ -619,13 +671,13 @@ def run_ours(args):
 
     # correctness of the last step: frames whose decoded word equals Bob's
     good_bits, raw_bits, fer = 0, 0, {}
-    edge_updates = sum(v["units"] for k, v in stats.items() if k.startswith("check_flood")) / args.steps
+    edge_updates = sum(v["units"] for k, v in stats.items() if k.startswith(("check_flood", "layer_oms"))) / args.steps
     for snr in SNRS:
         for ln in LOGNS:
             n, F = 1 << ln, N_SAMPLES >> ln
             errs = []
             for j in range(M_SLICES):
-                if rates[snr][j] <= 0:
+                if rate_of[(snr, ln, j)] <= 0:
                     continue
                 bad = (alice[(snr, ln)][j].view(F, n) != bob[snr][j].view(F, n)).any(dim=1)
                 nbad = int(bad.sum().item())
@@ -670,11 +722,18 @@ def run_ours(args):
     line = {
         "metric": "reconciled key bits/s", "value": value, "unit": "bit/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"f32": "f32", "f16": "f16+f32", "i8": "i8"}[prec],
         "data": "synthetic: seeded Philox Gaussian quadratures and seeded regular dv=3 LDPC codes",
-        "config": {"workload": WORKLOAD, "samples_per_snr": N_SAMPLES, "snr": list(SNRS),
-                   "sub_block_log2": list(LOGNS), "slices": M_SLICES, "algo": "sp_flood", "prec": "f32",
-                   "max_iter": MAX_ITER, "rates": {str(int(s)): rates[s] for s in SNRS},
+        "config": {"workload": WORKLOAD if args.decoder == "sp_f32" else
+                   WORKLOAD.replace("FP32 sum-product flooding", f"decoder {args.decoder} (failed frames re-decoded "
+                                                                 f"in FP32, {args.fallback} algorithm)"
+                                    if opts.fallback_f32 else args.decoder),
+                   "samples_per_snr": N_SAMPLES, "snr": list(SNRS),
+                   "sub_block_log2": list(LOGNS), "slices": M_SLICES, "algo": algo, "prec": prec,
+                   "fallback_f32": opts.fallback_f32,
+                   "max_iter": MAX_ITER, "rate_rule": args.rate_rule if args.rate_rule == "backoff" else "0.95 x capacity",
+                   "rates": {f"snr{int(s)}_n2^{ln}": [rate_of[(s, ln, j)] for j in range(M_SLICES)]
+                             for s in SNRS for ln in LOGNS},
                    "l2": "inputs larger than L2 (x, y 512 MiB each per SNR; edge messages up to 1.5 GiB)",
                    "raw_decoded_bits_per_s": raw_bits / (ms_step / 1e3),
                    "edge_updates_per_s": edge_updates * world / (ms_step / 1e3),
@@ -720,11 +779,12 @@ def run_reference(args):
         run_reference_uneven(args, world, cores)
         return
     per_snr = max(1, min(cores, 8) // 2)
+    rate_of = load_sweep_rates() if args.rate_rule == "backoff" else None
     for w in range(args.warmup):
-        oracle_sample(w, per_snr, cores)
+        oracle_sample(w, per_snr, cores, rate_of)
     goods, walls, nfr = 0, 0.0, 0
     for s in range(args.steps):
-        g, wall, n = oracle_sample(args.warmup + s, per_snr, cores)
+        g, wall, n = oracle_sample(args.warmup + s, per_snr, cores, rate_of)
         goods += g
         walls += wall
         nfr = n
@@ -847,11 +907,19 @@ def main():
     ap.add_argument("--workload", choices=["sweep", "uneven"], default="sweep",
                     help="sweep: the block-size sweep (default); uneven: the one-graph uneven batch")
     ap.add_argument("--calibrate", action="store_true",
-                    help="with --workload uneven: run the rate back-off and write uneven_rates.json")
+                    help="run the rate back-off of the workload and write its table (sweep_rates.json, "
+                         "uneven_rates.json)")
     ap.add_argument("--rates-out", help="where --calibrate writes the table (default: uneven_rates.json)")
-    ap.add_argument("--rate-rule", choices=["backoff", "capacity"], default="backoff",
-                    help="uneven workload: back-off table (default) or 0.95 x capacity per frame")
+    ap.add_argument("--decoder", choices=sorted(DECODERS), default="sp_f32",
+                    help="sweep workload: decoder form (default FP32 sum-product; others re-decode failures in FP32)")
+    ap.add_argument("--fallback", choices=["sp", "same"], default="sp",
+                    help="low-precision decoders: re-decode failed frames with FP32 sum-product (default) or "
+                         "with the same algorithm in FP32")
+    ap.add_argument("--rate-rule", choices=["backoff", "capacity"], default=None,
+                    help="rates: the back-off table or 0.95 x capacity (defaults: sweep capacity, uneven backoff)")
     args = ap.parse_args()
+    if args.rate_rule is None:
+        args.rate_rule = "capacity" if args.workload == "sweep" else "backoff"
     if args.case:
         run_case(args)
         return
@@ -859,7 +927,7 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "uneven" and args.calibrate:
+    elif args.calibrate:
         run_calibrate(args)
     elif args.workload == "uneven":
         run_uneven(args)

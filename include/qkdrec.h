@@ -164,8 +164,9 @@ typedef struct {
     float offset;          /* OMS offset beta (float modes); default 0.5 */
     float llr_step;        /* integer mode: LSB of the 6-bit LLR grid; default 0.5 (offset = 1 LSB) */
     int32_t early_stop;    /* 1: stop each frame at the first satisfied syndrome */
-    int32_t fallback_f32;  /* 1: frames a low-precision decode leaves unsatisfied are
-                              decoded again with FP32 messages (same algorithm) */
+    int32_t fallback_f32;  /* frames a low-precision decode leaves unsatisfied are decoded
+                              again in FP32: 0 never, 1 with the same algorithm,
+                              2 with FP32 sum-product flooding (the plain form) */
 } qkdrec_decode_opts;
 
 /* Defaults: SP flooding, FP32, 50 iterations, offset 0.5, step 0.5, early stop on, no fallback. */

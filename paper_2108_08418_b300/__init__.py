@@ -261,11 +261,12 @@ class DecodeOpts:
     offset: float = 0.5
     llr_step: float = 0.5
     early_stop: bool = True
-    fallback_f32: bool = False
+    fallback_f32: bool | str = False    # True / "same": FP32 with the same algorithm; "sp": FP32 sum-product
 
     def c(self) -> DecodeOptsC:
         return DecodeOptsC(_ALGOS[self.algo], _PRECS[self.prec], int(self.max_iter), float(self.offset),
-                           float(self.llr_step), int(bool(self.early_stop)), int(bool(self.fallback_f32)))
+                           float(self.llr_step), int(bool(self.early_stop)),
+                           2 if self.fallback_f32 == "sp" else int(bool(self.fallback_f32)))
 
 
 def qkdrec_decode_workspace_size(code: Code, F: int, opts: DecodeOpts) -> int:

@@ -219,6 +219,8 @@ struct DecArgs {
     unsigned long long *prof;  // (units, bytes) counters of this launch's kernel class, or NULL
     int64_t E;              // edges
     int32_t lgfb;           // log2 of the frame block FB
+    const int32_t *blk;     // frame blocks holding at least one decoding frame, ascending
+    const int32_t *blk_n;   // their number
 };
 
 // Position of (item, frame f) in a frame-block-major array [Fp/FB][items][FB]:
@@ -273,7 +275,9 @@ check_flood_f(DecArgs a) {
     constexpr bool SP_STASH = ALGO == kSP && CACHED && V == 1;
     float *my = stash + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+    const int32_t nblk = *a.blk_n;
+    for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
+        const int64_t fb = __ldg(a.blk + bi);
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         const bool fv_ok = fv < nvec;
         const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
@@ -410,7 +414,9 @@ check_flood_i(DecArgs a) {
     constexpr int CH = chunk_of<V>();
     constexpr int LG = lgfb_of<V>();
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+    const int32_t nblk = *a.blk_n;
+    for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
+        const int64_t fb = __ldg(a.blk + bi);
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         const bool fv_ok = fv < nvec;
         const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
@@ -499,14 +505,20 @@ check_flood_i(DecArgs a) {
 // Four frames per lane.
 template <int PREC>
 __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
-    const int64_t total = (int64_t)a.n * a.FV;
+    // items: (listed frame block, variable, frame vector of the block), the
+    // vectors of one variable and block contiguous in memory
+    const int64_t fbv = (int64_t)1 << (a.lgfb - 2);      // frame vectors per block
+    const int64_t per_blk = (int64_t)a.n * fbv;
+    const int64_t total = per_blk * *a.blk_n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // per updated variable-frame: its messages, its channel LLR, the new posterior
     constexpr unsigned ms = PREC == kF32 ? 4 : (PREC == kF16 ? 2 : 1);
     constexpr unsigned cs = PREC == kI8 ? 1 : 4, ls = PREC == kI8 ? 2 : 4;
     unsigned long long units = 0, bytes = 0;
     for (int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; item < total; item += stride) {
-        const int64_t v = item / a.FV, fv = item - v * a.FV, f0 = 4 * fv;
+        const int64_t bi = item / per_blk, r = item - bi * per_blk;
+        const int64_t v = r / fbv, fv = (int64_t)__ldg(a.blk + bi) * fbv + (r - v * fbv), f0 = 4 * fv;
+        if (f0 >= a.Fp) continue;
         const int64_t bL = fpos(0, a.n, f0, a.lgfb), bM = fpos(0, a.E, f0, a.lgfb);
         if (v == 0 && (fv & 7) == 0 && a.early_stop) a.unsat_next[fv >> 3] = 0;  // next test starts clear
         const uint32_t act = active_bits<4>(a.active + f0);
@@ -674,7 +686,7 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int 
 struct Layout {
     int64_t Fp, FV, W;
     int lgfb;
-    size_t llr_i, L, msg, sbits, active, mask, unsat0, unsat1, iters, total;
+    size_t llr_i, L, msg, sbits, active, mask, unsat0, unsat1, iters, blk, blk_n, total;
 };
 
 // register-cache size of the check kernels for a code: 8 or 32 edges, 0 = reload
@@ -709,19 +721,23 @@ static Layout make_layout(const CodeDev &d, int32_t F, int algo, int prec) {
     l.unsat0 = take((size_t)l.W * 4);
     l.unsat1 = take((size_t)l.W * 4);
     l.iters = take((size_t)l.Fp * 4);
+    l.blk = take((size_t)(l.Fp >> l.lgfb) * 4);
+    l.blk_n = take(4);
     l.total = off;
     return l;
 }
 
 static bool opts_ok(const qkdrec_decode_opts *o) {
     return o && o->algo >= 0 && o->algo <= 2 && o->prec >= 0 && o->prec <= 2 && o->max_iter >= 0 &&
-           isfinite(o->offset) && o->offset >= 0.0f && isfinite(o->llr_step) && o->llr_step > 0.0f;
+           isfinite(o->offset) && o->offset >= 0.0f && isfinite(o->llr_step) && o->llr_step > 0.0f &&
+           o->fallback_f32 >= 0 && o->fallback_f32 <= 2;
 }
 
 static size_t workspace_for(const CodeDev &d, int32_t F, const qkdrec_decode_opts *o) {
     size_t b = make_layout(d, F, o->algo, o->prec).total;
     if (o->fallback_f32 && o->prec != kF32) {
-        size_t b32 = make_layout(d, F, o->algo, kF32).total;
+        const int algo = o->fallback_f32 == 2 ? QKDREC_SP_FLOOD : o->algo;
+        size_t b32 = make_layout(d, F, algo, kF32).total;
         if (b32 > b) b = b32;
     }
     return b;
@@ -737,6 +753,9 @@ struct Geom {
     dim3 grid;
     int fvw;
 };
+// The frame-block dimension of a kernel that walks the block list: enough CTAs
+// to fill the device several times over; they stride over the listed blocks.
+static Geom list_geom(int64_t Fp, int V, int64_t checks);
 static Geom check_geom(int64_t Fp, int V, int64_t checks) {
     Geom g;
     const int64_t nvec = Fp / V;
@@ -746,6 +765,43 @@ static Geom check_geom(int64_t Fp, int V, int64_t checks) {
     const int64_t fblocks = ceil_div(nvec, g.fvw);
     g.grid = dim3((unsigned)ceil_div(checks, per_block), (unsigned)(fblocks < 65535 ? fblocks : 65535));
     return g;
+}
+
+static Geom list_geom(int64_t Fp, int V, int64_t checks) {
+    Geom g = check_geom(Fp, V, checks);
+    const int64_t target = (int64_t)sm_count() * 24;
+    const int64_t gy = std::max<int64_t>(1, ceil_div(target, (int64_t)g.grid.x));
+    if ((int64_t)g.grid.y > gy) g.grid.y = (unsigned)gy;
+    return g;
+}
+
+// Frame blocks that still hold a decoding frame -> a.blk / a.blk_n (order of
+// the list is the order blocks are found in; each block is processed the same
+// way wherever it sits in the list).
+__global__ void build_blocks(const uint8_t *__restrict__ active, int64_t nblk, int lgfb, int32_t *blk,
+                             int32_t *blk_n) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false;
+    if (b < nblk) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(active + (b << lgfb));
+        for (int k = 0; k < (1 << (lgfb - 2)); ++k) any |= w[k] != 0u;
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, any);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && bal) base = atomicAdd(blk_n, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (any) blk[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)b;
+}
+
+static qkdrec_status rebuild_blocks(const Layout &l, char *ws, cudaStream_t st) {
+    const int64_t nblk = l.Fp >> l.lgfb;
+    int32_t *cnt = reinterpret_cast<int32_t *>(ws + l.blk_n);
+    QKD_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), st));
+    build_blocks<<<(unsigned)ceil_div(nblk, 256), 256, 0, st>>>(
+        reinterpret_cast<const uint8_t *>(ws + l.active), nblk, l.lgfb, reinterpret_cast<int32_t *>(ws + l.blk), cnt);
+    QKD_LAUNCHED("build_blocks");
+    return QKDREC_OK;
 }
 
 // Shared set-up of one decode pass: per-frame state, interleaved LLRs and
@@ -781,6 +837,8 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     pr.mask = reinterpret_cast<uint8_t *>(ws + l.mask);
     a.unsat_cur = pr.unsat[0];
     a.unsat_next = pr.unsat[1];
+    a.blk = reinterpret_cast<const int32_t *>(ws + l.blk);
+    a.blk_n = reinterpret_cast<const int32_t *>(ws + l.blk_n);
     {
         prof::Scope ps(prof::kPrep, st);
         init_state<<<(unsigned)ceil_div(std::max<int64_t>(l.Fp, l.W), 256), 256, 0, st>>>(
@@ -803,7 +861,8 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     QKD_LAUNCHED("prep_synd");
     const size_t ms = prec == kF32 ? 4 : (prec == kF16 ? 2 : 1);
     QKD_CUDA(cudaMemsetAsync(ws + l.msg, 0, (size_t)d.E * l.Fp * ms, st));
-    return QKDREC_OK;
+    prof::Scope ps(prof::kPrep, st);
+    return rebuild_blocks(l, ws, st);
 }
 
 // Shared tail: iteration counts / converged flags, then bits and posteriors
@@ -836,7 +895,7 @@ static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const 
 static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaStream_t st) {
     const bool cached = dc_class(d) > 0;
     const int V = a.lgfb == lgfb_of<1>() ? 1 : 4;
-    const Geom g = check_geom(a.Fp, V, d.M);
+    const Geom g = list_geom(a.Fp, V, d.M);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
     const size_t stash = (size_t)kCheckWarps * kStash * 32 * sizeof(float);
@@ -904,6 +963,11 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
             else var_flood<kF32><<<vgrid, 256, 0, st>>>(a);
         }
         QKD_LAUNCHED("var_flood");
+        if (o.early_stop) {
+            // frames retired by this variable pass leave the list
+            prof::Scope ps(prof::kFinish, st);
+            if ((s = rebuild_blocks(l, ws, st)) != QKDREC_OK) return s;
+        }
     }
     // stopping test on the final posteriors (parity buffer (T+1)&1 is clear)
     const int T = o.max_iter;
@@ -981,15 +1045,17 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
     cudaStream_t st = as_stream(stream);
     char *ws = reinterpret_cast<char *>(workspace);
     qkdrec_status s;
-    auto pass = [&](int prec, const uint8_t *conv_prev) {
-        if (o.algo == QKDREC_OMS_LAYERED)
-            return run_layered(d, llr, synd, F, o, prec, conv_prev, bits_out, iters_out, conv_out, post_out, ws, st);
-        return run_flood(d, llr, synd, F, o, prec, conv_prev, bits_out, iters_out, conv_out, post_out, ws, st);
+    auto pass = [&](const qkdrec_decode_opts &po, int prec, const uint8_t *conv_prev) {
+        if (po.algo == QKDREC_OMS_LAYERED)
+            return run_layered(d, llr, synd, F, po, prec, conv_prev, bits_out, iters_out, conv_out, post_out, ws, st);
+        return run_flood(d, llr, synd, F, po, prec, conv_prev, bits_out, iters_out, conv_out, post_out, ws, st);
     };
-    if ((s = pass(o.prec, nullptr)) != QKDREC_OK) return s;
+    if ((s = pass(o, o.prec, nullptr)) != QKDREC_OK) return s;
     // FP32 re-decode of the frames a low-precision pass left unsatisfied
     if (o.fallback_f32 && o.prec != QKDREC_F32) {
-        if ((s = pass(QKDREC_F32, conv_out)) != QKDREC_OK) return s;
+        qkdrec_decode_opts o2 = o;
+        if (o.fallback_f32 == 2) o2.algo = QKDREC_SP_FLOOD;
+        if ((s = pass(o2, QKDREC_F32, conv_out)) != QKDREC_OK) return s;
     }
     return QKDREC_OK;
 }

@@ -30,7 +30,9 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     constexpr bool STASH = CACHED && V == 1;
     float *my = qstash + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+    const int32_t nblk = *a.blk_n;
+    for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
+        const int64_t fb = __ldg(a.blk + bi);
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         if (fv >= nvec) continue;
         const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
@@ -121,7 +123,9 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     constexpr bool STASH = CACHED && V == 1;
     int *my = reinterpret_cast<int *>(qstash) + (warp * kStash) * 32 + lane;
     unsigned long long units = 0;
-    for (int64_t fb = blockIdx.y; fb * fvw < nvec; fb += gridDim.y) {
+    const int32_t nblk = *a.blk_n;
+    for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
+        const int64_t fb = __ldg(a.blk + bi);
         const int64_t fv = fb * fvw + lfv, f0 = fv * V;
         if (fv >= nvec) continue;
         const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);  // item 0 of this lane
@@ -204,7 +208,7 @@ __global__ void retire(int64_t Fp, int64_t W, int32_t t, uint8_t *active, int32_
 
 static void launch_layer(DecArgs a, const CodeDev &d, int prec, int32_t lb, int32_t ls, cudaStream_t st) {
     const int V = a.lgfb == lgfb_of<1>() ? 1 : 4;
-    const Geom g = check_geom(a.Fp, V, ls);
+    const Geom g = list_geom(a.Fp, V, ls);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
     const size_t stash = (size_t)kCheckWarps * kStash * 32 * sizeof(float);
@@ -248,6 +252,8 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *syn
         prof::Scope ps(prof::kFinish, st);
         retire<<<(unsigned)ceil_div(std::max<int64_t>(l.Fp, l.W), 256), 256, 0, st>>>(
             l.Fp, l.W, t, a.active, a.iters_i, pr.unsat[t & 1], pr.unsat[(t + 1) & 1]);
+        // frames retired now leave the block list
+        rebuild_blocks(l, ws, st);
     };
     if (o.early_stop) {
         parity(0);

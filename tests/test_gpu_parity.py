@@ -261,6 +261,29 @@ def test_fp32_redecode_of_failed_frames(prec):
     assert fc.sum() >= lc.sum()
 
 
+@pytest.mark.parametrize("algo,prec", [("oms_flood", "f16"), ("oms_flood", "i8"), ("oms_layered", "i8")])
+def test_sum_product_redecode_of_failed_frames(algo, prec):
+    """Fallback 2: frames the low-precision min-sum pass leaves unsatisfied are
+    decoded again by the plain form (FP32 sum-product flooding)."""
+    n, F = 2048, 64
+    rp, ci, _ = code(150, n, 0.5)
+    b, llr = bpsk_frames(151, F, n, 0.88)
+    c = q.Code(n, rp, ci)
+    s = q.qkdrec_syndrome(c, dev(b))
+    lowp = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo=algo, prec=prec, max_iter=30))
+    sp = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=30))
+    fb = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo=algo, prec=prec, max_iter=30, fallback_f32="sp"))
+    lc = host(lowp["converged"]).astype(bool)
+    assert (~lc).any() and lc.any()
+    assert np.array_equal(host(fb["bits"])[lc], host(lowp["bits"])[lc])
+    redo = ~lc
+    assert np.array_equal(host(fb["bits"])[redo], host(sp["bits"])[redo])
+    assert np.array_equal(host(fb["converged"])[redo], host(sp["converged"])[redo])
+    assert np.array_equal(host(fb["iters"])[redo], host(lowp["iters"])[redo] + host(sp["iters"])[redo])
+    # the combined form fails no frame the plain form decodes
+    assert not np.any(host(sp["converged"]).astype(bool) & ~host(fb["converged"]).astype(bool))
+
+
 # ------------------------------------------------------------------ full pipeline
 def test_config1_pipeline_vs_oracle():
     """x, y at SNR 3, 16 frames x 4096, 4 Gray slices, codes at 0.95 x capacity, SP flooding,
