@@ -559,6 +559,101 @@ def roofline(stats, steps):
     return roof, kernels, launches
 
 
+# ------------------------------------------------ differentiable weighted min-sum
+WOMS_N, WOMS_F, WOMS_T, WOMS_K, WOMS_SNR, WOMS_SLICE = 16384, 1024, 20, 5, 3.0, 4
+WOMS_WORKLOAD = ("weighted offset min-sum training: 1024 frames of n=16384, slice 4 (capacity 0.545) of the 5-slice "
+                 "Gray quantiser at "
+                 "SNR 3, rate-1/2 (dv=3, dc=6) code, 20 unrolled flooding iterations, alpha/beta [20][2], "
+                 "checkpoints every 5, BCE loss, Adam; one step = forward + adjoint + update")
+
+
+def woms_frames(q, torch, code, seed, dev):
+    """Slice LLRs (Bob's lower slices reconciled), Bob's slice bits and syndromes."""
+    x, y = synth.gaussian_pair(seed, WOMS_F * WOMS_N, WOMS_SNR)
+    lo, hi = q.quantiser_range(WOMS_SNR)
+    _, bits = q.qkdrec_quantise_slices(torch.from_numpy(y).to(dev), M_SLICES, lo, hi, want_idx=False)
+    j = WOMS_SLICE
+    target = bits[j].reshape(WOMS_F, WOMS_N).contiguous()
+    llr = q.qkdrec_slice_llr(torch.from_numpy(x).to(dev), M_SLICES, j, lo, hi, WOMS_SNR ** -0.5, bits[:j])
+    return llr.reshape(WOMS_F, WOMS_N), q.qkdrec_syndrome(code, target), target
+
+
+def run_woms(args):
+    rank, world, local = rank_env()
+    import paper_2108_08418_b300 as q
+    from paper_2108_08418_b300 import build as qbuild
+    from paper_2108_08418_b300.woms import woms_loss
+    qbuild.build()
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rp, ci, res = synth.make_regular_code(5000, WOMS_N, synth.checks_for_rate(WOMS_N, 0.5))
+    code = q.Code(WOMS_N, rp, ci, seed=5000)
+    llr, synd, target = woms_frames(q, torch, code, 5 + 1000 * rank, dev)
+    ev_llr, ev_synd, ev_target = woms_frames(q, torch, code, 6 + 1000 * rank, dev)
+    alpha = torch.ones((WOMS_T, 2), device=dev, requires_grad=True)
+    beta = torch.full((WOMS_T, 2), 0.5, device=dev, requires_grad=True)
+    opt = torch.optim.Adam([alpha, beta], lr=0.02)
+
+    def fer(a, b):
+        ws = torch.empty(q.qkdrec_woms_workspace_size(code, WOMS_F, WOMS_T, WOMS_K), dtype=torch.uint8, device=dev)
+        _, post = q.qkdrec_woms_forward(code, ev_llr, ev_synd, ev_target, a.detach().contiguous(),
+                                        b.detach().contiguous(), WOMS_K, ws, want_post=True)
+        return float(((post < 0).to(torch.uint8) != ev_target).any(dim=1).float().mean())
+
+    fer_init = fer(alpha, beta)
+    sp = q.qkdrec_decode_batch(code, ev_llr, ev_synd, q.DecodeOpts(algo="sp_flood", max_iter=WOMS_T, early_stop=False))
+    fer_sp = float((sp["bits"] != ev_target).any(dim=1).float().mean())
+    losses = []
+
+    def step():
+        opt.zero_grad()
+        loss = woms_loss(code, llr, synd, target, alpha, beta, WOMS_K)
+        loss.backward()
+        opt.step()
+        return loss.detach()
+
+    for _ in range(args.warmup):
+        losses.append(float(step()))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(smi_index(torch, dev, local))
+    sampler.start()
+    q.qkdrec_profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    timed = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stats = q.qkdrec_profile_end()
+    clocks = sampler.stop()
+    losses += [float(v) for v in timed]
+    ms = e0.elapsed_time(e1) / args.steps
+    # check edge-updates of one step: the forward, its recomputation and the adjoint
+    upd_units = sum(stats.get(k, {}).get("units", 0) for k in ("woms_check_fwd", "woms_check_bwd")) / args.steps
+    roof, kernels, launches = roofline(stats, args.steps)
+    # a short training run after the timed steps, then the FER of the trained weights
+    for _ in range(max(0, args.train_steps - args.warmup - args.steps)):
+        losses.append(float(step()))
+    fer_trained = fer(alpha, beta)
+    if rank != 0:
+        return
+    line = {
+        "metric": "weighted min-sum training steps/s", "value": 1e3 / ms, "unit": "step/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded Philox Gaussian quadratures and a seeded regular (3,6) LDPC code",
+        "config": {"workload": WOMS_WORKLOAD, "frames": WOMS_F, "n": WOMS_N, "iterations": WOMS_T,
+                   "ckpt_every": WOMS_K, "check_edge_updates_per_s": upd_units / (ms / 1e3),
+                   "loss_first": losses[0], "loss_last": losses[-1], "train_steps": len(losses),
+                   "fer_eval": {"woms_initial": fer_init, "woms_trained": fer_trained, "sum_product_20it": fer_sp},
+                   "l2": "messages 201 MB per copy, checkpoints 805 MB: larger than L2"},
+        "roofline": roof, "kernels": kernels, "cpu_baseline": None,
+        "e2e": None, "gpu_launches": launches * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 # --decoder: the block-size sweep decoded with another form (the precision study)
 DECODERS = {"sp_f32": ("sp_flood", "f32"), "sp_f16": ("sp_flood", "f16"), "oms_f32": ("oms_flood", "f32"),
@@ -838,6 +933,8 @@ CASES = {
     # (rate 0.84375; ~0.9 GB on the device)
     "plan_layered": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
                          tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=6, ctas_per_tile=8)),
+    "plan_layered_cta": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
+                             tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=4, ctas_per_tile=1)),
     "plan_layered_ft32": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
                               tuning=dict(frames_per_tile=32, threads_per_cta=1024, stage_depth=6, ctas_per_tile=8)),
 }
@@ -904,8 +1001,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
     ap.add_argument("--case", choices=sorted(CASES), help="run one small fixed decode (for ncu)")
-    ap.add_argument("--workload", choices=["sweep", "uneven"], default="sweep",
-                    help="sweep: the block-size sweep (default); uneven: the one-graph uneven batch")
+    ap.add_argument("--workload", choices=["sweep", "uneven", "woms"], default="sweep",
+                    help="sweep: the block-size sweep (default); uneven: the one-graph uneven batch; "
+                         "woms: training of the weighted min-sum decoder")
+    ap.add_argument("--train-steps", type=int, default=60, help="woms: training steps before the FER check")
     ap.add_argument("--calibrate", action="store_true",
                     help="run the rate back-off of the workload and write its table (sweep_rates.json, "
                          "uneven_rates.json)")
@@ -931,6 +1030,8 @@ def main():
         run_calibrate(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "woms":
+        run_woms(args)
     else:
         run_ours(args)
 

@@ -127,7 +127,7 @@ def test_full_size_twenty_iterations_checkpoint_five():
     x, y = synth.gaussian_pair(5, F * n, 3.0)
     lo, hi = oracle.quantiser_range(3.0)
     _, bits = q.qkdrec_quantise_slices(dev(y), 5, lo, hi)
-    j = 3
+    j = 4      # the slice whose capacity (0.545) is closest above 0.5/0.95
     target = bits[j].reshape(F, n).contiguous()
     llr = q.qkdrec_slice_llr(dev(x), 5, j, lo, hi, 3.0 ** -0.5, bits[:j]).reshape(F, n)
     s = q.qkdrec_syndrome(c, target)
