@@ -221,6 +221,7 @@ struct DecArgs {
     int32_t lgfb;           // log2 of the frame block FB
     const int32_t *blk;     // frame blocks holding at least one decoding frame, ascending
     const int32_t *blk_n;   // their number
+    int32_t dstash;         // edges per lane in the shared-memory stash (the code's largest check degree)
 };
 
 // Position of (item, frame f) in a frame-block-major array [Fp/FB][items][FB]:
@@ -260,9 +261,9 @@ __device__ __forceinline__ void publish_unsat(uint32_t bits, int64_t f0, int64_t
 constexpr int kStash = 32;
 
 template <int ALGO, typename MsgT, int V, bool CACHED>
-__global__ void __launch_bounds__(kCheckWarps * 32, (ALGO == kSP && V == 1) ? 4 : 3)
+__global__ void __launch_bounds__(kCheckWarps * 32, (ALGO == kSP && V == 1) ? 8 : 3)
 check_flood_f(DecArgs a) {
-    extern __shared__ float stash[];  // SP cached: [kCheckWarps][kStash][32]
+    extern __shared__ float stash[];  // SP cached: [kCheckWarps][dstash][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
@@ -270,10 +271,13 @@ check_flood_f(DecArgs a) {
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
-    constexpr int CH = chunk_of<V>();
+    // sum-product, one frame per lane: two loads in flight per lane and the whole
+    // SM's 64 warps resident hide the gathers better than deeper chunks at lower
+    // occupancy (the kernel is issue-bound, not register-bound)
+    constexpr int CH = (ALGO == kSP && V == 1) ? 2 : chunk_of<V>();
     constexpr int LG = lgfb_of<V>();
     constexpr bool SP_STASH = ALGO == kSP && CACHED && V == 1;
-    float *my = stash + (warp * kStash) * 32 + lane;
+    float *my = stash + (warp * a.dstash) * 32 + lane;
     unsigned long long units = 0;
     const int32_t nblk = *a.blk_n;
     for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
@@ -827,6 +831,7 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     a.n = d.n;
     a.M = d.M;
     a.fvw = 32;
+    a.dstash = kStash;
     a.t = 0;
     a.do_msgs = 1;
     a.early_stop = o.early_stop ? 1 : 0;
@@ -898,7 +903,8 @@ static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaSt
     const Geom g = list_geom(a.Fp, V, d.M);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
-    const size_t stash = (size_t)kCheckWarps * kStash * 32 * sizeof(float);
+    a.dstash = std::min(std::max(d.dc_max, 1), kStash);
+    const size_t stash = (size_t)kCheckWarps * a.dstash * 32 * sizeof(float);
     if (prec == kI8) {
         if (V == 1) check_flood_i<1, 32><<<g.grid, B, 0, st>>>(a);
         else if (cached) check_flood_i<4, 32><<<g.grid, B, 0, st>>>(a);

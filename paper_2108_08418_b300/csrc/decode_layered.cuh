@@ -17,7 +17,7 @@
 template <typename MsgT, int V, bool CACHED>
 __global__ void __launch_bounds__(kCheckWarps * 32, 3)
 layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
-    extern __shared__ float qstash[];  // [kCheckWarps][kStash][32]
+    extern __shared__ float qstash[];  // [kCheckWarps][dstash][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
@@ -28,7 +28,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     constexpr int CH = chunk_of<V>();
     constexpr int LG = lgfb_of<V>();
     constexpr bool STASH = CACHED && V == 1;
-    float *my = qstash + (warp * kStash) * 32 + lane;
+    float *my = qstash + (warp * a.dstash) * 32 + lane;
     unsigned long long units = 0;
     const int32_t nblk = *a.blk_n;
     for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
@@ -110,7 +110,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 template <int V, bool CACHED>
 __global__ void __launch_bounds__(kCheckWarps * 32, 3)
 layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
-    extern __shared__ float qstash[];  // [kCheckWarps][kStash][32], holds ints
+    extern __shared__ float qstash[];  // [kCheckWarps][dstash][32], holds ints
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int fvw = a.fvw, slots = 32 / fvw;
     const int slot = lane / fvw, lfv = lane - slot * fvw;
@@ -121,7 +121,7 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     constexpr int CH = chunk_of<V>();
     constexpr int LG = lgfb_of<V>();
     constexpr bool STASH = CACHED && V == 1;
-    int *my = reinterpret_cast<int *>(qstash) + (warp * kStash) * 32 + lane;
+    int *my = reinterpret_cast<int *>(qstash) + (warp * a.dstash) * 32 + lane;
     unsigned long long units = 0;
     const int32_t nblk = *a.blk_n;
     for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
@@ -211,7 +211,8 @@ static void launch_layer(DecArgs a, const CodeDev &d, int prec, int32_t lb, int3
     const Geom g = list_geom(a.Fp, V, ls);
     a.fvw = g.fvw;
     const dim3 B(kCheckWarps * 32);
-    const size_t stash = (size_t)kCheckWarps * kStash * 32 * sizeof(float);
+    a.dstash = std::min(std::max(d.dc_max, 1), kStash);
+    const size_t stash = (size_t)kCheckWarps * a.dstash * 32 * sizeof(float);
     const int32_t *lc = d.layer_chk;
     if (prec == kI8) {
         if (V == 1) layer_oms_i<1, true><<<g.grid, B, stash, st>>>(a, lc, lb, ls);
