@@ -261,7 +261,7 @@ __device__ __forceinline__ void publish_unsat(uint32_t bits, int64_t f0, int64_t
 constexpr int kStash = 32;
 
 template <int ALGO, typename MsgT, int V, bool CACHED>
-__global__ void __launch_bounds__(kCheckWarps * 32, (ALGO == kSP && V == 1) ? 8 : 3)
+__global__ void __launch_bounds__(kCheckWarps * 32, (ALGO == kSP && V == 1) ? 8 : (ALGO == kOMS && V == 4 ? 4 : 3))
 check_flood_f(DecArgs a) {
     extern __shared__ float stash[];  // SP cached: [kCheckWarps][dstash][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -415,7 +415,7 @@ check_flood_i(DecArgs a) {
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
-    constexpr int CH = chunk_of<V>();
+    constexpr int CH = V == 4 ? 2 : chunk_of<V>();   // measured: two 4-frame loads in flight per lane
     constexpr int LG = lgfb_of<V>();
     unsigned long long units = 0;
     const int32_t nblk = *a.blk_n;

@@ -15,7 +15,7 @@
 // CACHED (degree <= kStash, one frame per lane): the q values of a check are
 // kept in shared memory ([warp][edge][lane]) between the two passes.
 template <typename MsgT, int V, bool CACHED>
-__global__ void __launch_bounds__(kCheckWarps * 32, 3)
+__global__ void __launch_bounds__(kCheckWarps * 32, V == 1 ? 6 : 3)
 layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
     extern __shared__ float qstash[];  // [kCheckWarps][dstash][32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -25,7 +25,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     MsgT *msg = reinterpret_cast<MsgT *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
-    constexpr int CH = chunk_of<V>();
+    constexpr int CH = V == 1 ? 4 : chunk_of<V>();   // 6 blocks per SM at one frame per lane
     constexpr int LG = lgfb_of<V>();
     constexpr bool STASH = CACHED && V == 1;
     float *my = qstash + (warp * a.dstash) * 32 + lane;
@@ -108,7 +108,7 @@ layer_oms_f(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
 
 // ---------------------------------------------------------- integer layered
 template <int V, bool CACHED>
-__global__ void __launch_bounds__(kCheckWarps * 32, 3)
+__global__ void __launch_bounds__(kCheckWarps * 32, V == 1 ? 8 : 3)
 layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t lsize) {
     extern __shared__ float qstash[];  // [kCheckWarps][dstash][32], holds ints
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -118,7 +118,7 @@ layer_oms_i(DecArgs a, const int32_t *__restrict__ lchk, int32_t lbeg, int32_t l
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
     const int64_t nvec = a.Fp / V;
     const uint32_t vmask = (1u << V) - 1u;
-    constexpr int CH = chunk_of<V>();
+    constexpr int CH = V == 1 ? 2 : chunk_of<V>();   // 8 blocks per SM at one frame per lane
     constexpr int LG = lgfb_of<V>();
     constexpr bool STASH = CACHED && V == 1;
     int *my = reinterpret_cast<int *>(qstash) + (warp * a.dstash) * 32 + lane;
