@@ -932,11 +932,11 @@ CASES = {
     # the plan decoder on a small uneven batch: 96 frames of n = 2^16, 192 of 2^14, 384 of 2^12
     # (rate 0.84375; ~0.9 GB on the device)
     "plan_layered": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
-                         tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=6, ctas_per_tile=8)),
+                         tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=4, ctas_per_tile=8)),
     "plan_layered_cta": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
                              tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=4, ctas_per_tile=1)),
     "plan_layered_ft32": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
-                              tuning=dict(frames_per_tile=32, threads_per_cta=1024, stage_depth=6, ctas_per_tile=8)),
+                              tuning=dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=8)),
 }
 
 

@@ -242,7 +242,9 @@ typedef struct {
 /* Launch shape of a plan; the autotuner searches all combinations.
  *   frames_per_tile 8, 16 or 32: frames decoded together (lanes per check)
  *   threads_per_cta 256, 512 or 1024
- *   stage_depth     4 or 6: edge loads in flight per lane
+ *   stage_depth     4, 8 or 16: edge loads in flight per lane; with at most
+ *                   1024, 512 or 256 threads per CTA (a launch outside these
+ *                   pairs returns QKDREC_ERR_UNSUPPORTED)
  *   ctas_per_tile   1, 2, 4 or 8: CTAs of a thread-block cluster sharing one
  *                   tile (they split each layer's checks and meet at the
  *                   cluster barrier after every layer) */
@@ -255,7 +257,7 @@ typedef struct {
 
 typedef struct qkdrec_plan_s *qkdrec_plan_t;
 
-/* Defaults: 32 frames per tile, 512 threads, depth 6, 4 CTAs per tile. */
+/* Defaults: 32 frames per tile, 512 threads, depth 8, 4 CTAs per tile. */
 void qkdrec_tuning_default(qkdrec_tuning *tuning);
 
 /*

@@ -236,8 +236,8 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
 
 // Persistent loop: the team (the whole cluster, or the CTA when CS = 1) takes
 // items from the queue until it is empty.
-template <int CH>
-__global__ void __launch_bounds__(1024, 1)
+template <int CH, int NT>
+__global__ void __launch_bounds__(NT, 1)
 plan_layered_kernel(PlanArgs a) {
     extern __shared__ float qst[];  // [warps][kStash][32]: q stash; 32 x 32 transposes
     __shared__ int s_item;
@@ -285,7 +285,10 @@ namespace qkd {
 
 static const int kPlanFT[] = {8, 16, 32};
 static const int kPlanThreads[] = {256, 512, 1024};
-static const int kPlanDepth[] = {4, 6};
+// load depth x threads per CTA: deeper chunks (fewer dependent round trips per
+// check) need more registers, so they come with smaller CTAs
+static const int kPlanDepth[] = {4, 8, 16};
+static int plan_max_threads(int depth) { return depth == 4 ? 1024 : (depth == 8 ? 512 : 256); }
 static const int kPlanCS[] = {1, 2, 4, 8};
 
 template <size_t N>
@@ -366,14 +369,14 @@ static qkdrec_status plan_build(qkdrec_plan_s &p) {
     return QKDREC_OK;
 }
 
-template <int CH>
+template <int CH, int NT>
 static qkdrec_status plan_launch_ch(const PlanArgs &a, int threads, int CS, int n_items, cudaStream_t st) {
     // up to 1024 threads x 128 B of stash: above the default 48 KB of dynamic shared memory
     static bool attr_set = false;
     const size_t stash = (size_t)(threads / 32) * kStash * 32 * sizeof(float);
     if (!attr_set) {
-        QKD_CUDA(cudaFuncSetAttribute(plan_layered_kernel<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((size_t)(1024 / 32) * kStash * 32 * sizeof(float))));
+        QKD_CUDA(cudaFuncSetAttribute(plan_layered_kernel<CH, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((size_t)(NT / 32) * kStash * 32 * sizeof(float))));
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
@@ -390,17 +393,17 @@ static qkdrec_status plan_launch_ch(const PlanArgs &a, int threads, int CS, int 
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         cfg.gridDim = dim3(CS);
-        QKD_CUDA(cudaOccupancyMaxActiveClusters(&groups_resident, plan_layered_kernel<CH>, &cfg));
+        QKD_CUDA(cudaOccupancyMaxActiveClusters(&groups_resident, plan_layered_kernel<CH, NT>, &cfg));
     } else {
         int per_sm = 0;
-        QKD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<CH>, threads, stash));
+        QKD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plan_layered_kernel<CH, NT>, threads, stash));
         groups_resident = per_sm * sm_count();
     }
     if (groups_resident < 1)
         QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "launch shape %d threads x %d CTAs does not fit", threads, CS);
     const int groups = std::min(groups_resident, n_items);
     cfg.gridDim = dim3((unsigned)(groups * CS));
-    QKD_CUDA(cudaLaunchKernelEx(&cfg, plan_layered_kernel<CH>, a));
+    QKD_CUDA(cudaLaunchKernelEx(&cfg, plan_layered_kernel<CH, NT>, a));
     return QKDREC_OK;
 }
 
@@ -423,8 +426,12 @@ static qkdrec_status plan_launch(const qkdrec_plan_s &p, void *ws, size_t bytes,
     QKD_CUDA(cudaMemsetAsync(p.d_head, 0, sizeof(int32_t), st));
     const int threads = p.tuning.threads_per_cta;
     prof::Scope ps(prof::kPlan, st);
-    qkdrec_status s = p.tuning.stage_depth == 4 ? plan_launch_ch<4>(a, threads, a.CS, p.n_items, st)
-                                                : plan_launch_ch<6>(a, threads, a.CS, p.n_items, st);
+    if (threads > plan_max_threads(p.tuning.stage_depth))
+        QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "load depth %d runs at most %d threads per CTA", p.tuning.stage_depth,
+                 plan_max_threads(p.tuning.stage_depth));
+    qkdrec_status s = p.tuning.stage_depth == 4   ? plan_launch_ch<4, 1024>(a, threads, a.CS, p.n_items, st)
+                      : p.tuning.stage_depth == 8 ? plan_launch_ch<8, 512>(a, threads, a.CS, p.n_items, st)
+                                                  : plan_launch_ch<16, 256>(a, threads, a.CS, p.n_items, st);
     if (s != QKDREC_OK) return s;
     QKD_LAUNCHED("plan_layered_kernel");
     return QKDREC_OK;
@@ -438,7 +445,7 @@ void qkdrec_tuning_default(qkdrec_tuning *t) {
     if (!t) return;
     t->frames_per_tile = 32;
     t->threads_per_cta = 512;
-    t->stage_depth = 6;
+    t->stage_depth = 8;
     t->ctas_per_tile = 4;
 }
 

@@ -92,8 +92,9 @@ def test_frames_empty_batch_is_a_no_op():
 TUNINGS = [None,
            dict(frames_per_tile=8, threads_per_cta=256, stage_depth=4, ctas_per_tile=1),
            dict(frames_per_tile=16, threads_per_cta=512, stage_depth=4, ctas_per_tile=2),
-           dict(frames_per_tile=32, threads_per_cta=1024, stage_depth=6, ctas_per_tile=8),
-           dict(frames_per_tile=32, threads_per_cta=256, stage_depth=6, ctas_per_tile=1)]
+           dict(frames_per_tile=32, threads_per_cta=1024, stage_depth=4, ctas_per_tile=8),
+           dict(frames_per_tile=32, threads_per_cta=256, stage_depth=16, ctas_per_tile=1),
+           dict(frames_per_tile=8, threads_per_cta=512, stage_depth=8, ctas_per_tile=4)]
 
 
 def make_groups(spec, seed=800):
@@ -216,7 +217,7 @@ def test_plan_autotune_picks_a_supported_tuning_and_keeps_results():
     best, ms = plan.autotune(ws, max_iter=5)
     assert best["frames_per_tile"] in (8, 16, 32)
     assert best["threads_per_cta"] in (256, 512, 1024)
-    assert best["stage_depth"] in (4, 6)
+    assert best["stage_depth"] in (4, 8, 16)
     assert best["ctas_per_tile"] in (1, 2, 4, 8)
     assert ms > 0 and plan.tuning() == best
     plan.launch(ws)
@@ -236,6 +237,9 @@ def test_plan_rejects_unsupported_options_and_small_workspace():
         q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(frames_per_tile=4))
     with pytest.raises(RuntimeError):
         q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(ctas_per_tile=3))
+    deep = q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(stage_depth=16, threads_per_cta=512))
+    with pytest.raises(RuntimeError):          # depth 16 runs at most 256 threads per CTA
+        deep.launch(deep.workspace())
     plan = q.Plan(groups, q.DecodeOpts(algo="oms_layered"))
     small = torch.empty(256, dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError):
