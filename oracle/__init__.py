@@ -193,6 +193,39 @@ def slice_llr(x, lower_bits, j: int, m: int, lo: float, hi: float, sigma_n: floa
     return np.clip(llr, -clip, clip)
 
 
+def slice_llr_soft(x, lower_post, j: int, m: int, lo: float, hi: float, sigma_n: float,
+                   label: str = "gray", clip: float = LLR_CLIP) -> np.ndarray:
+    """Channel LLR of slice j with the lower slices known only softly (Sec. III-B
+    step 4 and its footnote: the soft decoding output of the lower slices gives
+    a-priori reliabilities).
+
+    L_j(i) = ln sum_{k: b_j(k)=0} P(k|x_i) w_k(i) - ln sum_{k: b_j(k)=1} P(k|x_i) w_k(i),
+    w_k(i) = prod_{l<j} P(b_l = bit l of label(k) | L_l(i)),
+    P(b = 0 | L) = 1 / (1 + e^-L), P(b = 1 | L) = 1 / (1 + e^L).
+    lower_post: float [j][count] LLRs of the lower slices (+-inf = known bit).
+    With every |L_l| infinite this is `slice_llr` with those bits.
+    """
+    x = np.asarray(x, dtype=np.float64).ravel()
+    lp = interval_logprob(x, m, lo, hi, sigma_n)
+    lab = labels(m, label)
+    logw = np.zeros_like(lp)
+    for l in range(j):
+        L = np.asarray(lower_post[l], dtype=np.float64).ravel()[:, None]
+        bit = ((lab >> l) & 1)[None, :]
+        # log P(b_l = bit | L) = -log(1 + e^{-L}) for bit 0, -log(1 + e^{L}) for bit 1
+        z = np.where(bit == 0, L, -L)
+        with np.errstate(invalid="ignore"):
+            logw += -np.logaddexp(0.0, -z)
+    lw = lp + logw
+    bj = (lab >> j) & 1
+    l0 = _logsumexp_masked(lw, np.broadcast_to(bj[None, :] == 0, lw.shape))
+    l1 = _logsumexp_masked(lw, np.broadcast_to(bj[None, :] == 1, lw.shape))
+    with np.errstate(invalid="ignore"):
+        llr = l0 - l1
+    llr = np.where(np.isnan(llr), 0.0, llr)
+    return np.clip(llr, -clip, clip)
+
+
 # --------------------------------------------------- capacities and code rates
 def _cond_entropy_integrand(x, m, lo, hi, sigma_n, lab, j):
     """sum_low P(low|x) h2(P(b_j = 1 | x, low)) in bits, vectorised over x."""
