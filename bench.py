@@ -717,6 +717,8 @@ def run_ours(args):
     conv = {(snr, ln, j): torch.empty(N_SAMPLES >> ln, dtype=torch.uint8, device=dev)
             for snr in SNRS for ln in LOGNS for j in range(M_SLICES)}
     llr = torch.empty(N_SAMPLES, dtype=torch.float32, device=dev)
+    # soft chaining: the lower slices enter slice j's LLRs through their decoder posteriors
+    post = torch.empty((M_SLICES, N_SAMPLES), dtype=torch.float32, device=dev) if args.soft_chain else None
     setup_s = time.time() - t_setup
     lo_hi = {snr: q.quantiser_range(snr) for snr in SNRS}
     bob = {}
@@ -734,13 +736,19 @@ def run_ours(args):
                     r = rate_of[(snr, ln, j)]
                     if r <= 0:
                         a[j].copy_(bits[j])          # disclosed slice: Bob's bits in the clear
+                        if post is not None:
+                            q.qkdrec_bits_to_llr(bits[j], out=post[j])
                         continue
                     c = codes[(ln, j, r)]
                     synd = q.qkdrec_syndrome(c, bits[j].view(F, n))
-                    q.qkdrec_slice_llr(xs[snr], M_SLICES, j, lo, hi, sn, a[:j] if j else None, out=llr)
+                    if post is not None:
+                        q.qkdrec_slice_llr_soft(xs[snr], M_SLICES, j, lo, hi, sn, post[:j] if j else None, out=llr)
+                    else:
+                        q.qkdrec_slice_llr(xs[snr], M_SLICES, j, lo, hi, sn, a[:j] if j else None, out=llr)
                     q.qkdrec_decode_batch(c, llr.view(F, n), synd, opts, workspace=ws,
                                           out=dict(bits=a[j].view(F, n), iters=iters[(snr, ln, j)],
-                                                   converged=conv[(snr, ln, j)], post=None))
+                                                   converged=conv[(snr, ln, j)],
+                                                   post=post[j].view(F, n) if post is not None else None))
 
     def barrier():
         if world > 1:
@@ -824,6 +832,7 @@ def run_ours(args):
                                                                  f"in FP32, {args.fallback} algorithm)"
                                     if opts.fallback_f32 else args.decoder),
                    "samples_per_snr": N_SAMPLES, "snr": list(SNRS),
+                   "lower_slices": "soft (decoder posteriors)" if args.soft_chain else "hard (decoded bits)",
                    "sub_block_log2": list(LOGNS), "slices": M_SLICES, "algo": algo, "prec": prec,
                    "fallback_f32": opts.fallback_f32,
                    "max_iter": MAX_ITER, "rate_rule": args.rate_rule if args.rate_rule == "backoff" else "0.95 x capacity",
@@ -1011,6 +1020,8 @@ def main():
     ap.add_argument("--rates-out", help="where --calibrate writes the table (default: uneven_rates.json)")
     ap.add_argument("--decoder", choices=sorted(DECODERS), default="sp_f32",
                     help="sweep workload: decoder form (default FP32 sum-product; others re-decode failures in FP32)")
+    ap.add_argument("--soft-chain", action="store_true",
+                    help="sweep: slice LLRs from the lower slices' decoder posteriors (soft) instead of their bits")
     ap.add_argument("--fallback", choices=["sp", "same"], default="sp",
                     help="low-precision decoders: re-decode failed frames with FP32 sum-product (default) or "
                          "with the same algorithm in FP32")

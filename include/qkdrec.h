@@ -201,6 +201,26 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
                                   int32_t *iters_out, uint8_t *conv_out, float *post_out,
                                   void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * Slice LLR with the lower slices known softly (Sec. III-B step 4 and its
+ * footnote: the soft decoding output of the lower slices gives a-priori
+ * reliabilities for slice j):
+ *   L_j = ln sum_{k: b_j(k)=0} P(k|x) w_k - ln sum_{k: b_j(k)=1} P(k|x) w_k,
+ *   w_k = prod_{l<j} P(b_l = bit l of label(k) | L_l),  P(b = 0 | L) = 1/(1 + e^-L).
+ *   lower_post  DEVICE float [j][count]: LLRs of slices 0..j-1 (the decoders'
+ *               posteriors; +-inf = a known bit, see qkdrec_bits_to_llr);
+ *               NULL allowed when j == 0.
+ * With every lower LLR infinite this equals qkdrec_slice_llr with those bits.
+ * Other arguments and errors as qkdrec_slice_llr; clipped to +-30.
+ */
+qkdrec_status qkdrec_slice_llr_soft(const float *x, int64_t count, int32_t m_slices, int32_t j, double lo,
+                                    double hi, double sigma_n, qkdrec_label label, const float *lower_post,
+                                    float *llr_out, void *stream);
+
+/* Known bits as certain LLRs (0 -> +inf, 1 -> -inf): DEVICE uint8 [count] ->
+ * DEVICE float [count]; for slices that are disclosed rather than decoded. */
+qkdrec_status qkdrec_bits_to_llr(const uint8_t *bits, int64_t count, float *llr_out, void *stream);
+
 /* ------------------------------------------------ uneven batches (one launch) */
 
 /*

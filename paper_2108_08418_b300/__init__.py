@@ -37,7 +37,7 @@ EXPORTED = [
     "qkdrec_woms_workspace_size", "qkdrec_woms_forward", "qkdrec_woms_backward",
     "qkdrec_quantise_slices_frames", "qkdrec_slice_llr_frames", "qkdrec_tuning_default",
     "qkdrec_plan_create", "qkdrec_plan_destroy", "qkdrec_plan_workspace_size", "qkdrec_plan_launch",
-    "qkdrec_plan_get_tuning", "qkdrec_plan_autotune",
+    "qkdrec_plan_get_tuning", "qkdrec_plan_autotune", "qkdrec_slice_llr_soft", "qkdrec_bits_to_llr",
 ]
 SELFTEST = ["qkdrec_selftest_phi"]
 
@@ -93,6 +93,8 @@ def lib():
         "qkdrec_code_layers": (U, [P, P]),
         "qkdrec_quantise_slices": (U, [P, I64, I32, D, D, U, P, P, P]),
         "qkdrec_slice_llr": (U, [P, I64, I32, I32, D, D, D, U, P, P, P]),
+        "qkdrec_slice_llr_soft": (U, [P, I64, I32, I32, D, D, D, U, P, P, P]),
+        "qkdrec_bits_to_llr": (U, [P, I64, P, P]),
         "qkdrec_syndrome": (U, [P, P, I32, P, P]),
         "qkdrec_decode_opts_default": (None, [P]),
         "qkdrec_decode_workspace_size": (U, [P, I32, P, P]),
@@ -233,6 +235,37 @@ def qkdrec_slice_llr(x, m_slices: int, j: int, lo: float, hi: float, sigma_n: fl
     op = _dev(out, torch.float32, "out")
     _check(lib().qkdrec_slice_llr(xp, count, int(m_slices), int(j), float(lo), float(hi), float(sigma_n),
                                   _LABELS[label], lb, op, _stream(x)))
+    return out
+
+
+def qkdrec_slice_llr_soft(x, m_slices: int, j: int, lo: float, hi: float, sigma_n: float, lower_post=None,
+                          label: str = "gray", out=None):
+    """Channel LLR float32 [count] of slice j with the lower slices known softly:
+    lower_post float32 [j][count] LLRs of slices 0..j-1 (+-inf = known bit)."""
+    torch = _torch()
+    count = x.numel()
+    xp = _dev(x, torch.float32, "x")
+    lp = None
+    if j > 0:
+        if lower_post is None or lower_post.shape[0] < j or lower_post[0].numel() != count:
+            raise ValueError("lower_post must be float32 [>= j][count]")
+        lp = _dev(lower_post, torch.float32, "lower_post")
+    if out is None:
+        out = torch.empty(count, dtype=torch.float32, device=x.device)
+    op = _dev(out, torch.float32, "out")
+    _check(lib().qkdrec_slice_llr_soft(xp, count, int(m_slices), int(j), float(lo), float(hi), float(sigma_n),
+                                       _LABELS[label], lp, op, _stream(x)))
+    return out
+
+
+def qkdrec_bits_to_llr(bits, out=None):
+    """Known bits uint8 [count] as certain LLRs float32 [count] (0 -> +inf, 1 -> -inf)."""
+    torch = _torch()
+    count = bits.numel()
+    bp = _dev(bits, torch.uint8, "bits")
+    if out is None:
+        out = torch.empty(count, dtype=torch.float32, device=bits.device)
+    _check(lib().qkdrec_bits_to_llr(bp, count, _dev(out, torch.float32, "out"), _stream(bits)))
     return out
 
 

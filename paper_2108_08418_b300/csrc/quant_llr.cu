@@ -228,6 +228,117 @@ __global__ void slice_llr_kernel(const float *__restrict__ xs, int64_t count,
     prof_add(prof, units, units * (8 + p.j));
 }
 
+// ------------------------------------------------- soft lower slices
+// log P(b | L) for an LLR L = ln P(0)/P(1): z = L for b = 0, -L for b = 1;
+// -log(1 + e^-z) = min(z, 0) - log1p(e^-|z|)  (z = +-inf allowed).
+__device__ __forceinline__ float log_sigmoid(float z) { return fminf(z, 0.0f) - log1pf(expf(-fabsf(z))); }
+__device__ __forceinline__ double log_sigmoid64(double z) { return fmin(z, 0.0) - log1p(exp(-fabs(z))); }
+
+constexpr float kSoftSkipNats = 40.0f;   // terms below e^-40 of the largest bound are dropped
+constexpr float kSoftLinNats = 10.0f;    // largest bound above e^-10: plain FP32 sums of P(k|x) w_k
+constexpr float kSkipLinSoftNats = 20.0f;  // in those sums, terms bounded below e^-20 of the largest bound drop
+
+// LLR of slice j with every interval weighted by the lower slices' bit
+// probabilities: L = ln sum_{b_j(k)=0} P(k|x) w_k - ln sum_{b_j(k)=1} P(k|x) w_k,
+// w_k = prod_{l<j} P(b_l(k) | L_l).  Log domain: a first pass bounds every term
+// (log P(k|x) <= ln 1/2 - d^2/2 beside x, 0 inside), the second evaluates the
+// terms within e^-40 of the largest bound (e^-20 in the plain sums; the bound is
+// within a few nats of the exact term, so the dropped mass stays below 1e-5): as
+// plain FP32 sums of P(k|x) w_k when that bound is above e^-10 (every such term lies within 10 sigma of x, so
+// P(k|x) is an ordinary float), in the FP32 log domain below, in FP64 when the
+// bound is below e^-50.
+__device__ float llr_soft_one(const LlrParams &p, const uint8_t *lab_of_k, float x, const float *la,
+                              const float *lb) {
+    // pass 1: the largest bound of each set (b_j = 0, 1)
+    float mub[2] = {-INFINITY, -INFINITY};
+    for (int k = 0; k < p.K; ++k) {
+        float prior = 0.0f;
+        for (int l = 0; l < p.j; ++l) prior += ((lab_of_k[k] >> l) & 1) ? lb[l] : la[l];
+        const float d = interval_dist(p, k, x);
+        const int b = (lab_of_k[k] >> p.j) & 1;
+        mub[b] = fmaxf(mub[b], (d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f) + prior);
+    }
+    const float maxub = fmaxf(mub[0], mub[1]);
+    // a set whose bound is more than the clip (plus the bound's slack) below the
+    // other's cannot move the clipped result
+    if (mub[1] < maxub - kSoftSkipNats) return kLlrClip;
+    if (mub[0] < maxub - kSoftSkipNats) return -kLlrClip;
+    const bool lin = maxub >= -kSoftLinNats;
+    const bool wide = maxub < -kFarNats;
+    const float cut0 = mub[0] - (lin ? kSkipLinSoftNats : kSoftSkipNats);
+    const float cut1 = mub[1] - (lin ? kSkipLinSoftNats : kSoftSkipNats);
+    // pass 2: the terms within reach of their own set's largest bound
+    float t[2] = {0.0f, 0.0f}, m[2] = {-INFINITY, -INFINITY};
+    double M[2] = {-INFINITY, -INFINITY}, S[2] = {0.0, 0.0};
+    for (int k = 0; k < p.K; ++k) {
+        float prior = 0.0f;
+        for (int l = 0; l < p.j; ++l) prior += ((lab_of_k[k] >> l) & 1) ? lb[l] : la[l];
+        const float d = interval_dist(p, k, x);
+        const int b = (lab_of_k[k] >> p.j) & 1;
+        if ((d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f) + prior < (b ? cut1 : cut0)) continue;
+        if (lin) {
+            // every kept term lies within ~10 sigma of x: P(k|x) is an ordinary float
+            t[b] += p_lin32((p.tf[k] - x) * p.inv_sigma, (p.tf[k + 1] - x) * p.inv_sigma) * expf(prior);
+        } else if (!wide) {
+            const float lw = lp_interval32(p, k, x) + prior;
+            if (lw > m[b]) { t[b] = t[b] * expf(m[b] - lw) + 1.0f; m[b] = lw; }
+            else t[b] += expf(lw - m[b]);
+        } else {
+            double prior64 = 0.0;
+            for (int l = 0; l < p.j; ++l) prior64 += (double)(((lab_of_k[k] >> l) & 1) ? lb[l] : la[l]);
+            const double lw = lp_interval64(p, k, (double)x) + prior64;
+            if (lw > M[b]) { S[b] = S[b] * exp(M[b] - lw) + 1.0; M[b] = lw; }
+            else S[b] += exp(lw - M[b]);
+        }
+    }
+    float llr;
+    if (lin) {
+        llr = !(t[0] > 0.0f) ? -kLlrClip : (!(t[1] > 0.0f) ? kLlrClip : logf(t[0]) - logf(t[1]));
+    } else if (!wide) {
+        llr = !(t[0] > 0.0f) ? -kLlrClip : (!(t[1] > 0.0f) ? kLlrClip : (m[0] + logf(t[0])) - (m[1] + logf(t[1])));
+    } else {
+        llr = !(S[0] > 0.0) ? -kLlrClip
+                            : (!(S[1] > 0.0) ? kLlrClip : (float)((M[0] + log(S[0])) - (M[1] + log(S[1]))));
+    }
+    return fminf(fmaxf(llr, -kLlrClip), kLlrClip);
+}
+
+__global__ void slice_llr_soft_kernel(const float *__restrict__ xs, int64_t count, const float *__restrict__ post,
+                                      const LlrParams p_in, float *__restrict__ out, unsigned long long *prof) {
+    __shared__ LlrParams sp;
+    __shared__ uint8_t lab_of_k[kMaxK];
+    {
+        const int n4 = (int)(sizeof(LlrParams) / 4);
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&p_in);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sp);
+        for (int t = threadIdx.x; t < n4; t += blockDim.x) dst[t] = src[t];
+        for (int t = threadIdx.x; t < p_in.K; t += blockDim.x) lab_of_k[p_in.k_of_label[t]] = (uint8_t)t;
+    }
+    __syncthreads();
+    const LlrParams &p = sp;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long units = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        ++units;
+        float la[kMaxM], lb[kMaxM];   // log P(bit 0 | L_l), log P(bit 1 | L_l)
+        for (int l = 0; l < p.j; ++l) {
+            const float L = post[(int64_t)l * count + i];
+            la[l] = log_sigmoid(L);
+            lb[l] = log_sigmoid(-L);
+        }
+        out[i] = llr_soft_one(p, lab_of_k, xs[i], la, lb);
+    }
+    // x and the lower LLRs read, the LLR written
+    prof_add(prof, units, units * (8 + 4 * p.j));
+}
+
+// Known bits as certain LLRs: 0 -> +inf, 1 -> -inf.
+__global__ void bits_to_llr_kernel(const uint8_t *__restrict__ bits, int64_t count, float *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        out[i] = (bits[i] & 1) ? -INFINITY : INFINITY;
+}
+
 // ------------------------------------------- frames with their own parameters
 // One block per frame: the block builds the frame's tables (thresholds from its
 // quantiser range, its noise level) in shared memory, then walks its samples.
@@ -369,6 +480,48 @@ qkdrec_status qkdrec_slice_llr(const float *x, int64_t count, int32_t m, int32_t
     slice_llr_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(x, count, lower_bits, p, llr_out,
                                                                               prof::counters(prof::kSliceLlr));
     QKD_LAUNCHED("slice_llr_kernel");
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_slice_llr_soft(const float *x, int64_t count, int32_t m, int32_t j, double lo, double hi,
+                                    double sigma_n, qkdrec_label label, const float *lower_post, float *llr_out,
+                                    void *stream) {
+    clear_error();
+    if (count < 0) QKD_FAIL(QKDREC_ERR_ARG, "count < 0");
+    if (m < 1 || m > kMaxM) QKD_FAIL(QKDREC_ERR_ARG, "m_slices=%d outside [1, %d]", m, kMaxM);
+    if (j < 0 || j >= m) QKD_FAIL(QKDREC_ERR_ARG, "slice j=%d outside [0, %d)", j, m);
+    if (!(lo < hi) || !(sigma_n > 0)) QKD_FAIL(QKDREC_ERR_ARG, "need lo < hi and sigma_n > 0");
+    if (label != QKDREC_LABEL_GRAY && label != QKDREC_LABEL_BINARY) QKD_FAIL(QKDREC_ERR_ARG, "bad label");
+    if (count == 0) return QKDREC_OK;
+    if (!x || !llr_out) QKD_FAIL(QKDREC_ERR_ARG, "x/llr_out NULL");
+    if (j > 0 && !lower_post) QKD_FAIL(QKDREC_ERR_ARG, "lower_post NULL for j=%d", j);
+    LlrParams p;
+    p.m = m;
+    p.K = 1 << m;
+    p.j = j;
+    const double delta = (hi - lo) / p.K;
+    p.td[0] = -INFINITY;
+    p.td[p.K] = INFINITY;
+    for (int k = 1; k < p.K; ++k) p.td[k] = lo + delta * k;
+    for (int k = 0; k <= p.K; ++k) p.tf[k] = (float)p.td[k];
+    for (int k = 0; k < p.K; ++k) p.k_of_label[label_of(k, label)] = (uint8_t)k;
+    p.inv_sigma = (float)(1.0 / sigma_n);
+    p.inv_sigma_d = 1.0 / sigma_n;
+    const int block = 128;
+    prof::Scope ps(prof::kSliceLlr, as_stream(stream));
+    slice_llr_soft_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(
+        x, count, lower_post, p, llr_out, prof::counters(prof::kSliceLlr));
+    QKD_LAUNCHED("slice_llr_soft_kernel");
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_bits_to_llr(const uint8_t *bits, int64_t count, float *llr_out, void *stream) {
+    clear_error();
+    if (count < 0) QKD_FAIL(QKDREC_ERR_ARG, "count < 0");
+    if (count == 0) return QKDREC_OK;
+    if (!bits || !llr_out) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    bits_to_llr_kernel<<<grid_for(count, 256), 256, 0, as_stream(stream)>>>(bits, count, llr_out);
+    QKD_LAUNCHED("bits_to_llr_kernel");
     return QKDREC_OK;
 }
 
