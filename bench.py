@@ -940,6 +940,10 @@ CASES = {
     "decode_oms_i8": dict(logn=16, frames=512, rate=0.84375, algo="oms_flood", prec="i8", iters=5),
     # the plan decoder on a small uneven batch: 96 frames of n = 2^16, 192 of 2^14, 384 of 2^12
     # (rate 0.84375; ~0.9 GB on the device)
+    # layered min-sum of a quasi-cyclic code (Z = 2^13, 3 x 8 base matrix: n = 2^16, rate 0.625),
+    # 512 frames, 5 iterations: with the TMA-staged path, and the same matrix without the structure
+    "decode_layered_qc_f32": dict(qc=(8192, 8), frames=512, iters=5, attach=True),
+    "decode_layered_qcplain_f32": dict(qc=(8192, 8), frames=512, iters=5, attach=False),
     "plan_layered": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
                          tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=4, ctas_per_tile=8)),
     "plan_layered_cta": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
@@ -947,6 +951,32 @@ CASES = {
     "plan_layered_ft32": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
                               tuning=dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=8)),
 }
+
+
+def run_qc_case(args, c):
+    import torch
+    import paper_2108_08418_b300 as q
+    Z, nb = c["qc"]
+    n, F = Z * nb, c["frames"]
+    rp, ci, S, _ = synth.make_qc_code(4242, Z, nb)
+    code = q.Code(n, rp, ci)
+    if c["attach"]:
+        code.set_qc(Z, 3, nb, S)
+    g = synth.philox(79)
+    b = g.integers(0, 2, size=(F, n)).astype(np.uint8)
+    llr = ((2 / 0.6 ** 2) * ((1.0 - 2.0 * b) + 0.6 * g.standard_normal((F, n)))).astype(np.float32)
+    bd, ld = torch.from_numpy(b).cuda(), torch.from_numpy(llr).cuda()
+    synd = q.qkdrec_syndrome(code, bd)
+    opts = q.DecodeOpts(algo="oms_layered", prec="f32", max_iter=c["iters"], early_stop=False)
+    ws = q.workspace_for(code, F, opts, "cuda")
+    q.qkdrec_profile_begin()
+    for _ in range(args.warmup + args.steps):
+        q.qkdrec_decode_batch(code, ld, synd, opts, workspace=ws)
+    torch.cuda.synchronize()
+    st = q.qkdrec_profile_end()
+    k = "layer_qc_tma" if c["attach"] else "layer_oms_f32"
+    print(f"case {args.case}: n={n} F={F} {k}: {st[k]['ms'] / st[k]['launches']:.4f} ms/launch, "
+          f"{st[k]['bytes'] / st[k]['ms'] / 1e6:.1f} GB/s; timeouts {q.qkdrec_qc_timeouts()}", flush=True)
 
 
 def run_plan_case(args, c):
@@ -983,6 +1013,9 @@ def run_case(args):
     c = CASES[args.case]
     if "groups" in c:
         run_plan_case(args, c)
+        return
+    if "qc" in c:
+        run_qc_case(args, c)
         return
     n, F = 1 << c["logn"], c["frames"]
     M = synth.checks_for_rate(n, c["rate"])

@@ -99,6 +99,27 @@ qkdrec_status qkdrec_code_info(qkdrec_code_t code, int32_t *n, int32_t *m_checks
 /* HOST int32 [M]: the layer of every check (the partition the layered decoder uses). */
 qkdrec_status qkdrec_code_layers(qkdrec_code_t code, int32_t *layer_of_check);
 
+/*
+ * Declare the code quasi-cyclic: H is an mb x nb base matrix of Z x Z circulant
+ * permutations, check c = i Z + z holding, in edge order k = 0..nb-1, variable
+ * k Z + (z + shifts[i nb + k]) mod Z (HOST int32 shifts [mb][nb], in [0, Z)).
+ * The CSR given to qkdrec_code_create is checked against this (QKDREC_ERR_CSR
+ * on a mismatch) and the layer partition must be the base rows
+ * (QKDREC_ERR_UNSUPPORTED otherwise).  tma_staging = 1: the layered FP32
+ * decoder stages each layer chunk's posteriors (a circulant block row is a
+ * contiguous run of variables) and messages in shared memory with TMA tile
+ * copies instead of per-edge loads; results are identical.  Measured on B300
+ * the per-edge path is faster on these codes (their gathers are already
+ * sequential), so 0 keeps it.  Synchronous.  The paper's codes (Sec. V-B) are
+ * not quasi-cyclic; this is a code layout the decoder can exploit.
+ */
+qkdrec_status qkdrec_code_set_qc(qkdrec_code_t code, int32_t Z, int32_t mb, int32_t nb, const int32_t *shifts,
+                                 int32_t tma_staging);
+/* Number of times a quasi-cyclic layer kernel gave up waiting for its tile
+ * copies (bounded wait; the chunk is then left undecoded) since the library
+ * was loaded.  Synchronous read of a device counter; 0 in normal operation. */
+qkdrec_status qkdrec_qc_timeouts(int32_t *count);
+
 /* ------------------------------------------------------- quantiser (Bob) */
 
 /*

@@ -38,6 +38,7 @@ EXPORTED = [
     "qkdrec_quantise_slices_frames", "qkdrec_slice_llr_frames", "qkdrec_tuning_default",
     "qkdrec_plan_create", "qkdrec_plan_destroy", "qkdrec_plan_workspace_size", "qkdrec_plan_launch",
     "qkdrec_plan_get_tuning", "qkdrec_plan_autotune", "qkdrec_slice_llr_soft", "qkdrec_bits_to_llr",
+    "qkdrec_code_set_qc", "qkdrec_qc_timeouts",
 ]
 SELFTEST = ["qkdrec_selftest_phi"]
 
@@ -95,6 +96,8 @@ def lib():
         "qkdrec_slice_llr": (U, [P, I64, I32, I32, D, D, D, U, P, P, P]),
         "qkdrec_slice_llr_soft": (U, [P, I64, I32, I32, D, D, D, U, P, P, P]),
         "qkdrec_bits_to_llr": (U, [P, I64, P, P]),
+        "qkdrec_code_set_qc": (U, [P, I32, I32, I32, P, I32]),
+        "qkdrec_qc_timeouts": (U, [P]),
         "qkdrec_syndrome": (U, [P, P, I32, P, P]),
         "qkdrec_decode_opts_default": (None, [P]),
         "qkdrec_decode_workspace_size": (U, [P, I32, P, P]),
@@ -182,6 +185,13 @@ class Code:
     def handle(self):
         return self._h
 
+    def set_qc(self, Z: int, mb: int, nb: int, shifts, tma: bool = True):
+        """Declare the code quasi-cyclic (shifts int [mb][nb]); with `tma` the layered
+        FP32 decoder stages posteriors and messages with TMA tile copies."""
+        sh = np.ascontiguousarray(shifts, dtype=np.int32).reshape(mb, nb)
+        _check(lib().qkdrec_code_set_qc(self._h, int(Z), int(mb), int(nb), sh.ctypes.data, int(bool(tma))))
+        self.qc = (int(Z), int(mb), int(nb))
+
     def layers(self) -> np.ndarray:
         out = np.zeros(self.M, dtype=np.int32)
         _check(lib().qkdrec_code_layers(self._h, out.ctypes.data))
@@ -197,6 +207,13 @@ class Code:
             self.destroy()
         except Exception:
             pass
+
+
+def qkdrec_qc_timeouts() -> int:
+    """Tile-copy waits the quasi-cyclic layer kernel gave up on (0 in normal operation)."""
+    c = ctypes.c_int32()
+    _check(lib().qkdrec_qc_timeouts(ctypes.byref(c)))
+    return c.value
 
 
 def qkdrec_code_create(n, row_ptr, col_idx, seed=0, device=None) -> Code:

@@ -41,6 +41,7 @@ static void free_code(CodeDev &d) {
     cudaFree(d.vedge);
     cudaFree(d.layer_ptr);
     cudaFree(d.layer_chk);
+    cudaFree(d.qc_shift);
     free(d.h_layer_of);
     d = CodeDev();
 }
@@ -175,6 +176,46 @@ qkdrec_status qkdrec_code_info(qkdrec_code_t code, int32_t *n, int32_t *m_checks
     if (edges) *edges = code->d.E;
     if (n_layers) *n_layers = code->d.n_layers;
     if (dc_max) *dc_max = code->d.dc_max;
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_code_set_qc(qkdrec_code_t code, int32_t Z, int32_t mb, int32_t nb, const int32_t *shifts,
+                                 int32_t tma_staging) {
+    clear_error();
+    if (!code || !shifts) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    CodeDev &d = code->d;
+    if (Z < 1 || mb < 1 || nb < 2) QKD_FAIL(QKDREC_ERR_ARG, "need Z >= 1, mb >= 1, nb >= 2");
+    if ((int64_t)nb * Z != d.n || (int64_t)mb * Z != d.M || (int64_t)mb * Z * nb != d.E)
+        QKD_FAIL(QKDREC_ERR_ARG, "n = %d, M = %d, E = %lld do not match a %d x %d base matrix of %d x %d circulants",
+                 d.n, d.M, (long long)d.E, mb, nb, Z, Z);
+    for (int32_t t = 0; t < mb * nb; ++t)
+        if (shifts[t] < 0 || shifts[t] >= Z) QKD_FAIL(QKDREC_ERR_ARG, "shift %d outside [0, %d)", shifts[t], Z);
+    std::vector<int32_t> rp((size_t)d.M + 1), ci((size_t)d.E);
+    QKD_CUDA(cudaMemcpy(rp.data(), d.rp, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    QKD_CUDA(cudaMemcpy(ci.data(), d.ci, ci.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int32_t c = 0; c < d.M; ++c) {
+        const int32_t i = c / Z, z = c - i * Z;
+        if (rp[c] != (int64_t)c * nb) QKD_FAIL(QKDREC_ERR_CSR, "check %d does not have degree %d", c, nb);
+        for (int32_t k = 0; k < nb; ++k)
+            if (ci[(size_t)c * nb + k] != k * Z + (z + shifts[i * nb + k]) % Z)
+                QKD_FAIL(QKDREC_ERR_CSR, "check %d edge %d is not the circulant entry of base (%d, %d)", c, k, i, k);
+        if (d.h_layer_of[c] != i)
+            QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "layer partition differs from the base rows at check %d", c);
+    }
+    if (d.n_layers != mb) QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "%d layers for %d base rows", d.n_layers, mb);
+    int32_t *dev = nullptr;
+    QKD_CUDA(cudaMalloc(&dev, sizeof(int32_t) * (size_t)mb * nb));
+    cudaError_t e = cudaMemcpy(dev, shifts, sizeof(int32_t) * (size_t)mb * nb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        QKD_FAIL(QKDREC_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    cudaFree(d.qc_shift);
+    d.qc_shift = dev;
+    d.qc_Z = Z;
+    d.qc_mb = mb;
+    d.qc_nb = nb;
+    d.qc_tma = tma_staging ? 1 : 0;
     return QKDREC_OK;
 }
 

@@ -68,6 +68,9 @@ struct CodeDev {
     int32_t *vedge = nullptr;      // [E]   edges of each variable, ascending edge index
     int32_t *layer_ptr = nullptr;  // [n_layers+1]
     int32_t *layer_chk = nullptr;  // [M] checks of each layer, ascending index
+    // quasi-cyclic structure (qkdrec_code_set_qc), qc_Z = 0 when absent
+    int32_t qc_Z = 0, qc_mb = 0, qc_nb = 0, qc_tma = 0;
+    int32_t *qc_shift = nullptr;   // [mb][nb] circulant shifts
 };
 
 }  // namespace qkd

@@ -26,6 +26,7 @@
 // signs) in registers for checks of degree <= DCMAX, so pass 2 only computes
 // and stores the outgoing messages; larger degrees use a variant that reloads.
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <math.h>
 
 #include <algorithm>
@@ -1067,6 +1068,13 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
 }
 
 }  // extern "C"
+
+extern "C" qkdrec_status qkdrec_qc_timeouts(int32_t *count) {
+    clear_error();
+    if (!count) QKD_FAIL(QKDREC_ERR_ARG, "count is NULL");
+    QKD_CUDA(cudaMemcpyFromSymbol(count, qkd::g_qc_timeouts, sizeof(int32_t)));
+    return QKDREC_OK;
+}
 
 #include "decode_woms.cuh"
 #include "decode_plan.cuh"

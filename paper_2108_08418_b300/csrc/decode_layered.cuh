@@ -226,6 +226,93 @@ static void launch_layer(DecArgs a, const CodeDev &d, int prec, int32_t lb, int3
     }
 }
 
+#include "decode_qc.cuh"
+
+// ------------------------------------------------- quasi-cyclic layer launch
+__device__ int32_t g_qc_timeouts = 0;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// checks per CTA chunk: two stages of (two posterior tiles per base column +
+// one message tile) of Zc x 128 B each within ~96 KB (two CTAs per SM); the
+// message tile's Zc nb rows within one tile copy (<= 256 rows)
+static int qc_chunk(const CodeDev &d) {
+    int zc = 256;
+    while (zc > 1 && (zc > d.qc_Z || zc * d.qc_nb > 256 || (size_t)6 * d.qc_nb * zc * 128 > (size_t)96 * 1024))
+        zc >>= 1;
+    return zc;
+}
+
+static bool qc_usable(const CodeDev &d, int prec, int lgfb) {
+    return d.qc_Z > 0 && d.qc_tma && prec == kF32 && lgfb == lgfb_of<1>() && encode_tiled() != nullptr;
+}
+
+// Tensor map of the messages [Fp/32][E][32], tiles of Zc nb edges.
+static qkdrec_status qc_msg_map(const CodeDev &d, void *msg, int64_t Fp, CUtensorMap *tm) {
+    const cuuint64_t dims[3] = {32, (cuuint64_t)d.E, (cuuint64_t)(Fp >> 5)};
+    const cuuint64_t strides[2] = {32 * 4, (cuuint64_t)d.E * 128};
+    const cuuint32_t box[3] = {32, (cuuint32_t)(qc_chunk(d) * d.qc_nb), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode_tiled()(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, msg, dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) QKD_FAIL(QKDREC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return QKDREC_OK;
+}
+
+// Tensor map of the posteriors [Fp/32][nb][Z][32] (one decode's workspace).
+static qkdrec_status qc_tensor_map(const CodeDev &d, void *L, int64_t Fp, CUtensorMap *tm) {
+    const cuuint64_t dims[4] = {32, (cuuint64_t)d.qc_Z, (cuuint64_t)d.qc_nb, (cuuint64_t)(Fp >> 5)};
+    const cuuint64_t strides[3] = {32 * 4, (cuuint64_t)d.qc_Z * 128, (cuuint64_t)d.qc_nb * d.qc_Z * 128};
+    const cuuint32_t box[4] = {32, (cuuint32_t)qc_chunk(d), 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode_tiled()(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L, dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) QKD_FAIL(QKDREC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return QKDREC_OK;
+}
+
+static qkdrec_status launch_layer_qc(DecArgs a, const CodeDev &d, int32_t row, const CUtensorMap &tm,
+                                     const CUtensorMap &tmm, cudaStream_t st) {
+    static bool attr_set = false;
+    const int zc = qc_chunk(d);
+    const size_t smem = (size_t)6 * d.qc_nb * zc * 128 + 128;
+    if (!attr_set) {
+        QKD_CUDA(cudaFuncSetAttribute(layer_qc_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((size_t)96 * 1024 + 128)));
+        attr_set = true;
+    }
+    QcLayer q;
+    q.shift = d.qc_shift;
+    q.Z = d.qc_Z;
+    q.nb = d.qc_nb;
+    q.row = row;
+    q.Zc = zc;
+    QKD_CUDA(cudaGetSymbolAddress(reinterpret_cast<void **>(&q.timeouts), g_qc_timeouts));
+    const int64_t chunks = ceil_div(d.qc_Z, zc);
+    const int64_t nblk = a.Fp >> 5;
+    const int64_t gy = std::min<int64_t>(nblk, std::max<int64_t>(1, ceil_div((int64_t)sm_count() * 16, chunks)));
+    layer_qc_tma<<<dim3((unsigned)chunks, (unsigned)std::min<int64_t>(gy, 65535)), 256, smem, st>>>(a, tm, tmm, q);
+    QKD_LAUNCHED("layer_qc_tma");
+    return QKDREC_OK;
+}
+
 qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
                           const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev,
                           uint8_t *bits_out, int32_t *iters_out, uint8_t *conv_out, float *post_out,
@@ -262,11 +349,20 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *syn
         QKD_LAUNCHED("retire");
     }
     const int lkind = prec == kI8 ? prof::kLayerI8 : (prec == kF16 ? prof::kLayerF16 : prof::kLayerF32);
+    // quasi-cyclic codes: posterior tiles staged by TMA (same results)
+    const bool qc = qc_usable(d, prec, l.lgfb);
+    CUtensorMap tm, tmm;
+    if (qc && (s = qc_tensor_map(d, a.L, l.Fp, &tm)) != QKDREC_OK) return s;
+    if (qc && (s = qc_msg_map(d, a.msg, l.Fp, &tmm)) != QKDREC_OK) return s;
     for (int t = 1; t <= T; ++t) {
-        a.prof = prof::counters(lkind);
+        a.prof = prof::counters(qc ? prof::kLayerQc : lkind);
         for (int32_t ly = 0; ly < d.n_layers; ++ly) {
-            prof::Scope ps(lkind, st);
-            launch_layer(a, d, prec, lptr[ly], lptr[ly + 1] - lptr[ly], st);
+            prof::Scope ps(qc ? prof::kLayerQc : lkind, st);
+            if (qc) {
+                if ((s = launch_layer_qc(a, d, ly, tm, tmm, st)) != QKDREC_OK) return s;
+            } else {
+                launch_layer(a, d, prec, lptr[ly], lptr[ly + 1] - lptr[ly], st);
+            }
         }
         QKD_LAUNCHED("layer_oms");
         if (o.early_stop) {

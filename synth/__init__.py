@@ -140,6 +140,48 @@ def make_regular_code(seed: int, n: int, m_checks: int, dv: int = 3, max_passes:
     return row_ptr, col_idx, int(residual)
 
 
+def make_qc_code(seed: int, Z: int, nb: int, mb: int = 3, max_tries: int = 10000):
+    """Quasi-cyclic parity-check matrix: an mb x nb base matrix with every entry
+    a Z x Z circulant permutation P^s (shift s drawn from Philox key (seed, 3)),
+    so every variable has degree mb and every check degree nb; n = nb Z,
+    M = mb Z.  Shifts are redrawn until no 4-cycle remains
+    (s_ij - s_ik + s_lk - s_lj != 0 mod Z for all row pairs i, l and column
+    pairs j, k), at most `max_tries` redraws.
+    Check c = i Z + z (base row i) has its edges in base-column order: edge
+    k goes to variable k Z + (z + s_ik) mod Z.
+    Returns (row_ptr int32[M+1], col_idx int32[E], shifts int32[mb][nb], residual
+    4-cycle count)."""
+    g = np.random.Generator(np.random.Philox(key=[int(seed), 3]))
+    S = g.integers(0, Z, size=(mb, nb)).astype(np.int64)
+
+    def cycles(S):
+        bad = []
+        for i in range(mb):
+            for l in range(i + 1, mb):
+                d = (S[i] - S[l]) % Z                 # s_ij - s_lj per column j
+                for j in range(nb):
+                    for k in range(j + 1, nb):
+                        if d[j] == d[k]:
+                            bad.append((i, j))
+        return bad
+
+    for _ in range(max_tries):
+        bad = cycles(S)
+        if not bad:
+            break
+        i, j = bad[int(g.integers(0, len(bad)))]
+        S[i, j] = g.integers(0, Z)
+    residual = len(cycles(S))
+    M, E = mb * Z, mb * Z * nb
+    row_ptr = (np.arange(M + 1, dtype=np.int64) * nb).astype(np.int32)
+    z = np.arange(Z, dtype=np.int64)
+    col = np.empty((mb, Z, nb), dtype=np.int64)
+    for i in range(mb):
+        for k in range(nb):
+            col[i, :, k] = k * Z + (z + S[i, k]) % Z
+    return row_ptr, col.reshape(E).astype(np.int32), S.astype(np.int32), residual
+
+
 def degrees(row_ptr, col_idx, n):
     """(column degrees, row degrees) of a CSR parity-check matrix."""
     cols = np.bincount(col_idx, minlength=n)

@@ -70,3 +70,21 @@ def test_uneven_frames_and_gaussian_frames():
     x, y = synth.gaussian_frames(4, lengths, np.array([3.0, 5.0, 1e6]))
     assert x.size == y.size == 12 and x.dtype == np.float32
     assert np.allclose(x[5:], y[5:], atol=1e-2)          # SNR 1e6: y ~ x
+
+
+@pytest.mark.parametrize("Z,nb", [(64, 6), (256, 24), (1024, 8)])
+def test_quasi_cyclic_code_structure(Z, nb):
+    rp, ci, S, res = synth.make_qc_code(11, Z, nb)
+    n, M = nb * Z, 3 * Z
+    assert res == 0 and rp.size == M + 1 and ci.size == 3 * n
+    cols, rows = synth.degrees(rp, ci, n)
+    assert np.all(cols == 3) and np.all(rows == nb)
+    # check i Z + z, edge k -> variable k Z + (z + S[i, k]) mod Z
+    for c in (0, Z - 1, Z, 2 * Z + 5):
+        i, z = divmod(c, Z)
+        assert np.array_equal(ci[rp[c]:rp[c + 1]], np.arange(nb) * Z + (z + S[i]) % Z)
+    # no 4-cycle: two checks share at most one variable
+    from scipy.sparse import csr_matrix
+    H = csr_matrix((np.ones(ci.size, dtype=np.int32), ci, rp), shape=(M, n))
+    overlap = (H @ H.T).tocoo()
+    assert overlap.data[overlap.row != overlap.col].max(initial=0) <= 1
