@@ -22,8 +22,11 @@
 // cleared: the first iteration reads m = 0 without loading it.  The q values of
 // the first kStash edges of a check wait in shared memory between the two
 // passes; the rest are recomputed from L and m, which no other check of the
-// layer touches.  All posterior and message accesses go through L2 only
-// (ld/st .cg), so what one SM of the cluster wrote is what the others read.
+// layer touches.  Posteriors go through L2 only (ld/st .cg), so what one SM of
+// the cluster wrote is what the others read; messages stream with the
+// evict-first hint (each check, hence each message, is always handled by the
+// same warp of the same CTA), so L2 keeps the tiles' posteriors, which the
+// checks gather.
 
 namespace qkd {
 namespace cg = cooperative_groups;
@@ -173,7 +176,7 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
                     for (int j = 0; j < CH; ++j) {
                         const int32_t e = beg + min(k0 + j, d - 1);
                         Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl));
-                        mo[j] = first ? 0.0f : __ldcg(msg + ((uint32_t)e * FT + fl));
+                        mo[j] = first ? 0.0f : __ldcs(msg + ((uint32_t)e * FT + fl));
                     }
 #pragma unroll
                     for (int j = 0; j < CH; ++j) {
@@ -193,10 +196,10 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
                     float *Lp = L + ((uint32_t)__ldg(G.ci + e) * FT + fl);
                     float *mp = msg + ((uint32_t)e * FT + fl);
                     // edges beyond the stash: L and m of this edge are still unchanged
-                    const float q = k < kStash ? my[k * 32] : __ldcg(Lp) - (first ? 0.0f : __ldcg(mp));
+                    const float q = k < kStash ? my[k * 32] : __ldcg(Lp) - (first ? 0.0f : __ldcs(mp));
                     const float mag = fmaxf(((k == arg) ? mn2 : mn1) - a.beta, 0.0f);
                     const float mn = ((neg ^ (uint32_t)(q < 0.0f)) & 1u) ? -mag : mag;
-                    __stcg(mp, mn);
+                    __stcs(mp, mn);
                     __stcg(Lp, q + mn);
                 }
             }
