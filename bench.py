@@ -492,13 +492,8 @@ def run_uneven(args):
         barrier()
         t_e2e = e2.elapsed_time(e3)
 
-    tot = torch.tensor([good_bits, raw_bits], dtype=torch.float64, device=dev)
-    tmax = torch.tensor([ms, t_e2e or 0.0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    good_bits, raw_bits = float(tot[0]), float(tot[1])
-    ms, t_e2e_max = float(tmax[0]), float(tmax[1])
+    (good_bits, raw_bits), (ms, t_e2e_max) = reduce_over_ranks([good_bits, raw_bits], [ms, t_e2e or 0.0], dev,
+                                                                world)
     ms_step = ms / args.steps
     roof, kernels, launches = roofline(stats, args.steps)
     if rank != 0:
@@ -528,6 +523,19 @@ def run_uneven(args):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def reduce_over_ranks(sums, maxes, dev, world):
+    """Whole-job figures: counters summed over ranks, times maxed over ranks (every
+    rank calls this; one rank returns its own values)."""
+    import torch
+    import torch.distributed as dist
+    tot = torch.tensor([float(v) for v in sums], dtype=torch.float64, device=dev)
+    tmax = torch.tensor([float(v) for v in maxes], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    return [float(v) for v in tot], [float(v) for v in tmax]
 
 
 def smi_index(torch, dev, local):
@@ -809,13 +817,8 @@ def run_ours(args):
         t_e2e = e2.elapsed_time(e3)
 
     # aggregate over ranks
-    tot = torch.tensor([good_bits, raw_bits], dtype=torch.float64, device=dev)
-    tmax = torch.tensor([ms, t_e2e or 0.0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    good_bits, raw_bits = float(tot[0]), float(tot[1])
-    ms, t_e2e_max = float(tmax[0]), float(tmax[1])
+    (good_bits, raw_bits), (ms, t_e2e_max) = reduce_over_ranks([good_bits, raw_bits], [ms, t_e2e or 0.0], dev,
+                                                                world)
     ms_step = ms / args.steps
     value = good_bits / (ms_step / 1e3)
 
