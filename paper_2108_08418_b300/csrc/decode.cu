@@ -586,7 +586,9 @@ __global__ void prep_llr(const float *__restrict__ llr, int32_t F, int32_t n, in
                          float step, void *llr_i, void *L) {
     __shared__ float tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t v0 = (int64_t)blockIdx.x * 32, f0 = (int64_t)blockIdx.y * 32;
+    const int64_t v0 = (int64_t)blockIdx.x * 32;
+    // frame groups of 32, grid-stride (a padded frame count can exceed 65535 groups)
+    for (int64_t f0 = (int64_t)blockIdx.y * 32; f0 < Fp; f0 += (int64_t)gridDim.y * 32) {
     for (int r = 0; r < 32; r += 8) {
         const int64_t f = f0 + ty + r, v = v0 + tx;
         float val = kLlrClip;
@@ -612,19 +614,22 @@ __global__ void prep_llr(const float *__restrict__ llr, int32_t F, int32_t n, in
             reinterpret_cast<float *>(L)[o] = val;
         }
     }
+    __syncthreads();
+    }
 }
 
 // synd [F][M] (bytes) -> sbits [M][W] (bit f%32 of word f/32).
 __global__ void prep_synd(const uint8_t *__restrict__ synd, int32_t F, int32_t M, int64_t W,
                           uint32_t *__restrict__ sbits) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t w = blockIdx.y;
-    const int64_t f = w * 32 + lane;
     const int64_t cbeg = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 64;
-    for (int64_t c = cbeg; c < cbeg + 64 && c < M; ++c) {
-        const uint32_t bit = (f < F) ? (synd[f * M + c] & 1u) : 0u;
-        const uint32_t word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) sbits[c * W + w] = word;
+    for (int64_t w = blockIdx.y; w < W; w += gridDim.y) {   // grid-stride over the words
+        const int64_t f = w * 32 + lane;
+        for (int64_t c = cbeg; c < cbeg + 64 && c < M; ++c) {
+            const uint32_t bit = (f < F) ? (synd[f * M + c] & 1u) : 0u;
+            const uint32_t word = __ballot_sync(0xffffffffu, bit);
+            if (lane == 0) sbits[c * W + w] = word;
+        }
     }
 }
 
@@ -667,7 +672,8 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int 
                           const uint8_t *__restrict__ mask, uint8_t *bits, float *post) {
     __shared__ float tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t v0 = (int64_t)blockIdx.x * 32, f0 = (int64_t)blockIdx.y * 32;
+    const int64_t v0 = (int64_t)blockIdx.x * 32;
+    for (int64_t f0 = (int64_t)blockIdx.y * 32; f0 < Fp; f0 += (int64_t)gridDim.y * 32) {
     for (int r = 0; r < 32; r += 8) {
         const int64_t v = v0 + ty + r, f = f0 + tx;
         float val = 0.0f;
@@ -684,6 +690,8 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int 
         const float val = tile[ty + r][tx];
         bits[f * n + v] = val < 0.0f ? 1 : 0;
         if (post) post[f * n + v] = PREC == kI8 ? val * step : val;
+    }
+    __syncthreads();
     }
 }
 
@@ -853,7 +861,7 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     QKD_LAUNCHED("init_state");
     {
         prof::Scope ps(prof::kPrep, st);
-        dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
+        dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
         if (prec == kI8)
             prep_llr<kI8><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L);
         else prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L);
@@ -861,7 +869,7 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     QKD_LAUNCHED("prep_llr");
     {
         prof::Scope ps(prof::kPrep, st);
-        dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)l.W);
+        dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)std::min<int64_t>(l.W, 65535));
         prep_synd<<<grd, 256, 0, st>>>(synd, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits));
     }
     QKD_LAUNCHED("prep_synd");
@@ -884,7 +892,7 @@ static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const 
     }
     QKD_LAUNCHED("finalize");
     prof::Scope ps(prof::kFinish, st);
-    dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
+    dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
     if (prec == kI8)
         write_out<kI8><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out, post_out);
     else write_out<kF32><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out, post_out);

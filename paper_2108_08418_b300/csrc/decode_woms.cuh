@@ -394,11 +394,11 @@ static void woms_forward_range(WomsArgs a, const CodeDev &d, const WomsLayout &l
 static qkdrec_status woms_prepare(const CodeDev &d, const float *llr, const uint8_t *synd, const uint8_t *target,
                                   int32_t F, char *ws, const WomsLayout &l, cudaStream_t st) {
     prof::Scope ps(prof::kPrep, st);
-    dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
+    dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
     prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, kWomsLg, 1.0f, ws + l.llr_i, ws + l.seg_L);
     prep_target<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)d.n * l.Fp, 256), 65535), 256, 0, st>>>(
         target, F, d.n, l.Fp, reinterpret_cast<uint8_t *>(ws + l.tgt_i));
-    dim3 sg((unsigned)ceil_div(d.M, 8 * 64), (unsigned)l.W);
+    dim3 sg((unsigned)ceil_div(d.M, 8 * 64), (unsigned)std::min<int64_t>(l.W, 65535));
     prep_synd<<<sg, 256, 0, st>>>(synd, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits));
     QKD_LAUNCHED("woms prepare");
     return QKDREC_OK;
@@ -443,7 +443,7 @@ qkdrec_status qkdrec_woms_forward(qkdrec_code_t code, const float *llr, const ui
         woms_loss<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)d.n * l.Fp, 256), 4096), 256, 0, st>>>(a, 0);
         copy_loss<<<1, 1, 0, st>>>(a.loss, loss_out);
         if (post_out) {
-            dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)ceil_div(l.Fp, 32));
+            dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
             write_post<<<grd, blk, 0, st>>>(LT, F, d.n, l.Fp, kWomsLg, post_out);
         }
     }

@@ -345,3 +345,62 @@ def test_full_size_sampled_frames():
     synd_out = host(q.qkdrec_syndrome(c, full["bits"]))
     assert np.array_equal(synd_out[conv], host(s)[conv])
     assert np.all(np.any(synd_out[~conv] != host(s)[~conv], axis=1))
+
+
+@pytest.mark.parametrize("logn,F", [(20, 128), (12, 32768)])
+def test_sweep_extreme_sizes_sampled_frames(logn, F):
+    """The largest and the smallest sub-blocks of the sweep in its launch
+    configuration (2^27 samples per slice): sampled frames after two SP
+    iterations against the oracle."""
+    n = 1 << logn
+    rp, ci, M = code(2000 + 100 * logn + 2, n, 0.5)
+    c = q.Code(n, rp, ci)
+    b, llr = bpsk_frames(2100 + logn, F, n, 0.8)
+    s = q.qkdrec_syndrome(c, dev(b))
+    out = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(max_iter=2, early_stop=False), want_post=True)
+    pick = [0, F // 2 + 3, F - 1]
+    s_ref = oracle.syndrome(rp, ci, b[pick])
+    assert np.array_equal(host(s[pick]), s_ref)
+    ref = oracle.decode(rp, ci, llr[pick].astype(np.float64), s_ref, "sp_flood", max_iter=2, early_stop=False)
+    assert rel_ok(host(out["post"][pick]), ref["post"]).all()
+
+
+def test_maximum_frame_count_of_one_launch():
+    """F = 65535 x 32 frames (the most one decode accepts) of a 64-variable code:
+    first, middle and last frames against the oracle; one frame more is refused."""
+    n, F = 64, 65535 * 32
+    rp, ci, M = code(2200, n, 0.5)
+    c = q.Code(n, rp, ci)
+    g = synth.philox(2201)
+    b = g.integers(0, 2, size=(F, n)).astype(np.uint8)
+    llr = ((2 / 0.8 ** 2) * ((1.0 - 2.0 * b) + 0.8 * g.standard_normal((F, n), dtype=np.float32))).astype(np.float32)
+    s = q.qkdrec_syndrome(c, dev(b))
+    out = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo="oms_flood", max_iter=3, early_stop=False),
+                                want_post=True)
+    pick = [0, 1048577, F - 1]
+    ref = oracle.decode(rp, ci, llr[pick].astype(np.float64), oracle.syndrome(rp, ci, b[pick]), "oms_flood",
+                        max_iter=3, early_stop=False, offset=0.5)
+    assert rel_ok(host(out["post"][pick]), ref["post"]).all()
+    del out
+    torch.cuda.empty_cache()
+    with pytest.raises(RuntimeError):
+        q.qkdrec_decode_batch(c, torch.zeros((F + 1, n), device="cuda"), torch.zeros((F + 1, M), dtype=torch.uint8,
+                                                                                        device="cuda"),
+                              q.DecodeOpts(algo="oms_flood", max_iter=1))
+
+
+def test_full_block_quantiser_and_llr_sampled():
+    """2^27 samples (one SNR point of the sweep) through the quantiser and the
+    slice-3 LLR with random lower bits: sampled positions against the oracle."""
+    snr, m, N = 15.0, 5, 1 << 27
+    lo, hi = oracle.quantiser_range(snr)
+    x, y = synth.gaussian_pair(3, N, snr)
+    idx, bits = q.qkdrec_quantise_slices(dev(y), m, lo, hi)
+    g = synth.philox(2300)
+    pos = np.sort(g.integers(0, N, size=20000))
+    ridx, rbits = oracle.quantise(y[pos], m, lo, hi)
+    assert np.array_equal(host(idx)[pos], ridx) and np.array_equal(host(bits)[:, pos], rbits)
+    lower = g.integers(0, 2, size=(3, N)).astype(np.uint8)
+    llr = q.qkdrec_slice_llr(dev(x), m, 3, lo, hi, snr ** -0.5, dev(lower))
+    ref = oracle.slice_llr(x[pos].astype(np.float64), lower[:, pos], 3, m, lo, hi, snr ** -0.5)
+    assert rel_ok(host(llr)[pos], ref).all()
