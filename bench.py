@@ -857,19 +857,26 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def source_region_sha(path, start, end):
+    """SHA-256 prefix of the source text from the line holding `start` up to the
+    line holding `end` (the kernel and the device helpers it compiles from)."""
+    import hashlib
+    text = open(path).read()
+    i = text.index(start)
+    j = text.index(end, i)
+    return hashlib.sha256(text[i:j].encode()).hexdigest()[:16]
+
+
 def load_traffic(kernel, d):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled by the
-    units this run's launches processed; None if no capture matches the current source."""
+    units this run's launches processed; None if no capture matches the current
+    source of that kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         t = json.load(open(path))[kernel]
+        src = os.path.join(ROOT, "paper_2108_08418_b300", "csrc", t["source"])
+        sha = source_region_sha(src, *t["region"])
     except (OSError, ValueError, KeyError):
-        return None
-    import hashlib
-    src = os.path.join(ROOT, "paper_2108_08418_b300", "csrc", t["source"])
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
         return None
     if sha != t.get("source_sha"):
         return None
