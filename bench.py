@@ -781,12 +781,12 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
 
     # correctness of the last step: frames whose decoded word equals Bob's
-    good_bits, raw_bits, fer = 0, 0, {}
+    good_bits, raw_bits, fer, mean_iters = 0, 0, {}, {}
     edge_updates = sum(v["units"] for k, v in stats.items() if k.startswith(("check_flood", "layer_oms"))) / args.steps
     for snr in SNRS:
         for ln in LOGNS:
             n, F = 1 << ln, N_SAMPLES >> ln
-            errs = []
+            errs, its = [], []
             for j in range(M_SLICES):
                 if rate_of[(snr, ln, j)] <= 0:
                     continue
@@ -795,7 +795,9 @@ def run_ours(args):
                 good_bits += n * (F - nbad)
                 raw_bits += N_SAMPLES
                 errs.append(round(nbad / F, 4))
+                its.append(round(float(iters[(snr, ln, j)].float().mean().item()), 2))
             fer[f"snr{int(snr)}_n2^{ln}"] = errs
+            mean_iters[f"snr{int(snr)}_n2^{ln}"] = its
 
     # end to end through the public API: pinned host inputs -> device, result flags back
     t_e2e = None
@@ -844,7 +846,11 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (x, y 512 MiB each per SNR; edge messages up to 1.5 GiB)",
                    "raw_decoded_bits_per_s": raw_bits / (ms_step / 1e3),
                    "edge_updates_per_s": edge_updates * world / (ms_step / 1e3),
-                   "fer_per_slice": fer, "code_residual_4cycles": residual, "setup_s": round(setup_s, 1)},
+                   # Sec. III-C: E_j = 7G operations per iteration, so the time per operation is
+                   # the step time over 7 x the edge-updates executed (the paper's GPU: 3.2e-9 s)
+                   "equivalent_c_h_s": (ms_step / 1e3) / (7 * edge_updates * world) if edge_updates else None,
+                   "fer_per_slice": fer, "mean_iters_per_slice": mean_iters,
+                   "code_residual_4cycles": residual, "setup_s": round(setup_s, 1)},
         "roofline": roof,
         "kernels": kernels,
         "cpu_baseline": cpu,
