@@ -363,7 +363,7 @@ def run_calibrate(args):
 def _oracle_uneven_frame(task):
     """Reverse reconciliation of one frame of the uneven batch by the FP64 oracle."""
     import oracle
-    x, y, snr, rates, csr = task
+    x, y, snr, rates, csr, algo, max_iter = task
     lo, hi = oracle.quantiser_range(snr)
     t0 = time.perf_counter()
     _, bits = oracle.quantise(y, M_SLICES, lo, hi)
@@ -376,13 +376,13 @@ def _oracle_uneven_frame(task):
         rp, ci = csr[j]
         s = oracle.syndrome(rp, ci, bits[j][None])
         llr = oracle.slice_llr(x.astype(np.float64), alice[:j] if j else None, j, M_SLICES, lo, hi, snr ** -0.5)
-        out = oracle.decode(rp, ci, llr[None], s, "oms_layered", max_iter=UNEVEN_MAX_ITER, offset=0.5)
+        out = oracle.decode(rp, ci, llr[None], s, algo, max_iter=max_iter, offset=0.5)
         alice[j] = out["bits"][0]
         good += y.size * int(np.array_equal(out["bits"][0], bits[j]))
     return good, time.perf_counter() - t0
 
 
-def oracle_uneven_sample(step, per_step, cores, setup=None):
+def oracle_uneven_sample(step, per_step, cores, setup=None, algo="oms_layered", max_iter=UNEVEN_MAX_ITER):
     """A bounded sample of the uneven batch: `per_step` frames of n = 4096 (spread over
     the SNR range), each reconciled over all 5 slices by the oracle."""
     n, snr, rates, codes = setup or uneven_setup(UNEVEN_SEED, max(1, min(cores, 16)))
@@ -393,7 +393,8 @@ def oracle_uneven_sample(step, per_step, cores, setup=None):
     tasks = []
     for f in pick:
         csr = {j: codes[(int(n[f]), float(rates[j, f]))][:2] for j in range(M_SLICES) if rates[j, f] > 0}
-        tasks.append((x[off[f]:off[f + 1]], y[off[f]:off[f + 1]], float(snr[f]), rates[:, f].copy(), csr))
+        tasks.append((x[off[f]:off[f + 1]], y[off[f]:off[f + 1]], float(snr[f]), rates[:, f].copy(), csr, algo,
+                      max_iter))
     t0 = time.perf_counter()
     res = _pool_map(_oracle_uneven_frame, tasks, min(cores, len(tasks)))
     wall = time.perf_counter() - t0
@@ -409,14 +410,17 @@ def run_uneven(args):
     t_setup = time.time()
     seed = UNEVEN_SEED + 1000 * rank
     n, snr, rates, codes_h = uneven_setup(seed, max(1, min(cores, 16)), args.rate_rule)
+    plain = args.uneven_decoder == "sp_f32"
+    algo, max_iter = ("sp_flood", MAX_ITER) if plain else ("oms_layered", UNEVEN_MAX_ITER)
+    algo_text = (f"sum-product flooding <= {max_iter} iterations" if plain
+                 else f"layered offset min-sum <= {max_iter} iterations")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         per = 3 * max(1, min(cores, 8))
-        good, wall, nfr = oracle_uneven_sample(0, per, cores, (n, snr, rates, codes_h))
+        good, wall, nfr = oracle_uneven_sample(0, per, cores, (n, snr, rates, codes_h), algo, max_iter)
         cpu = {"value": good / wall, "unit": "bit/s", "cores": min(cores, nfr), "kind": "oracle",
                "sample": f"{nfr} frames of n=4096 of the batch, each reconciled over all 5 slices (FP64 quantiser, "
-                         f"LLR, syndrome, layered offset min-sum <= {UNEVEN_MAX_ITER} iterations), one process "
-                         f"per frame", "wall_s": wall}
+                         f"LLR, syndrome, {algo_text}), one process per frame", "wall_s": wall}
 
     import torch
     import torch.distributed as dist
@@ -429,7 +433,8 @@ def run_uneven(args):
     residual = max(v[2] for v in codes_h.values())
     x, y = synth.gaussian_frames(seed, n, snr)
     hx, hy = torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()
-    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=UNEVEN_MAX_ITER, device=dev)
+    decoder = q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=MAX_ITER, early_stop=True) if plain else None
+    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=UNEVEN_MAX_ITER, device=dev, decoder=decoder)
     ub.x.copy_(hx)
     ub.y.copy_(hy)
     tunings = ub.autotune(max_iter=10)
@@ -503,9 +508,12 @@ def run_uneven(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: seeded Philox Gaussian quadratures and seeded regular dv=3 LDPC codes",
-        "config": {"workload": UNEVEN_WORKLOAD, "frames": int(n.size), "samples": int(n.sum()),
-                   "groups_per_slice": [len(g) for g in ub.groups], "algo": "oms_layered", "prec": "f32",
-                   "max_iter": UNEVEN_MAX_ITER, "tuning_per_slice": [t[0] for t in tunings],
+        "config": {"workload": UNEVEN_WORKLOAD if not plain else UNEVEN_WORKLOAD.replace(
+                       "layered offset min-sum FP32 (offset 0.5), <= 50 iterations",
+                       f"FP32 sum-product flooding, <= {MAX_ITER} iterations, one batch-decoder call per group"),
+                   "frames": int(n.size), "samples": int(n.sum()),
+                   "groups_per_slice": [len(g) for g in ub.groups], "algo": algo, "prec": "f32",
+                   "max_iter": max_iter, "tuning_per_slice": [t[0] for t in tunings],
                    "rate_rule": args.rate_rule,
                    "l2": "inputs larger than L2 (x, y 470 MB each; plan workspace "
                          f"{ub.ws.numel() / 2**30:.2f} GiB)",
@@ -925,11 +933,12 @@ def run_reference(args):
 def run_reference_uneven(args, world, cores):
     setup = uneven_setup(UNEVEN_SEED, max(1, min(cores, 16)), args.rate_rule)
     per = 3 * max(1, min(cores, 8))
+    algo, max_iter = ("sp_flood", MAX_ITER) if args.uneven_decoder == "sp_f32" else ("oms_layered", UNEVEN_MAX_ITER)
     for w in range(args.warmup):
-        oracle_uneven_sample(w, per, cores, setup)
+        oracle_uneven_sample(w, per, cores, setup, algo, max_iter)
     goods, walls, nfr = 0, 0.0, 0
     for s in range(args.steps):
-        g, wall, nfr = oracle_uneven_sample(args.warmup + s, per, cores, setup)
+        g, wall, nfr = oracle_uneven_sample(args.warmup + s, per, cores, setup, algo, max_iter)
         goods += g
         walls += wall
     value = goods / walls
@@ -1071,6 +1080,9 @@ def main():
                     help="sweep workload: decoder form (default FP32 sum-product; others re-decode failures in FP32)")
     ap.add_argument("--soft-chain", action="store_true",
                     help="sweep: slice LLRs from the lower slices' decoder posteriors (soft) instead of their bits")
+    ap.add_argument("--uneven-decoder", choices=["plan", "sp_f32"], default="plan",
+                    help="uneven workload: one persistent layered min-sum plan launch per slice (default) or the "
+                         "plain FP32 sum-product batch decoder on every group")
     ap.add_argument("--fallback", choices=["sp", "same"], default="sp",
                     help="low-precision decoders: re-decode failed frames with FP32 sum-product (default) or "
                          "with the same algorithm in FP32")

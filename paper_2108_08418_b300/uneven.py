@@ -25,7 +25,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import DecodeOpts, Plan, qkdrec_quantise_slices_frames, qkdrec_slice_llr_frames, qkdrec_syndrome
-from . import qkdrec_quantise_slices, qkdrec_slice_llr, quantiser_range
+from . import qkdrec_decode_batch, qkdrec_decode_workspace_size, qkdrec_quantise_slices, qkdrec_slice_llr
+from . import quantiser_range
 
 
 def _torch():
@@ -36,11 +37,16 @@ def _torch():
 class UnevenBatch:
     """lengths int [F] (samples per frame, in sample order); snrs float [F];
     rates float [m][F] (0 = the slice of that frame is disclosed); codes: dict
-    (n, rate) -> Code for every decoded (n_f, rates[j][f]) pair."""
+    (n, rate) -> Code for every decoded (n_f, rates[j][f]) pair.
+
+    decoder: None (default) decodes each slice with one persistent plan launch
+    (layered offset min-sum, `max_iter`, `offset`); a DecodeOpts instead runs
+    the plain batch decoder on every group of the slice in turn with those
+    options (the same step otherwise, also capturable)."""
 
     def __init__(self, lengths, snrs, rates, codes, m_slices: int = 5, label: str = "gray",
                  max_iter: int = 50, offset: float = 0.5, tuning: dict | None = None, device="cuda",
-                 va: float = 1.0):
+                 va: float = 1.0, decoder: DecodeOpts | None = None):
         torch = _torch()
         self.lengths = np.asarray(lengths, dtype=np.int64)
         self.snrs = np.asarray(snrs, dtype=np.float64)
@@ -67,6 +73,7 @@ class UnevenBatch:
         self.iters = torch.zeros((self.m, F), dtype=torch.int32, device=dev)
         self.conv = torch.ones((self.m, F), dtype=torch.uint8, device=dev)
         self.opts = DecodeOpts(algo="oms_layered", prec="f32", max_iter=max_iter, offset=offset, early_stop=True)
+        self.group_opts = decoder
         self.codes = codes
         # per slice: groups (runs of frames with one code) and disclosed sample ranges
         self.groups, self.disclosed, self.synd, self.plans, self.llr_runs = [], [], [], [], []
@@ -107,8 +114,14 @@ class UnevenBatch:
             self.llr_runs.append(runs_j)
             self.disclosed.append(opened)
             self.synd.append(synd)
-            self.plans.append(Plan(groups, self.opts, tuning))
-        self.ws = torch.empty(max(p.workspace_size() for p in self.plans), dtype=torch.uint8, device=dev)
+            if decoder is None:
+                self.plans.append(Plan(groups, self.opts, tuning))
+        if decoder is None:
+            ws = max(p.workspace_size() for p in self.plans)
+        else:
+            ws = max([qkdrec_decode_workspace_size(g["code"], g["f1"] - g["f0"], decoder)
+                      for gs in self.groups for g in gs] or [1])
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
         self.graph = None
 
     # ------------------------------------------------------------------ run
@@ -124,7 +137,11 @@ class UnevenBatch:
             for f, g in self.llr_runs[j]:
                 qkdrec_slice_llr_frames(self.x, self.d_off[f:g + 1], self.d_params[f:g], self.m, j,
                                         self.alice[:j] if j else None, self.label, out=self.llr)
-            if self.groups[j]:
+            if self.group_opts is not None:
+                for g in self.groups[j]:
+                    qkdrec_decode_batch(g["code"], g["llr"], g["synd"], self.group_opts, workspace=self.ws,
+                                        out=dict(bits=g["bits"], iters=g["iters"], converged=g["conv"]))
+            elif self.groups[j]:
                 self.plans[j].launch(self.ws)
             for a, b in self.disclosed[j]:
                 self.alice[j, a:b].copy_(self.bob[j, a:b])
@@ -133,6 +150,8 @@ class UnevenBatch:
         """Pick each slice plan's fastest tuning on the batch now in x, y (synchronous)."""
         torch = _torch()
         out = []
+        if self.group_opts is not None:
+            return [(None, 0.0)] * self.m
         self.step()
         torch.cuda.synchronize(self.device)
         for j, p in enumerate(self.plans):

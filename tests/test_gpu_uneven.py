@@ -84,7 +84,7 @@ def per_group_reference(ub, x, y):
         for g in ub.groups[j]:
             nf, n = g["f1"] - g["f0"], g["code"].n
             s = q.qkdrec_syndrome(g["code"], bob[j, g["a"]:g["b"]].view(nf, n))
-            out = q.qkdrec_decode_batch(g["code"], llr[g["a"]:g["b"]].view(nf, n), s, ub.opts)
+            out = q.qkdrec_decode_batch(g["code"], llr[g["a"]:g["b"]].view(nf, n), s, ub.group_opts or ub.opts)
             alice[j, g["a"]:g["b"]] = out["bits"].view(-1)
             iters[j, g["f0"]:g["f1"]] = out["iters"]
             conv[j, g["f0"]:g["f1"]] = out["converged"]
@@ -119,6 +119,26 @@ def test_uneven_graph_equals_per_group_calls_and_replays():
     torch.cuda.synchronize()
     bob2, alice2, iters2, conv2 = per_group_reference(ub, x2, y2)
     assert torch.equal(ub.alice, alice2) and torch.equal(ub.iters, iters2) and torch.equal(ub.conv, conv2)
+    ub.destroy()
+
+
+def test_uneven_plain_decoder_graph_equals_per_group_calls():
+    """The same batch with the plain FP32 sum-product batch decoder on every group
+    instead of the plan: graph replay equals the per-group calls."""
+    n, snr, rates, codes, csr, x, y = make_batch(44, 40)
+    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, device="cuda",
+                     decoder=q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=40, early_stop=True))
+    assert ub.plans == [] and ub.autotune() == [(None, 0.0)] * M_SLICES
+    ub.x.copy_(torch.from_numpy(x))
+    ub.y.copy_(torch.from_numpy(y))
+    ub.replay()
+    torch.cuda.synchronize()
+    bob, alice, iters, conv = per_group_reference(ub, x, y)
+    assert torch.equal(ub.bob, bob)
+    assert torch.equal(ub.alice, alice)
+    assert torch.equal(ub.iters, iters)
+    assert torch.equal(ub.conv, conv)
+    assert ub.frame_ok().cpu().numpy().mean() > 0.5
     ub.destroy()
 
 
