@@ -504,6 +504,139 @@ check_flood_i(DecArgs a) {
     prof_add(a.prof, units, units * (a.do_msgs ? 4 : 2));
 }
 
+// ------------------------------------------ integer check kernel, 16-bit lanes
+// The same offset min-sum check update as check_flood_i<4, 32>, bit for bit,
+// with a lane's four frames held as two pairs of 16-bit lanes (s16x2: frames
+// 0-1 and 2-3), so that one min/max/add serves two frames.  Identities used
+// (every lane value is small: |L| <= 31 (dv + 1), |m|, |q| <= 31):
+//   t = ~L + m = -q - 1 per lane, so q = ~t, -q = t + 1, sign(q) = NOT sign(t);
+//   the second minimum is needed exactly where |q_k| equals the minimum (if
+//   another edge shares the minimum, the second minimum equals it), so no
+//   argmin is tracked;  max(x - 1, 0) commutes with that choice, so the
+//   offset is applied to the two minima once per check.
+// Pass 1 keeps |q| with the sign of q in bit 7 of one byte per frame
+// (four frames in a word) in shared memory for pass 2.
+__device__ __forceinline__ uint32_t vmin_s16(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t vmax_s16(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t vmin_u16(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t vadd_16(uint32_t a, uint32_t b) {   // lane-wise, no carry between lanes
+    uint32_t r;
+    asm("add.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+    return r;
+}
+// sign bits 15 and 31 of a pair -> frame bits (b0 -> bit `lo`, b1 -> bit lo + 1)
+__device__ __forceinline__ uint32_t pair_signs(uint32_t x, int lo) {
+    return (((x >> 15) & 1u) | ((x >> 30) & 2u)) << lo;
+}
+
+__global__ void __launch_bounds__(kCheckWarps * 32, 4)
+check_flood_i16x2(DecArgs a) {
+    extern __shared__ uint32_t istash[];   // [kCheckWarps][dstash][32]: per edge, four frames of |q| | sign << 7
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int fvw = a.fvw, slots = 32 / fvw;
+    const int slot = lane / fvw, lfv = lane - slot * fvw;
+    const int16_t *L = reinterpret_cast<const int16_t *>(a.L);
+    int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
+    const int64_t nvec = a.Fp / 4;
+    constexpr int CH = 2;
+    constexpr int LG = lgfb_of<4>();
+    constexpr uint32_t kOnes = 0x00010001u, kMax = 0x001F001Fu;   // 1 and kQMax in both lanes
+    uint32_t *my = istash + (warp * a.dstash) * 32 + lane;
+    unsigned long long units = 0;
+    const int32_t nblk = *a.blk_n;
+    for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
+        const int64_t fb = __ldg(a.blk + bi);
+        const int64_t fv = fb * fvw + lfv, f0 = fv * 4;
+        const bool fv_ok = fv < nvec;
+        const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);
+        const uint32_t act = fv_ok ? active_bits<4>(a.active + f0) : 0u;
+        uint32_t unsat_bits = 0;
+        if (act) {
+            const int nact = __popc(act);
+            const int64_t c0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * (kChecksPerWarp * slots);
+            for (int it = 0; it < kChecksPerWarp; ++it) {
+                const int64_t c = c0 + it * slots + slot;
+                if (c >= a.M) break;
+                const int32_t beg = __ldg(a.rp + c), end = __ldg(a.rp + c + 1), d = end - beg;
+                const uint32_t s = (__ldg(a.sbits + c * a.W + (f0 >> 5)) >> (f0 & 31)) & 0xFu;
+                uint32_t pA = 0, pB = 0;                 // xor of L: hard decisions in the sign bits
+                uint32_t nA = 0, nB = 0;                 // xor of t = -q - 1
+                uint32_t m1A = 0x7FFF7FFFu, m1B = 0x7FFF7FFFu, m2A = 0x7FFF7FFFu, m2B = 0x7FFF7FFFu;
+                units += (unsigned long long)d * nact;
+                auto edge = [&](uint32_t Lx, uint32_t mx, uint32_t &m1, uint32_t &m2, uint32_t &n) {
+                    const uint32_t t = vadd_16(~Lx, mx);
+                    const uint32_t q = ~t;
+                    const uint32_t aq = vmin_s16(vmax_s16(q, vadd_16(t, kOnes)), kMax);   // |clamp(q)|
+                    n ^= t;
+                    m2 = vmin_s16(m2, vmax_s16(m1, aq));
+                    m1 = vmin_s16(m1, aq);
+                    return aq | ((q >> 8) & 0x00800080u);
+                };
+                for (int k0 = 0; k0 < d; k0 += CH) {
+                    uint2 Lw[CH];
+                    uint32_t mw[CH];
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        const int32_t e = beg + min(k0 + j, d - 1);
+                        Lw[j] = *reinterpret_cast<const uint2 *>(L + bL + ((uint32_t)__ldg(a.ci + e) << LG));
+                        mw[j] = a.do_msgs ? __ldcs(reinterpret_cast<const unsigned int *>(msg + bM + ((uint32_t)e << LG)))
+                                          : 0u;
+                    }
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        const int k = k0 + j;
+                        if (k >= d) break;
+                        pA ^= Lw[j].x;
+                        pB ^= Lw[j].y;
+                        const uint32_t sa = edge(Lw[j].x, prmt(mw[j], 0u, 0x9180u), m1A, m2A, nA);
+                        const uint32_t sb = edge(Lw[j].y, prmt(mw[j], 0u, 0xB3A2u), m1B, m2B, nB);
+                        my[k * 32] = prmt(sa, sb, 0x6420u);
+                    }
+                }
+                unsat_bits |= (s ^ pair_signs(pA, 0) ^ pair_signs(pB, 2)) & act;
+                if (!a.do_msgs) continue;
+                // per frame: syndrome xor the signs of all q (sign(q) = NOT sign(t))
+                const uint32_t neg = s ^ pair_signs(nA, 0) ^ pair_signs(nB, 2) ^ ((d & 1) ? 0xFu : 0u);
+                const uint32_t NA = ((neg & 1u) << 7) | ((neg & 2u) << 22), NB = ((neg & 4u) << 5) | ((neg & 8u) << 20);
+                const uint32_t o1A = vmax_s16(vadd_16(m1A, 0xFFFFFFFFu), 0u), o2A = vmax_s16(vadd_16(m2A, 0xFFFFFFFFu), 0u);
+                const uint32_t o1B = vmax_s16(vadd_16(m1B, 0xFFFFFFFFu), 0u), o2B = vmax_s16(vadd_16(m2B, 0xFFFFFFFFu), 0u);
+                auto out = [&](uint32_t w, uint32_t m1, uint32_t o1, uint32_t o2, uint32_t N) {
+                    const uint32_t u = vmin_u16((w & kMax) - m1, kOnes) ^ kOnes;   // 1 where |q| is the minimum
+                    const uint32_t mag = vmin_u16(o2, u * 0x7FFFu + o1);          // u ? o2 : o1
+                    const uint32_t sg = ((w ^ N) >> 7) & kOnes;                     // 1 where the message is negative
+                    return vadd_16(mag ^ (sg * 0xFFFFu), sg);
+                };
+                for (int k = 0; k < d; ++k) {
+                    const uint32_t w = my[k * 32];
+                    const uint32_t rA = out(prmt(w, 0u, 0x4140u), m1A, o1A, o2A, NA);
+                    const uint32_t rB = out(prmt(w, 0u, 0x4342u), m1B, o1B, o2B, NB);
+                    __stcs(reinterpret_cast<unsigned int *>(msg + bM + ((uint32_t)(beg + k) << LG)), prmt(rA, rB, 0x6420u));
+                }
+            }
+        }
+        if (a.early_stop || !a.do_msgs)
+            publish_unsat<4>(unsat_bits, f0, fb * fvw * 4, fv_ok, a.unsat_cur);
+    }
+    prof_add(a.prof, units, units * (a.do_msgs ? 4 : 2));
+}
+
 // ------------------------------------------------------------ variable kernels
 // Retire frames whose stopping test passed on L^(t-1); update the rest:
 // L_v = llr_v + sum of the messages on the edges of v (ascending edge order).
@@ -573,6 +706,83 @@ __global__ void __launch_bounds__(256) var_flood(DecArgs a) {
                     if (!((upd >> i) & 1u)) s.v[i] = old.v[i];
             }
             sti16<4>(L + pv, s);
+        }
+    }
+    prof_add(a.prof, units, bytes);
+}
+
+// Integer flooding, variable side, 16 frames per thread as eight pairs of
+// 16-bit lanes: thread (listed frame block on y, (variable, group of 16 frames)
+// on x).  Sums are the same as var_flood<kI8>'s: with |L| <= kQMax (dv + 1)
+// the saturation at kPMax is never reached, so plain lane-wise adds agree.
+__global__ void __launch_bounds__(256) var_flood_i8x16(DecArgs a) {
+    constexpr int LG = lgfb_of<4>();                   // 128-frame blocks: 8 groups of 16
+    const int64_t items = (int64_t)a.n * 8;
+    const int16_t *Lc = reinterpret_cast<const int16_t *>(a.L);
+    int16_t *L = reinterpret_cast<int16_t *>(a.L);
+    const int8_t *llr = reinterpret_cast<const int8_t *>(a.llr_i);
+    const int8_t *msg = reinterpret_cast<const int8_t *>(a.msg);
+    unsigned long long units = 0, bytes = 0;
+    const int32_t nblk = *a.blk_n;
+    for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
+        const int64_t fb = __ldg(a.blk + bi);
+        for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
+             idx += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t v = idx >> 3, f0 = (fb << LG) + ((idx & 7) << 4);
+            const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);
+            if (v == 0 && (f0 & 31) == 0 && a.early_stop) a.unsat_next[f0 >> 5] = 0;   // next test starts clear
+            const uint4 aw = *reinterpret_cast<const uint4 *>(a.active + f0);
+            const uint32_t act = active_bits<4>(reinterpret_cast<const uint8_t *>(&aw.x)) |
+                                 (active_bits<4>(reinterpret_cast<const uint8_t *>(&aw.y)) << 4) |
+                                 (active_bits<4>(reinterpret_cast<const uint8_t *>(&aw.z)) << 8) |
+                                 (active_bits<4>(reinterpret_cast<const uint8_t *>(&aw.w)) << 12);
+            if (!act) continue;
+            const uint32_t u = a.early_stop ? (__ldcg(a.unsat_cur + (f0 >> 5)) >> (f0 & 31)) & 0xffffu : 0xffffu;
+            const uint32_t done = a.early_stop ? (act & ~u) : 0u;
+            const uint32_t upd = act & ~done;
+            if (v == 0)
+                for (uint32_t r = done; r; r &= r - 1) {
+                    const int i = __ffs(r) - 1;
+                    a.active[f0 + i] = 0;
+                    a.iters_i[f0 + i] = a.t - 1;
+                }
+            if (!upd) continue;
+            const int32_t vb = __ldg(a.vptr + v), ve = __ldg(a.vptr + v + 1);
+            const int64_t pv = bL + (v << LG);
+            const unsigned nu = __popc(upd);
+            units += nu;
+            bytes += (unsigned long long)nu * ((ve - vb) + 1 + 2);
+            uint32_t acc[8];
+            {
+                const uint4 c = __ldg(reinterpret_cast<const uint4 *>(llr + pv));
+                const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
+                for (int w = 0; w < 4; ++w) {
+                    acc[2 * w] = prmt(cw[w], 0u, 0x9180u);       // frames 4w, 4w+1 sign-extended
+                    acc[2 * w + 1] = prmt(cw[w], 0u, 0xB3A2u);   // frames 4w+2, 4w+3
+                }
+            }
+            for (int32_t k = vb; k < ve; ++k) {
+                const int64_t e = __ldg(a.vedge + k);
+                const uint4 m = __ldcs(reinterpret_cast<const uint4 *>(msg + bM + (e << LG)));
+                const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+                for (int w = 0; w < 4; ++w) {
+                    acc[2 * w] = vadd_16(acc[2 * w], prmt(mw[w], 0u, 0x9180u));
+                    acc[2 * w + 1] = vadd_16(acc[2 * w + 1], prmt(mw[w], 0u, 0xB3A2u));
+                }
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(L + pv);
+            if (upd != 0xffffu) {
+                // frames not updated keep their posterior
+                const uint4 o0 = reinterpret_cast<const uint4 *>(Lc + pv)[0], o1 = reinterpret_cast<const uint4 *>(Lc + pv)[1];
+                const uint32_t old[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+                for (int r = 0; r < 8; ++r) {
+                    const uint32_t keep = (((upd >> (2 * r)) & 1u) ? 0u : 0x0000ffffu) |
+                                          (((upd >> (2 * r + 1)) & 1u) ? 0u : 0xffff0000u);
+                    acc[r] = (acc[r] & ~keep) | (old[r] & keep);
+                }
+            }
+            dst[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+            dst[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
         }
     }
     prof_add(a.prof, units, bytes);
@@ -915,7 +1125,10 @@ static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaSt
     a.dstash = std::min(std::max(d.dc_max, 1), kStash);
     const size_t stash = (size_t)kCheckWarps * a.dstash * 32 * sizeof(float);
     if (prec == kI8) {
+        // 16-bit lanes need L - m to stay inside int16: |L| <= kQMax (dv + 1)
         if (V == 1) check_flood_i<1, 32><<<g.grid, B, 0, st>>>(a);
+        else if (cached && d.dv_max <= 1000)
+            check_flood_i16x2<<<g.grid, B, (size_t)kCheckWarps * a.dstash * 32 * sizeof(uint32_t), st>>>(a);
         else if (cached) check_flood_i<4, 32><<<g.grid, B, 0, st>>>(a);
         else check_flood_i<4, 0><<<g.grid, B, 0, st>>>(a);
     } else if (algo == QKDREC_SP_FLOOD) {
@@ -951,6 +1164,10 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
     if (s != QKDREC_OK) return s;
     const int64_t vitems = (int64_t)d.n * l.FV;
     const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(vitems, 256), (int64_t)sm_count() * 64);
+    // integer form: (variable, 16 frames) on x, listed frame blocks on y
+    const bool i16 = prec == kI8 && l.lgfb == lgfb_of<4>() && d.dv_max <= 1000;
+    dim3 igrid((unsigned)std::min<int64_t>(ceil_div((int64_t)d.n * 8, 256), (int64_t)sm_count() * 64), 1);
+    igrid.y = (unsigned)std::max<int64_t>(1, std::min<int64_t>(l.Fp >> l.lgfb, (int64_t)sm_count() * 64 / igrid.x));
 
     auto check = [&](int t, int do_msgs) {
         a.t = t;
@@ -973,7 +1190,8 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
             const int kind = prec == kI8 ? prof::kVarI8 : (prec == kF16 ? prof::kVarF16 : prof::kVarF32);
             a.prof = prof::counters(kind);
             prof::Scope ps(kind, st);
-            if (prec == kI8) var_flood<kI8><<<vgrid, 256, 0, st>>>(a);
+            if (i16) var_flood_i8x16<<<igrid, 256, 0, st>>>(a);
+            else if (prec == kI8) var_flood<kI8><<<vgrid, 256, 0, st>>>(a);
             else if (prec == kF16) var_flood<kF16><<<vgrid, 256, 0, st>>>(a);
             else var_flood<kF32><<<vgrid, 256, 0, st>>>(a);
         }
