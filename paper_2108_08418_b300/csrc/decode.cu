@@ -555,7 +555,7 @@ check_flood_i16x2(DecArgs a) {
     const int16_t *L = reinterpret_cast<const int16_t *>(a.L);
     int8_t *msg = reinterpret_cast<int8_t *>(a.msg);
     const int64_t nvec = a.Fp / 4;
-    constexpr int CH = 2;
+    constexpr int CH = 4;
     constexpr int LG = lgfb_of<4>();
     constexpr uint32_t kOnes = 0x00010001u, kMax = 0x001F001Fu;   // 1 and kQMax in both lanes
     uint32_t *my = istash + (warp * a.dstash) * 32 + lane;
@@ -761,13 +761,24 @@ __global__ void __launch_bounds__(256) var_flood_i8x16(DecArgs a) {
                     acc[2 * w + 1] = prmt(cw[w], 0u, 0xB3A2u);   // frames 4w+2, 4w+3
                 }
             }
-            for (int32_t k = vb; k < ve; ++k) {
-                const int64_t e = __ldg(a.vedge + k);
-                const uint4 m = __ldcs(reinterpret_cast<const uint4 *>(msg + bM + (e << LG)));
-                const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
-                for (int w = 0; w < 4; ++w) {
-                    acc[2 * w] = vadd_16(acc[2 * w], prmt(mw[w], 0u, 0x9180u));
-                    acc[2 * w + 1] = vadd_16(acc[2 * w + 1], prmt(mw[w], 0u, 0xB3A2u));
+            // edges in chunks of four: the index loads, then the message loads,
+            // are issued together (a variable of degree 3 is one chunk)
+            for (int32_t k0 = vb; k0 < ve; k0 += 4) {
+                int32_t e[4];
+                uint4 m[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) e[j] = __ldg(a.vedge + min(k0 + j, ve - 1));
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (k0 + j < ve) m[j] = __ldcs(reinterpret_cast<const uint4 *>(msg + bM + ((int64_t)e[j] << LG)));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (k0 + j >= ve) break;
+                    const uint32_t mw[4] = {m[j].x, m[j].y, m[j].z, m[j].w};
+                    for (int w = 0; w < 4; ++w) {
+                        acc[2 * w] = vadd_16(acc[2 * w], prmt(mw[w], 0u, 0x9180u));
+                        acc[2 * w + 1] = vadd_16(acc[2 * w + 1], prmt(mw[w], 0u, 0xB3A2u));
+                    }
                 }
             }
             uint4 *dst = reinterpret_cast<uint4 *>(L + pv);
