@@ -800,20 +800,30 @@ __global__ void __launch_bounds__(256) var_flood_i8x16(DecArgs a) {
 }
 
 // ------------------------------------------------------- layout conversions
+// Frame placement of a decode pass: position f holds frame f, or, in a
+// compacted re-decode, frame fmap[f] for f < *fcnt (the frames a first pass
+// left unsatisfied, packed to the front; later positions hold no frame).
+__device__ __forceinline__ int64_t frames_placed(int32_t F, const int32_t *fcnt) { return fcnt ? *fcnt : F; }
+__device__ __forceinline__ int64_t frame_at(int64_t f, const int32_t *fmap) { return fmap ? fmap[f] : f; }
+
 // llr [F][n] -> llr_i [n][Fp] and L [n][Fp]; padding frames get a
 // confident all-zero word (they satisfy a zero syndrome at iteration 0).
 template <int PREC>
 __global__ void prep_llr(const float *__restrict__ llr, int32_t F, int32_t n, int64_t Fp, int lgfb,
-                         float step, void *llr_i, void *L) {
+                         float step, void *llr_i, void *L, const int32_t *fmap = nullptr,
+                         const int32_t *fcnt = nullptr) {
     __shared__ float tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t v0 = (int64_t)blockIdx.x * 32;
+    const int64_t Fv = frames_placed(F, fcnt);
+    // positions past the placed frames of a compacted pass are never read
+    const int64_t Fend = fcnt ? min(Fp, (Fv + 31) & ~(int64_t)31) : Fp;
     // frame groups of 32, grid-stride (a padded frame count can exceed 65535 groups)
-    for (int64_t f0 = (int64_t)blockIdx.y * 32; f0 < Fp; f0 += (int64_t)gridDim.y * 32) {
+    for (int64_t f0 = (int64_t)blockIdx.y * 32; f0 < Fend; f0 += (int64_t)gridDim.y * 32) {
     for (int r = 0; r < 32; r += 8) {
         const int64_t f = f0 + ty + r, v = v0 + tx;
         float val = kLlrClip;
-        if (f < F && v < n) val = llr[f * n + v];
+        if (f < Fv && v < n) val = llr[frame_at(f, fmap) * n + v];
         tile[ty + r][tx] = val;
     }
     __syncthreads();
@@ -841,13 +851,16 @@ __global__ void prep_llr(const float *__restrict__ llr, int32_t F, int32_t n, in
 
 // synd [F][M] (bytes) -> sbits [M][W] (bit f%32 of word f/32).
 __global__ void prep_synd(const uint8_t *__restrict__ synd, int32_t F, int32_t M, int64_t W,
-                          uint32_t *__restrict__ sbits) {
+                          uint32_t *__restrict__ sbits, const int32_t *fmap = nullptr,
+                          const int32_t *fcnt = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t cbeg = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 64;
-    for (int64_t w = blockIdx.y; w < W; w += gridDim.y) {   // grid-stride over the words
+    const int64_t Fv = frames_placed(F, fcnt);
+    const int64_t Wend = fcnt ? min(W, (Fv + 31) >> 5) : W;
+    for (int64_t w = blockIdx.y; w < Wend; w += gridDim.y) {   // grid-stride over the words
         const int64_t f = w * 32 + lane;
         for (int64_t c = cbeg; c < cbeg + 64 && c < M; ++c) {
-            const uint32_t bit = (f < F) ? (synd[f * M + c] & 1u) : 0u;
+            const uint32_t bit = (f < Fv) ? (synd[frame_at(f, fmap) * M + c] & 1u) : 0u;
             const uint32_t word = __ballot_sync(0xffffffffu, bit);
             if (lane == 0) sbits[c * W + w] = word;
         }
@@ -855,17 +868,18 @@ __global__ void prep_synd(const uint8_t *__restrict__ synd, int32_t F, int32_t M
 }
 
 // per-frame state; `mask` marks the frames this decode owns (all real frames,
-// or only the frames a low-precision pass left unsatisfied)
+// or only the frames a low-precision pass left unsatisfied, in place or
+// compacted to the first *fcnt positions)
 __global__ void init_state(int32_t F, int64_t Fp, int64_t W, const uint8_t *__restrict__ conv_prev,
                            uint8_t *active, uint8_t *mask, int32_t *iters_i, uint32_t *unsat0,
-                           uint32_t *unsat1) {
+                           uint32_t *unsat1, const int32_t *fcnt = nullptr) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f < W) {
         unsat0[f] = 0;
         unsat1[f] = 0;
     }
     if (f >= Fp) return;
-    const uint8_t a = (f < F) && (!conv_prev || !conv_prev[f]);
+    const uint8_t a = fcnt ? (f < *fcnt) : ((f < F) && (!conv_prev || !conv_prev[f]));
     active[f] = a;
     mask[f] = a;
     iters_i[f] = 0;
@@ -874,27 +888,57 @@ __global__ void init_state(int32_t F, int64_t Fp, int64_t W, const uint8_t *__re
 // `accumulate`: a re-decode adds its iterations to those of the first pass.
 __global__ void finalize(int32_t F, int32_t T, int32_t accumulate, const uint8_t *__restrict__ mask,
                          const uint8_t *__restrict__ active, const int32_t *__restrict__ iters_i,
-                         const uint32_t *__restrict__ unsat, int32_t *iters_out, uint8_t *conv_out) {
+                         const uint32_t *__restrict__ unsat, int32_t *iters_out, uint8_t *conv_out,
+                         const int32_t *fmap = nullptr) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F || !mask[f]) return;
-    const int32_t base = accumulate ? iters_out[f] : 0;
+    const int64_t g = frame_at(f, fmap);      // the frame at position f
+    const int32_t base = accumulate ? iters_out[g] : 0;
     if (active[f]) {
-        iters_out[f] = base + T;
-        conv_out[f] = !((unsat[f >> 5] >> (f & 31)) & 1u);
+        iters_out[g] = base + T;
+        conv_out[g] = !((unsat[f >> 5] >> (f & 31)) & 1u);
     } else {
-        iters_out[f] = base + iters_i[f];
-        conv_out[f] = 1;
+        iters_out[g] = base + iters_i[f];
+        conv_out[g] = 1;
     }
+}
+
+// Compacted re-decode: the frames with conv_prev[f] == 0, packed to positions
+// 0 .. *fcnt - 1 (*fcnt cleared before the launch).  Their order depends on
+// scheduling; each frame decodes alone, so the results do not.
+__global__ void compact_failed(int32_t F, const uint8_t *__restrict__ conv_prev, int32_t *fmap,
+                               int32_t *fcnt) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool fail = f < F && !conv_prev[f];
+    const uint32_t m = __ballot_sync(0xffffffffu, fail);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(fcnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (fail) fmap[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)f;
+}
+
+// Clear the messages of the frame blocks that hold placed frames (compacted
+// pass: *fcnt frames from position 0; frame-block-major layout, so they are
+// one contiguous prefix of block_bytes per block).
+__global__ void zero_placed_msgs(uint4 *msg, int64_t block_bytes, int lgfb, const int32_t *fcnt) {
+    const int64_t nb = ((int64_t)*fcnt + (1 << lgfb) - 1) >> lgfb;
+    const int64_t words = nb * block_bytes / 16;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+        msg[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // L [n][Fp] -> bits [F][n] (+ posterior [F][n]) for the frames in `mask`.
 template <int PREC>
 __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int lgfb, float step,
-                          const uint8_t *__restrict__ mask, uint8_t *bits, float *post) {
+                          const uint8_t *__restrict__ mask, uint8_t *bits, float *post,
+                          const int32_t *fmap = nullptr, const int32_t *fcnt = nullptr) {
     __shared__ float tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int64_t v0 = (int64_t)blockIdx.x * 32;
-    for (int64_t f0 = (int64_t)blockIdx.y * 32; f0 < Fp; f0 += (int64_t)gridDim.y * 32) {
+    const int64_t Fend = fcnt ? min(Fp, ((int64_t)*fcnt + 31) & ~(int64_t)31) : Fp;
+    for (int64_t f0 = (int64_t)blockIdx.y * 32; f0 < Fend; f0 += (int64_t)gridDim.y * 32) {
     for (int r = 0; r < 32; r += 8) {
         const int64_t v = v0 + ty + r, f = f0 + tx;
         float val = 0.0f;
@@ -909,8 +953,9 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int 
         const int64_t f = f0 + ty + r, v = v0 + tx;
         if (f >= F || v >= n || !mask[f]) continue;
         const float val = tile[ty + r][tx];
-        bits[f * n + v] = val < 0.0f ? 1 : 0;
-        if (post) post[f * n + v] = PREC == kI8 ? val * step : val;
+        const int64_t g = frame_at(f, fmap);
+        bits[g * n + v] = val < 0.0f ? 1 : 0;
+        if (post) post[g * n + v] = PREC == kI8 ? val * step : val;
     }
     __syncthreads();
     }
@@ -920,7 +965,7 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int 
 struct Layout {
     int64_t Fp, FV, W;
     int lgfb;
-    size_t llr_i, L, msg, sbits, active, mask, unsat0, unsat1, iters, blk, blk_n, total;
+    size_t llr_i, L, msg, sbits, active, mask, unsat0, unsat1, iters, blk, blk_n, fmap, fcnt, total;
 };
 
 // register-cache size of the check kernels for a code: 8 or 32 edges, 0 = reload
@@ -957,6 +1002,8 @@ static Layout make_layout(const CodeDev &d, int32_t F, int algo, int prec) {
     l.iters = take((size_t)l.Fp * 4);
     l.blk = take((size_t)(l.Fp >> l.lgfb) * 4);
     l.blk_n = take(4);
+    l.fmap = take((size_t)l.Fp * 4);
+    l.fcnt = take(4);
     l.total = off;
     return l;
 }
@@ -1040,9 +1087,11 @@ static qkdrec_status rebuild_blocks(const Layout &l, char *ws, cudaStream_t st) 
 
 // Shared set-up of one decode pass: per-frame state, interleaved LLRs and
 // posteriors, packed syndromes, zero messages.
+// compact: decode the frames with conv_prev[f] == 0 packed to the front (a
+// re-decode then touches only the frame blocks that hold them)
 static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
-                             const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, char *ws,
-                             const Layout &l, cudaStream_t st, DecArgs &a, Prepared &pr) {
+                             const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, bool compact,
+                             char *ws, const Layout &l, cudaStream_t st, DecArgs &a, Prepared &pr) {
     a.rp = d.rp;
     a.ci = d.ci;
     a.vptr = d.vptr;
@@ -1074,28 +1123,45 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     a.unsat_next = pr.unsat[1];
     a.blk = reinterpret_cast<const int32_t *>(ws + l.blk);
     a.blk_n = reinterpret_cast<const int32_t *>(ws + l.blk_n);
+    int32_t *fmap = compact ? reinterpret_cast<int32_t *>(ws + l.fmap) : nullptr;
+    int32_t *fcnt = compact ? reinterpret_cast<int32_t *>(ws + l.fcnt) : nullptr;
+    if (compact) {
+        QKD_CUDA(cudaMemsetAsync(fcnt, 0, sizeof(int32_t), st));
+        prof::Scope ps(prof::kPrep, st);
+        compact_failed<<<(unsigned)ceil_div(F, 256), 256, 0, st>>>(F, conv_prev, fmap, fcnt);
+        QKD_LAUNCHED("compact_failed");
+    }
     {
         prof::Scope ps(prof::kPrep, st);
         init_state<<<(unsigned)ceil_div(std::max<int64_t>(l.Fp, l.W), 256), 256, 0, st>>>(
-            F, l.Fp, l.W, conv_prev, a.active, pr.mask, a.iters_i, pr.unsat[0], pr.unsat[1]);
+            F, l.Fp, l.W, conv_prev, a.active, pr.mask, a.iters_i, pr.unsat[0], pr.unsat[1], fcnt);
     }
     QKD_LAUNCHED("init_state");
     {
         prof::Scope ps(prof::kPrep, st);
         dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
         if (prec == kI8)
-            prep_llr<kI8><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L);
-        else prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L);
+            prep_llr<kI8><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L, fmap,
+                                                fcnt);
+        else prep_llr<kF32><<<grd, blk, 0, st>>>(llr, F, d.n, l.Fp, l.lgfb, o.llr_step, ws + l.llr_i, ws + l.L,
+                                                  fmap, fcnt);
     }
     QKD_LAUNCHED("prep_llr");
     {
         prof::Scope ps(prof::kPrep, st);
         dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)std::min<int64_t>(l.W, 65535));
-        prep_synd<<<grd, 256, 0, st>>>(synd, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits));
+        prep_synd<<<grd, 256, 0, st>>>(synd, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits), fmap, fcnt);
     }
     QKD_LAUNCHED("prep_synd");
     const size_t ms = prec == kF32 ? 4 : (prec == kF16 ? 2 : 1);
-    QKD_CUDA(cudaMemsetAsync(ws + l.msg, 0, (size_t)d.E * l.Fp * ms, st));
+    if (compact) {
+        prof::Scope ps(prof::kPrep, st);
+        zero_placed_msgs<<<(unsigned)sm_count() * 8, 256, 0, st>>>(reinterpret_cast<uint4 *>(ws + l.msg),
+                                                                    (int64_t)d.E * ms << l.lgfb, l.lgfb, fcnt);
+        QKD_LAUNCHED("zero_placed_msgs");
+    } else {
+        QKD_CUDA(cudaMemsetAsync(ws + l.msg, 0, (size_t)d.E * l.Fp * ms, st));
+    }
     prof::Scope ps(prof::kPrep, st);
     return rebuild_blocks(l, ws, st);
 }
@@ -1103,20 +1169,25 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
 // Shared tail: iteration counts / converged flags, then bits and posteriors
 // back to the frame-major output layout.
 static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const qkdrec_decode_opts &o,
-                            const uint8_t *conv_prev, char *ws, const Layout &l, const Prepared &pr,
+                            const uint8_t *conv_prev, bool compact, char *ws, const Layout &l, const Prepared &pr,
                             const DecArgs &a, int final_buf, uint8_t *bits_out, int32_t *iters_out,
                             uint8_t *conv_out, float *post_out, cudaStream_t st) {
+    const int32_t *fmap = compact ? reinterpret_cast<const int32_t *>(ws + l.fmap) : nullptr;
+    const int32_t *fcnt = compact ? reinterpret_cast<const int32_t *>(ws + l.fcnt) : nullptr;
     {
         prof::Scope ps(prof::kFinish, st);
         finalize<<<(unsigned)ceil_div(F, 256), 256, 0, st>>>(F, T, conv_prev ? 1 : 0, pr.mask, a.active,
-                                                             a.iters_i, pr.unsat[final_buf], iters_out, conv_out);
+                                                             a.iters_i, pr.unsat[final_buf], iters_out, conv_out,
+                                                             fmap);
     }
     QKD_LAUNCHED("finalize");
     prof::Scope ps(prof::kFinish, st);
     dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
     if (prec == kI8)
-        write_out<kI8><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out, post_out);
-    else write_out<kF32><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out, post_out);
+        write_out<kI8><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out, post_out,
+                                            fmap, fcnt);
+    else write_out<kF32><<<grd, blk, 0, st>>>(ws + l.L, F, d.n, l.Fp, l.lgfb, o.llr_step, pr.mask, bits_out,
+                                              post_out, fmap, fcnt);
     QKD_LAUNCHED("write_out");
     return QKDREC_OK;
 }
@@ -1165,13 +1236,13 @@ static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaSt
 
 // One flooding decode pass over the frames selected by conv_prev (NULL = all).
 static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
-                               const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev,
+                               const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, bool compact,
                                uint8_t *bits_out, int32_t *iters_out, uint8_t *conv_out,
                                float *post_out, char *ws, cudaStream_t st) {
     const Layout l = make_layout(d, F, o.algo, prec);
     DecArgs a;
     Prepared pr;
-    qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, ws, l, st, a, pr);
+    qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, compact, ws, l, st, a, pr);
     if (s != QKDREC_OK) return s;
     const int64_t vitems = (int64_t)d.n * l.FV;
     const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(vitems, 256), (int64_t)sm_count() * 64);
@@ -1218,7 +1289,7 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
     a.early_stop = 1;
     check(T + 1, 0);
     QKD_LAUNCHED("check_flood(parity)");
-    return finish(d, F, T, prec, o, conv_prev, ws, l, pr, a, (T + 1) & 1, bits_out, iters_out, conv_out,
+    return finish(d, F, T, prec, o, conv_prev, compact, ws, l, pr, a, (T + 1) & 1, bits_out, iters_out, conv_out,
                   post_out, st);
 }
 
@@ -1289,17 +1360,20 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
     cudaStream_t st = as_stream(stream);
     char *ws = reinterpret_cast<char *>(workspace);
     qkdrec_status s;
-    auto pass = [&](const qkdrec_decode_opts &po, int prec, const uint8_t *conv_prev) {
+    auto pass = [&](const qkdrec_decode_opts &po, int prec, const uint8_t *conv_prev, bool compact) {
         if (po.algo == QKDREC_OMS_LAYERED)
-            return run_layered(d, llr, synd, F, po, prec, conv_prev, bits_out, iters_out, conv_out, post_out, ws, st);
-        return run_flood(d, llr, synd, F, po, prec, conv_prev, bits_out, iters_out, conv_out, post_out, ws, st);
+            return run_layered(d, llr, synd, F, po, prec, conv_prev, compact, bits_out, iters_out, conv_out,
+                               post_out, ws, st);
+        return run_flood(d, llr, synd, F, po, prec, conv_prev, compact, bits_out, iters_out, conv_out, post_out,
+                         ws, st);
     };
-    if ((s = pass(o, o.prec, nullptr)) != QKDREC_OK) return s;
-    // FP32 re-decode of the frames a low-precision pass left unsatisfied
+    if ((s = pass(o, o.prec, nullptr, false)) != QKDREC_OK) return s;
+    // FP32 re-decode of the frames a low-precision pass left unsatisfied,
+    // compacted to the front so that it costs what the failed frames need
     if (o.fallback_f32 && o.prec != QKDREC_F32) {
         qkdrec_decode_opts o2 = o;
         if (o.fallback_f32 == 2) o2.algo = QKDREC_SP_FLOOD;
-        if ((s = pass(o2, QKDREC_F32, conv_out)) != QKDREC_OK) return s;
+        if ((s = pass(o2, QKDREC_F32, conv_out, true)) != QKDREC_OK) return s;
     }
     return QKDREC_OK;
 }

@@ -314,13 +314,13 @@ static qkdrec_status launch_layer_qc(DecArgs a, const CodeDev &d, int32_t row, c
 }
 
 qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
-                          const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev,
+                          const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, bool compact,
                           uint8_t *bits_out, int32_t *iters_out, uint8_t *conv_out, float *post_out,
                           char *ws, cudaStream_t st) {
     const Layout l = make_layout(d, F, o.algo, prec);
     DecArgs a;
     Prepared pr;
-    qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, ws, l, st, a, pr);
+    qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, compact, ws, l, st, a, pr);
     if (s != QKDREC_OK) return s;
     const std::vector<int32_t> &lptr = d.h_layer_ptr;
     const int T = o.max_iter;
@@ -374,6 +374,6 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *syn
     // final stopping test on the last posteriors: parity buffer (T+1)&1 is clear
     parity(T + 1);
     QKD_LAUNCHED("parity");
-    return finish(d, F, T, prec, o, conv_prev, ws, l, pr, a, (T + 1) & 1, bits_out, iters_out, conv_out,
+    return finish(d, F, T, prec, o, conv_prev, compact, ws, l, pr, a, (T + 1) & 1, bits_out, iters_out, conv_out,
                   post_out, st);
 }

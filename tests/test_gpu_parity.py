@@ -284,6 +284,40 @@ def test_sum_product_redecode_of_failed_frames(algo, prec):
     assert not np.any(host(sp["converged"]).astype(bool) & ~host(fb["converged"]).astype(bool))
 
 
+@pytest.mark.parametrize("algo,prec,fallback", [("oms_flood", "i8", "sp"), ("oms_flood", "f16", True),
+                                                ("oms_layered", "i8", True)])
+def test_redecode_compaction_many_failures_across_blocks(algo, prec, fallback):
+    """The re-decode packs the failed frames to the front; with failures spread
+    over many frame blocks and a ragged frame count, every re-decoded frame
+    (bits, flags, iterations, posteriors) equals a plain FP32 decode of it, and
+    every other frame keeps the first pass's outputs."""
+    n, F = 1024, 301
+    rp, ci, _ = code(160, n, 0.5)
+    # half the frames easy, half hard, mixed at random over the frame blocks
+    b1, llr1 = bpsk_frames(161, F, n, 0.7)
+    b2, llr2 = bpsk_frames(162, F, n, 1.0)
+    hard = synth.philox(163).random(F) < 0.5
+    b = np.where(hard[:, None], b2, b1)
+    llr = np.where(hard[:, None], llr2, llr1)
+    c = q.Code(n, rp, ci)
+    s = q.qkdrec_syndrome(c, dev(b))
+    lowp = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo=algo, prec=prec, max_iter=12), want_post=True)
+    o2 = "sp_flood" if fallback == "sp" else algo
+    ref = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo=o2, prec="f32", max_iter=12), want_post=True)
+    fb = q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo=algo, prec=prec, max_iter=12, fallback_f32=fallback),
+                               want_post=True)
+    lc = host(lowp["converged"]).astype(bool)
+    redo = ~lc
+    blocks = np.unique(np.flatnonzero(redo) // 32)
+    assert redo.sum() > 40 and blocks.size > 4 and lc.any()
+    for k in ("bits", "post", "iters", "converged"):
+        assert np.array_equal(host(fb[k])[lc], host(lowp[k])[lc]), k
+    assert np.array_equal(host(fb["bits"])[redo], host(ref["bits"])[redo])
+    assert np.array_equal(host(fb["post"])[redo], host(ref["post"])[redo])
+    assert np.array_equal(host(fb["converged"])[redo], host(ref["converged"])[redo])
+    assert np.array_equal(host(fb["iters"])[redo], host(lowp["iters"])[redo] + host(ref["iters"])[redo])
+
+
 # ------------------------------------------------------------------ full pipeline
 def test_config1_pipeline_vs_oracle():
     """x, y at SNR 3, 16 frames x 4096, 4 Gray slices, codes at 0.95 x capacity, SP flooding,
