@@ -799,6 +799,85 @@ __global__ void __launch_bounds__(256) var_flood_i8x16(DecArgs a) {
     prof_add(a.prof, units, bytes);
 }
 
+// FP16-message flooding, variable side, 8 frames per thread: thread (listed
+// frame block on y, (variable, group of 8 frames) on x).  The same sums, in
+// the same (ascending edge) order, as var_flood<kF16>.
+__global__ void __launch_bounds__(256) var_flood_f16x8(DecArgs a) {
+    constexpr int LG = lgfb_of<4>();                   // 128-frame blocks: 16 groups of 8
+    const int64_t items = (int64_t)a.n * 16;
+    float *L = reinterpret_cast<float *>(a.L);
+    const float *llr = reinterpret_cast<const float *>(a.llr_i);
+    const __half *msg = reinterpret_cast<const __half *>(a.msg);
+    unsigned long long units = 0, bytes = 0;
+    const int32_t nblk = *a.blk_n;
+    for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
+        const int64_t fb = __ldg(a.blk + bi);
+        for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
+             idx += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t v = idx >> 4, f0 = (fb << LG) + ((idx & 15) << 3);
+            const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);
+            if (v == 0 && (f0 & 31) == 0 && a.early_stop) a.unsat_next[f0 >> 5] = 0;   // next test starts clear
+            const uint2 aw = *reinterpret_cast<const uint2 *>(a.active + f0);
+            const uint32_t act = active_bits<4>(reinterpret_cast<const uint8_t *>(&aw.x)) |
+                                 (active_bits<4>(reinterpret_cast<const uint8_t *>(&aw.y)) << 4);
+            if (!act) continue;
+            const uint32_t u = a.early_stop ? (__ldcg(a.unsat_cur + (f0 >> 5)) >> (f0 & 31)) & 0xffu : 0xffu;
+            const uint32_t done = a.early_stop ? (act & ~u) : 0u;
+            const uint32_t upd = act & ~done;
+            if (v == 0)
+                for (uint32_t r = done; r; r &= r - 1) {
+                    const int i = __ffs(r) - 1;
+                    a.active[f0 + i] = 0;
+                    a.iters_i[f0 + i] = a.t - 1;
+                }
+            if (!upd) continue;
+            const int32_t vb = __ldg(a.vptr + v), ve = __ldg(a.vptr + v + 1);
+            const int64_t pv = bL + (v << LG);
+            const unsigned nu = __popc(upd);
+            units += nu;
+            bytes += (unsigned long long)nu * ((ve - vb) * 2 + 4 + 4);
+            float acc[8];
+            {
+                const float4 c0 = __ldg(reinterpret_cast<const float4 *>(llr + pv));
+                const float4 c1 = __ldg(reinterpret_cast<const float4 *>(llr + pv) + 1);
+                acc[0] = c0.x; acc[1] = c0.y; acc[2] = c0.z; acc[3] = c0.w;
+                acc[4] = c1.x; acc[5] = c1.y; acc[6] = c1.z; acc[7] = c1.w;
+            }
+            // edges in chunks of four: index loads, then message loads, issued together
+            for (int32_t k0 = vb; k0 < ve; k0 += 4) {
+                int32_t e[4];
+                uint4 m[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) e[j] = __ldg(a.vedge + min(k0 + j, ve - 1));
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (k0 + j < ve) m[j] = __ldcs(reinterpret_cast<const uint4 *>(msg + bM + ((int64_t)e[j] << LG)));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (k0 + j >= ve) break;
+                    const uint32_t mw[4] = {m[j].x, m[j].y, m[j].z, m[j].w};
+                    for (int w = 0; w < 4; ++w) {
+                        const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&mw[w]));
+                        acc[2 * w] += h.x;
+                        acc[2 * w + 1] += h.y;
+                    }
+                }
+            }
+            float4 *dst = reinterpret_cast<float4 *>(L + pv);
+            if (upd != 0xffu) {
+                // frames not updated keep their posterior
+                const float4 o0 = dst[0], o1 = dst[1];
+                const float old[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+                for (int i = 0; i < 8; ++i)
+                    if (!((upd >> i) & 1u)) acc[i] = old[i];
+            }
+            dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+        }
+    }
+    prof_add(a.prof, units, bytes);
+}
+
 // ------------------------------------------------------- layout conversions
 // Frame placement of a decode pass: position f holds frame f, or, in a
 // compacted re-decode, frame fmap[f] for f < *fcnt (the frames a first pass
@@ -1246,9 +1325,11 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
     if (s != QKDREC_OK) return s;
     const int64_t vitems = (int64_t)d.n * l.FV;
     const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(vitems, 256), (int64_t)sm_count() * 64);
-    // integer form: (variable, 16 frames) on x, listed frame blocks on y
+    // integer form: (variable, 16 frames) on x, listed frame blocks on y; FP16
+    // messages: (variable, 8 frames)
     const bool i16 = prec == kI8 && l.lgfb == lgfb_of<4>() && d.dv_max <= 1000;
-    dim3 igrid((unsigned)std::min<int64_t>(ceil_div((int64_t)d.n * 8, 256), (int64_t)sm_count() * 64), 1);
+    const bool h8 = prec == kF16 && l.lgfb == lgfb_of<4>();
+    dim3 igrid((unsigned)std::min<int64_t>(ceil_div((int64_t)d.n * (h8 ? 16 : 8), 256), (int64_t)sm_count() * 64), 1);
     igrid.y = (unsigned)std::max<int64_t>(1, std::min<int64_t>(l.Fp >> l.lgfb, (int64_t)sm_count() * 64 / igrid.x));
 
     auto check = [&](int t, int do_msgs) {
@@ -1273,6 +1354,7 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t
             a.prof = prof::counters(kind);
             prof::Scope ps(kind, st);
             if (i16) var_flood_i8x16<<<igrid, 256, 0, st>>>(a);
+            else if (h8) var_flood_f16x8<<<igrid, 256, 0, st>>>(a);
             else if (prec == kI8) var_flood<kI8><<<vgrid, 256, 0, st>>>(a);
             else if (prec == kF16) var_flood<kF16><<<vgrid, 256, 0, st>>>(a);
             else var_flood<kF32><<<vgrid, 256, 0, st>>>(a);

@@ -239,6 +239,29 @@ def test_f16_messages_fer_matches_f32(algo):
     assert lo <= res["f16"] / F <= hi + 0.05
 
 
+@pytest.mark.parametrize("early_stop", [False, True])
+def test_f16_message_posteriors_track_f32(early_stop):
+    """FP16 message storage changes each message by at most 2^-11 of itself, and
+    offset min-sum passes such changes on without growth: after two flooding
+    iterations the FP16-message posteriors stay within 1e-2 (relative) of the
+    FP32 ones and make the same hard decisions wherever |L| > 0.1 (a frame or
+    variable mixed up anywhere would be off by O(1))."""
+    n, F = 1024, 200                      # two 128-frame blocks, the second partial
+    rp, ci, _ = code(170, n, 0.5)
+    b, llr = bpsk_frames(171, F, n, 0.8)
+    c = q.Code(n, rp, ci)
+    s = q.qkdrec_syndrome(c, dev(b))
+    out = {p: q.qkdrec_decode_batch(c, dev(llr), s, q.DecodeOpts(algo="oms_flood", prec=p, max_iter=2,
+                                                                   early_stop=early_stop), want_post=True)
+           for p in ("f16", "f32")}
+    p16, p32 = host(out["f16"]["post"]), host(out["f32"]["post"])
+    same = host(out["f16"]["iters"]) == host(out["f32"]["iters"])
+    assert same.sum() > F // 2
+    assert np.all(np.abs(p16[same] - p32[same]) <= 1e-2 * np.maximum(np.abs(p32[same]), 1.0))
+    sure = same[:, None] & (np.abs(p32) > 0.1)
+    assert np.array_equal(host(out["f16"]["bits"])[sure], host(out["f32"]["bits"])[sure])
+
+
 @pytest.mark.parametrize("prec", ["i8", "f16"])
 def test_fp32_redecode_of_failed_frames(prec):
     n, F = 2048, 64
