@@ -508,7 +508,7 @@ check_flood_i(DecArgs a) {
 // The same offset min-sum check update as check_flood_i<4, 32>, bit for bit,
 // with a lane's four frames held as two pairs of 16-bit lanes (s16x2: frames
 // 0-1 and 2-3), so that one min/max/add serves two frames.  Identities used
-// (every lane value is small: |L| <= 31 (dv + 1), |m|, |q| <= 31):
+// (|L| <= 31 (dv + 1) and |m| <= 31, so L - m fits a 16-bit lane):
 //   t = ~L + m = -q - 1 per lane, so q = ~t, -q = t + 1, sign(q) = NOT sign(t);
 //   the second minimum is needed exactly where |q_k| equals the minimum (if
 //   another edge shares the minimum, the second minimum equals it), so no
