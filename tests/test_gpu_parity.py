@@ -341,6 +341,39 @@ def test_redecode_compaction_many_failures_across_blocks(algo, prec, fallback):
     assert np.array_equal(host(fb["iters"])[redo], host(lowp["iters"])[redo] + host(ref["iters"])[redo])
 
 
+@pytest.mark.parametrize("algo,prec", [("sp_flood", "f32"), ("oms_flood", "i8"), ("oms_layered", "f32")])
+def test_corrupted_syndromes_are_detected(algo, prec):
+    """Failure detection without a device fault: one syndrome bit flipped on the
+    host in half the frames (a message corrupted in transit).  The decode ends
+    with every frame accounted for: intact frames decode Bob's word; a corrupted
+    frame either reports no convergence after all its iterations (its word may
+    still be Bob's: the flag carries the failure), or converges to a word that
+    satisfies the corrupted syndrome, which cannot be Bob's -- so the flag and
+    the comparison with Bob's bits (the protocol's check) together flag every
+    corrupted frame."""
+    n, F, T = 1024, 64, 30
+    rp, ci, M = code(180, n, 0.5)
+    b, llr = bpsk_frames(181, F, n, 0.6)
+    synd = oracle.syndrome(rp, ci, b)
+    g = synth.philox(182)
+    bad = g.random(F) < 0.5
+    flip = g.integers(0, M, size=F)
+    s2 = synd.copy()
+    s2[bad, flip[bad]] ^= 1
+    c = q.Code(n, rp, ci)
+    out = q.qkdrec_decode_batch(c, dev(llr), dev(s2), q.DecodeOpts(algo=algo, prec=prec, max_iter=T))
+    bits, conv, iters = host(out["bits"]), host(out["converged"]).astype(bool), host(out["iters"])
+    good = ~bad
+    assert bad.sum() > 10 and good.sum() > 10
+    assert np.array_equal(bits[good], b[good]) and conv[good].all()
+    wrong = (bits != b).any(axis=1)
+    assert np.all(~conv[bad] | wrong[bad])
+    assert not np.any(conv[bad] & ~wrong[bad])
+    assert np.all(iters[bad & ~conv] == T)
+    got = oracle.syndrome(rp, ci, bits)
+    assert np.array_equal(got[conv], s2[conv])
+
+
 # ------------------------------------------------------------------ full pipeline
 def test_config1_pipeline_vs_oracle():
     """x, y at SNR 3, 16 frames x 4096, 4 Gray slices, codes at 0.95 x capacity, SP flooding,
