@@ -592,6 +592,42 @@ WOMS_WORKLOAD = ("weighted offset min-sum training: 1024 frames of n=16384, slic
                  "checkpoints every 5, BCE loss, Adam; one step = forward + adjoint + update")
 
 
+def _oracle_woms_task(task):
+    """Loss and FP64 reverse-mode gradient of the unrolled weighted min-sum for a
+    few frames by the oracle; returns the wall time."""
+    import oracle
+    rp, ci, llr, synd, tgt, a, b = task
+    t0 = time.perf_counter()
+    oracle.woms(rp, ci, llr, synd, tgt, a, b)
+    return time.perf_counter() - t0
+
+
+def oracle_woms_sample(step, cores, per_proc=12):
+    """A bounded sample of one training step: `per_proc` frames per host process
+    (frames step*k .. of the training batch, k = processes x per_proc), inputs
+    from the oracle's own quantiser, slice LLRs and syndromes; weights at their
+    initial values.  Returns (frames, wall seconds, processes)."""
+    import oracle
+    procs = max(1, min(cores, 8))
+    k = procs * per_proc
+    f0 = (step * k) % WOMS_F
+    rp, ci, _ = synth.make_regular_code(5000, WOMS_N, synth.checks_for_rate(WOMS_N, 0.5))
+    x, y = synth.gaussian_pair(5, (f0 + k) * WOMS_N, WOMS_SNR)
+    x, y = x[f0 * WOMS_N:], y[f0 * WOMS_N:]
+    lo, hi = oracle.quantiser_range(WOMS_SNR)
+    _, bits = oracle.quantise(y, M_SLICES, lo, hi)
+    j = WOMS_SLICE
+    llr = oracle.slice_llr(x.astype(np.float64), bits[:j], j, M_SLICES, lo, hi, WOMS_SNR ** -0.5).reshape(k, WOMS_N)
+    tgt = bits[j].reshape(k, WOMS_N)
+    synd = oracle.syndrome(rp, ci, tgt)
+    a, b = np.ones((WOMS_T, 2)), np.full((WOMS_T, 2), 0.5)
+    tasks = [(rp, ci, llr[i:i + per_proc], synd[i:i + per_proc], tgt[i:i + per_proc], a, b)
+             for i in range(0, k, per_proc)]
+    t0 = time.perf_counter()
+    _pool_map(_oracle_woms_task, tasks, procs)
+    return k, time.perf_counter() - t0, procs
+
+
 def woms_frames(q, torch, code, seed, dev):
     """Slice LLRs (Bob's lower slices reconciled), Bob's slice bits and syndromes."""
     x, y = synth.gaussian_pair(seed, WOMS_F * WOMS_N, WOMS_SNR)
@@ -605,6 +641,15 @@ def woms_frames(q, torch, code, seed, dev):
 
 def run_woms(args):
     rank, world, local = rank_env()
+    cores = len(os.sched_getaffinity(0))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # before CUDA is touched (spawn pool)
+        nfr, wall, procs = oracle_woms_sample(0, cores)
+        cpu = {"value": nfr / (WOMS_F * wall), "unit": "step/s", "cores": procs, "kind": "oracle",
+               "sample": f"{nfr} of the {WOMS_F} frames of one step: FP64 forward and reverse-mode gradient "
+                         f"({WOMS_T} iterations), {procs} processes; steps/s = frames / ({WOMS_F} x wall)",
+               "wall_s": wall}
     import paper_2108_08418_b300 as q
     from paper_2108_08418_b300 import build as qbuild
     from paper_2108_08418_b300.woms import woms_loss
@@ -661,6 +706,24 @@ def run_woms(args):
     for _ in range(max(0, args.train_steps - args.warmup - args.steps)):
         losses.append(float(step()))
     fer_trained = fer(alpha, beta)
+
+    # end to end: each step's frames from pinned host memory, the loss read back
+    e2e = None
+    if not args.no_e2e:
+        hl, hs, ht = llr.cpu().pin_memory(), synd.cpu().pin_memory(), target.cpu().pin_memory()
+        h2d = hl.numel() * 4 + hs.numel() + ht.numel()
+        torch.cuda.synchronize()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(args.steps):
+            llr.copy_(hl, non_blocking=True)
+            synd.copy_(hs, non_blocking=True)
+            target.copy_(ht, non_blocking=True)
+            losses.append(float(step()))
+        e3.record(stream)
+        torch.cuda.synchronize()
+        e2e = {"value": 1e3 / (e2.elapsed_time(e3) / args.steps), "unit": "step/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 4}
     if rank != 0:
         return
     line = {
@@ -673,8 +736,8 @@ def run_woms(args):
                    "loss_first": losses[0], "loss_last": losses[-1], "train_steps": len(losses),
                    "fer_eval": {"woms_initial": fer_init, "woms_trained": fer_trained, "sum_product_20it": fer_sp},
                    "l2": "messages 201 MB per copy, checkpoints 805 MB: larger than L2"},
-        "roofline": roof, "kernels": kernels, "cpu_baseline": None,
-        "e2e": None, "gpu_launches": launches * args.steps, "clocks": clocks,
+        "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+        "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -917,6 +980,9 @@ def run_reference(args):
     if args.workload == "uneven":
         run_reference_uneven(args, world, cores)
         return
+    if args.workload == "woms":
+        run_reference_woms(args, world, cores)
+        return
     per_snr = max(1, min(cores, 8) // 2)
     rate_of = load_sweep_rates() if args.rate_rule == "backoff" else None
     for w in range(args.warmup):
@@ -937,6 +1003,29 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "bit/s", "cores": min(cores, nfr), "kind": "oracle",
                          "sample": f"{nfr} sub-blocks of n=4096 per step, each reconciled over all 5 slices"},
         "e2e": {"value": value, "unit": "bit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_woms(args, world, cores):
+    for w in range(args.warmup):
+        oracle_woms_sample(w, cores)
+    frames, walls, procs = 0, 0.0, 1
+    for s in range(args.steps):
+        k, wall, procs = oracle_woms_sample(args.warmup + s, cores)
+        frames += k
+        walls += wall
+    value = frames / (WOMS_F * walls)
+    line = {
+        "impl": "reference", "metric": "weighted min-sum training steps/s", "value": value, "unit": "step/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded Philox Gaussian quadratures and a seeded regular (3,6) LDPC code",
+        "config": {"workload": WOMS_WORKLOAD, "sample": f"per step: {frames // max(args.steps, 1)} of the {WOMS_F} "
+                                                        f"frames, forward and gradient (no optimiser update)"},
+        "cpu_baseline": {"value": value, "unit": "step/s", "cores": procs, "kind": "oracle",
+                         "sample": f"{frames // max(args.steps, 1)} frames per step, {procs} processes"},
+        "e2e": {"value": value, "unit": "step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
