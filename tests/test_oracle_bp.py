@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 import synth
+from _workloads import bpsk_frames
 
 
 def random_tree_code(rng, n_target, max_dc=4):
@@ -212,3 +213,18 @@ def test_layer_partition_valid_and_first_fit():
 def test_syndrome_vs_dense_product():
     rp, ci, b, s, _, H = _random_frames(10)
     assert np.array_equal(oracle.syndrome(rp, ci, b), s)
+
+
+def test_sum_product_threshold_of_the_regular_3_6_ensemble():
+    """Density evolution puts the BP threshold of the regular (3,6) ensemble on the
+    binary-input AWGN channel at sigma* = 0.881 (a textbook value of the theory of
+    iterative decoding).  A length-8192 code of the seeded construction decodes
+    every frame 5 % below it and none 5 % above it within 100 iterations; a
+    dropped exclusion term, a sign error or a wrong phi moves that transition."""
+    n = 8192
+    rp, ci, _ = synth.make_regular_code(190, n, synth.checks_for_rate(n, 0.5))
+    for sigma, seed, want in ((0.84, 191, 8), (0.93, 192, 0)):
+        b, llr = bpsk_frames(seed, 8, n, sigma)
+        out = oracle.decode(rp, ci, llr.astype(np.float64), oracle.syndrome(rp, ci, b), "sp_flood", max_iter=100)
+        assert int((out["bits"] == b).all(axis=1).sum()) == want, sigma
+        assert int(out["converged"].sum()) == want, sigma
