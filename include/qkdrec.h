@@ -187,7 +187,11 @@ typedef struct {
     int32_t early_stop;    /* 1: stop each frame at the first satisfied syndrome */
     int32_t fallback_f32;  /* frames a low-precision decode leaves unsatisfied are decoded
                               again in FP32: 0 never, 1 with the same algorithm,
-                              2 with FP32 sum-product flooding (the plain form) */
+                              2 with FP32 sum-product flooding (the plain form).  The
+                              failed frames are packed together on the device first, so
+                              the second pass costs what they need; each gets exactly the
+                              outputs a plain FP32 decode would give it (iterations of
+                              both passes added), the other frames keep the first pass's */
 } qkdrec_decode_opts;
 
 /* Defaults: SP flooding, FP32, 50 iterations, offset 0.5, step 0.5, early stop on, no fallback. */
