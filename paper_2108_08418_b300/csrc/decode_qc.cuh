@@ -164,7 +164,6 @@ layer_qc_tma(DecArgs a, const __grid_constant__ CUtensorMap tmL, const __grid_co
             if (!act) continue;
             const int z = z0 + zz;
             const int32_t c = row * Z + z;
-            const int64_t e0 = (int64_t)c * nb;
             uint32_t neg = (__ldg(a.sbits + (int64_t)c * a.W + (f >> 5)) >> (f & 31)) & 1u;
             float mn1 = INFINITY, mn2 = INFINITY;
             int arg = -1;
