@@ -66,10 +66,11 @@ def rank_env():
 
 # ------------------------------------------------------------------ set-up
 def slice_rates(snr, capacity_fn):
-    lo, hi = (-4.0 * np.sqrt(1 + 1 / snr), 4.0 * np.sqrt(1 + 1 / snr))
+    """Capacities and 0.95 x capacity rates of the sweep's slices (library calls)."""
+    import paper_2108_08418_b300 as q
+    lo, hi = q.qkdrec_quantiser_range(snr)
     caps = [capacity_fn(snr, M_SLICES, j, lo, hi) for j in range(M_SLICES)]
-    k = [min(int(np.floor(0.95 * c * 64 + 0.5)), 63) for c in caps]
-    return caps, [max(v, 0) / 64 for v in k]
+    return caps, [q.qkdrec_code_rate(c) for c in caps]
 
 
 def _make_code(args):
@@ -189,7 +190,8 @@ def oracle_sample(step, budget_frames, cores, rate_of=None):
     tasks = []
     for snr in SNRS:
         if rate_of is None:
-            _, rates = slice_rates(snr, lambda s, m, j, lo, hi: oracle.slice_capacity(s, m, j))
+            # the oracle's own capacities and rate rule (no library call on this leg)
+            rates = [oracle.code_rate(oracle.slice_capacity(snr, M_SLICES, j)) for j in range(M_SLICES)]
         else:
             rates = [rate_of[(snr, 12, j)] for j in range(M_SLICES)]
         codes = {}
@@ -237,8 +239,10 @@ def _capacity_row(snr):
 
 
 def uneven_start_rate(capacity):
-    """First rate the back-off tries: 0.95 x capacity on the 1/64 grid, at most 60/64."""
-    return min(int(np.floor(0.95 * capacity * 64 + 0.5)), 60) / 64
+    """First rate the back-off tries: 0.95 x capacity on the 1/64 grid (the library's
+    rate rule), at most 60/64."""
+    import paper_2108_08418_b300 as q
+    return min(q.qkdrec_code_rate(capacity), 60 / 64)
 
 
 def uneven_bin(snr):

@@ -96,6 +96,42 @@ void qkdrec_code_destroy(qkdrec_code_t code);
 qkdrec_status qkdrec_code_info(qkdrec_code_t code, int32_t *n, int32_t *m_checks,
                                int64_t *edges, int32_t *n_layers, int32_t *dc_max);
 
+/*
+ * Build the seeded parity-check matrix of one slice code (Sec. II Step 5: Bob
+ * and Alice agree on H_j; Sec. III-A: one H_j shared by all sub-blocks of the
+ * slice).  The paper's code database (Sec. V-B) is not public; this is the
+ * random left-regular family that stands in for it:
+ *   - n variables of degree dv, m_checks checks; with E = dv n, the first
+ *     E - m_checks floor(E / m_checks) checks have degree floor(E / m_checks) + 1,
+ *     the others floor(E / m_checks);
+ *   - the E variable sockets (socket s belongs to variable s / dv) are placed on
+ *     the check sockets in edge order by a uniformly random permutation drawn
+ *     from Philox-4x64-10 keyed by (seed, 0) (Fisher-Yates from the last
+ *     position, masked-rejection draws; numpy's Generator(Philox(seed)) draws
+ *     the same permutation);
+ *   - edges on 4-cycles or double edges are swapped with uniformly drawn other
+ *     edges (splitmix64 stream of the seed; at most 100 passes; degrees are
+ *     kept), then any repeated (check, variable) pair left in dense codes is
+ *     swapped away alone, so H never holds a pair twice.
+ *   row_ptr   out: HOST int32 [m_checks + 1], allocated by the library;
+ *   col_idx   out: HOST int32 [dv n], allocated by the library, check-major edge
+ *             order (the layout qkdrec_code_create takes);
+ *             release both with qkdrec_free.
+ *   cycles4_left  out (may be NULL): 4-cycle / double-edge detections left
+ *             after the passes (0 = girth >= 6; dense high-rate codes may keep
+ *             some), saturated at INT32_MAX.
+ * Synchronous, host only (no device work).  Deterministic in (seed, n,
+ * m_checks, dv).
+ * Errors: QKDREC_ERR_ARG (NULL outputs, n, dv or m_checks <= 0, m_checks > dv n,
+ *         dv n >= 2^31, a check degree above n), QKDREC_ERR_NOMEM.
+ */
+qkdrec_status qkdrec_make_regular_code(uint64_t seed, int32_t n, int32_t m_checks, int32_t dv,
+                                       int32_t **row_ptr, int32_t **col_idx, int32_t *cycles4_left);
+
+/* Release an array the library allocated for the caller (qkdrec_make_regular_code).
+ * NULL is ignored. */
+void qkdrec_free(void *p);
+
 /* HOST int32 [M]: the layer of every check (the partition the layered decoder uses). */
 qkdrec_status qkdrec_code_layers(qkdrec_code_t code, int32_t *layer_of_check);
 
@@ -444,6 +480,28 @@ qkdrec_status qkdrec_profile_end(qkdrec_kernel_stat *stats, int32_t capacity, in
  */
 qkdrec_status qkdrec_slice_capacity(double snr, int32_t m_slices, int32_t j, double lo, double hi,
                                     qkdrec_label label, double va, double *capacity);
+
+/*
+ * Rate rule of a slice code (Sec. II Step 5: the code rate is chosen close to
+ * the slice's capacity; the workloads take a fraction of it):
+ *   rate = k / denom, k = floor(fraction * capacity * denom + 1/2) clamped to
+ *   [0, denom - 1] (nearest multiple of 1/denom, ties up; at most
+ *   (denom - 1)/denom).  rate = 0 means the slice is disclosed, not decoded.
+ * Errors: QKDREC_ERR_ARG (NULL, non-finite capacity or fraction, fraction < 0,
+ *         denom outside [2, 2^20]).  HOST.
+ */
+qkdrec_status qkdrec_code_rate(double capacity, double fraction, int32_t denom, double *rate);
+
+/* Checks of a rate-r code of length n: m = n (1 - rate) rounded to the nearest
+ * integer (ties to even).  Errors: QKDREC_ERR_ARG (n <= 0, rate outside [0, 1),
+ * m outside [1, n]).  HOST. */
+qkdrec_status qkdrec_checks_for_rate(int32_t n, double rate, int32_t *m_checks);
+
+/* Quantiser range of the workloads: [lo, hi] = [-4 sigma_y, 4 sigma_y] with the
+ * model value sigma_y^2 = va + 1/snr of y = x + n (the paper's quantiser has a
+ * constant step whose size depends on the SNR, Sec. III-B).  Errors:
+ * QKDREC_ERR_ARG (NULL, snr or va not positive and finite).  HOST. */
+qkdrec_status qkdrec_quantiser_range(double snr, double va, double *lo, double *hi);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *qkdrec_last_error(void);

@@ -39,6 +39,8 @@ EXPORTED = [
     "qkdrec_plan_create", "qkdrec_plan_destroy", "qkdrec_plan_workspace_size", "qkdrec_plan_launch",
     "qkdrec_plan_get_tuning", "qkdrec_plan_autotune", "qkdrec_slice_llr_soft", "qkdrec_bits_to_llr",
     "qkdrec_code_set_qc", "qkdrec_qc_timeouts",
+    "qkdrec_make_regular_code", "qkdrec_free", "qkdrec_code_rate", "qkdrec_checks_for_rate",
+    "qkdrec_quantiser_range",
 ]
 SELFTEST = ["qkdrec_selftest_phi"]
 
@@ -103,6 +105,11 @@ def lib():
         "qkdrec_decode_workspace_size": (U, [P, I32, P, P]),
         "qkdrec_decode_batch": (U, [P, P, P, I32, P, P, P, P, P, P, ctypes.c_size_t, P]),
         "qkdrec_slice_capacity": (U, [D, I32, I32, D, D, U, D, P]),
+        "qkdrec_make_regular_code": (U, [U64, I32, I32, I32, P, P, P]),
+        "qkdrec_free": (None, [P]),
+        "qkdrec_code_rate": (U, [D, D, I32, P]),
+        "qkdrec_checks_for_rate": (U, [I32, D, P]),
+        "qkdrec_quantiser_range": (U, [D, D, P, P]),
         "qkdrec_decode_static_capacity": (ctypes.c_size_t, []),
         "qkdrec_decode_batch_static": (U, [P, P, P, I32, P, P, P, P, P, P]),
         "qkdrec_woms_workspace_size": (U, [P, I32, I32, I32, P]),
@@ -556,17 +563,47 @@ def qkdrec_slice_capacity(snr: float, m_slices: int, j: int, lo: float, hi: floa
     return c.value
 
 
-def quantiser_range(snr: float, va: float = 1.0):
+def qkdrec_quantiser_range(snr: float, va: float = 1.0):
     """[-4 sigma_y, 4 sigma_y], sigma_y^2 = V_A + 1/SNR: the quantiser range the workloads use."""
-    sy = float(np.sqrt(va + 1.0 / snr))
-    return -4.0 * sy, 4.0 * sy
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().qkdrec_quantiser_range(float(snr), float(va), ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
 
 
-def code_rate(capacity: float, fraction: float = 0.95, denom: int = 64) -> float:
+quantiser_range = qkdrec_quantiser_range
+
+
+def qkdrec_code_rate(capacity: float, fraction: float = 0.95, denom: int = 64) -> float:
     """Rate rule: fraction * capacity rounded to the nearest 1/denom (ties up), at most
     (denom-1)/denom; 0.0 means the slice is disclosed."""
-    k = int(np.floor(fraction * capacity * denom + 0.5))
-    return max(min(k, denom - 1), 0) / denom
+    r = ctypes.c_double()
+    _check(lib().qkdrec_code_rate(float(capacity), float(fraction), int(denom), ctypes.byref(r)))
+    return r.value
+
+
+code_rate = qkdrec_code_rate
+
+
+def qkdrec_checks_for_rate(n: int, rate: float) -> int:
+    """Number of checks M = n (1 - rate) of a rate-r code of length n."""
+    m = ctypes.c_int32()
+    _check(lib().qkdrec_checks_for_rate(int(n), float(rate), ctypes.byref(m)))
+    return m.value
+
+
+def qkdrec_make_regular_code(seed: int, n: int, m_checks: int, dv: int = 3):
+    """Seeded left-regular parity-check matrix from the library: (row_ptr int32 [M+1],
+    col_idx int32 [dv n], residual 4-cycle detections)."""
+    rp, ci, left = ctypes.POINTER(ctypes.c_int32)(), ctypes.POINTER(ctypes.c_int32)(), ctypes.c_int32()
+    _check(lib().qkdrec_make_regular_code(ctypes.c_uint64(int(seed) & (2**64 - 1)), int(n), int(m_checks),
+                                          int(dv), ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(left)))
+    try:
+        row_ptr = np.ctypeslib.as_array(rp, shape=(int(m_checks) + 1,)).copy()
+        col_idx = np.ctypeslib.as_array(ci, shape=(int(dv) * int(n),)).copy()
+    finally:
+        lib().qkdrec_free(ctypes.cast(rp, ctypes.c_void_p))
+        lib().qkdrec_free(ctypes.cast(ci, ctypes.c_void_p))
+    return row_ptr, col_idx, left.value
 
 
 # ------------------------------------------------------------- measurement

@@ -19,8 +19,13 @@ LIB = os.path.join(LIBDIR, "libqkdrec.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
+# the seeded code construction (input generation, shared with the test inputs)
+# is compiled in so that C callers can build the slice codes themselves
+CODEGEN = os.path.join(ROOT, "synth", "_codegen.c")
+
+
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu")) + [CODEGEN]
 
 
 def _deps():

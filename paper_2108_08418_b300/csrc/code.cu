@@ -59,6 +59,10 @@ static qkdrec_status upload(T **dst, const T *src, size_t count) {
 
 using namespace qkd;
 
+// seeded left-regular construction (synth/_codegen.c, compiled into the library)
+extern "C" int64_t synth_make_regular_code(uint64_t seed, int32_t n, int32_t M, int32_t dv, int32_t max_passes,
+                                           int32_t *rp, int32_t *ci);
+
 extern "C" {
 
 const char *qkdrec_last_error(void) { return g_err; }
@@ -216,6 +220,72 @@ qkdrec_status qkdrec_code_set_qc(qkdrec_code_t code, int32_t Z, int32_t mb, int3
     d.qc_mb = mb;
     d.qc_nb = nb;
     d.qc_tma = tma_staging ? 1 : 0;
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_make_regular_code(uint64_t seed, int32_t n, int32_t m_checks, int32_t dv,
+                                       int32_t **row_ptr, int32_t **col_idx, int32_t *cycles4_left) {
+    clear_error();
+    if (!row_ptr || !col_idx) QKD_FAIL(QKDREC_ERR_ARG, "row_ptr/col_idx NULL");
+    *row_ptr = nullptr;
+    *col_idx = nullptr;
+    const int64_t E = (int64_t)dv * n;
+    if (n <= 0 || dv <= 0 || m_checks <= 0 || m_checks > E || E > INT32_MAX)
+        QKD_FAIL(QKDREC_ERR_ARG, "n=%d m_checks=%d dv=%d: need n, dv > 0 and 0 < m_checks <= dv n < 2^31", n,
+                 m_checks, dv);
+    if ((E + m_checks - 1) / m_checks > n)
+        QKD_FAIL(QKDREC_ERR_ARG, "check degree %lld above n=%d", (long long)((E + m_checks - 1) / m_checks), n);
+    int32_t *rp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m_checks + 1));
+    int32_t *ci = (int32_t *)malloc(sizeof(int32_t) * (size_t)E);
+    if (!rp || !ci) {
+        free(rp);
+        free(ci);
+        QKD_FAIL(QKDREC_ERR_NOMEM, "host allocation of %lld edges", (long long)E);
+    }
+    const int64_t res = synth_make_regular_code(seed, n, m_checks, dv, 100, rp, ci);
+    if (res < 0) {
+        free(rp);
+        free(ci);
+        QKD_FAIL(QKDREC_ERR_NOMEM, "code construction ran out of host memory");
+    }
+    *row_ptr = rp;
+    *col_idx = ci;
+    if (cycles4_left) *cycles4_left = res > INT32_MAX ? INT32_MAX : (int32_t)res;
+    return QKDREC_OK;
+}
+
+void qkdrec_free(void *p) { free(p); }
+
+qkdrec_status qkdrec_code_rate(double capacity, double fraction, int32_t denom, double *rate) {
+    clear_error();
+    if (!rate) QKD_FAIL(QKDREC_ERR_ARG, "rate is NULL");
+    if (!isfinite(capacity) || !isfinite(fraction) || fraction < 0.0 || denom < 2 || denom > (1 << 20))
+        QKD_FAIL(QKDREC_ERR_ARG, "capacity=%g fraction=%g denom=%d", capacity, fraction, denom);
+    // nearest multiple of 1/denom, ties up; at most (denom - 1)/denom; 0 = disclosed
+    double k = floor(fraction * capacity * denom + 0.5);
+    k = std::min(std::max(k, 0.0), (double)(denom - 1));
+    *rate = k / denom;
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_checks_for_rate(int32_t n, double rate, int32_t *m_checks) {
+    clear_error();
+    if (!m_checks) QKD_FAIL(QKDREC_ERR_ARG, "m_checks is NULL");
+    if (n <= 0 || !(rate >= 0.0) || !(rate < 1.0)) QKD_FAIL(QKDREC_ERR_ARG, "n=%d rate=%g", n, rate);
+    const double m = nearbyint((double)n * (1.0 - rate));   // nearest, ties to even
+    if (m < 1.0 || m > n) QKD_FAIL(QKDREC_ERR_ARG, "rate %g gives %g checks for n=%d", rate, m, n);
+    *m_checks = (int32_t)m;
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_quantiser_range(double snr, double va, double *lo, double *hi) {
+    clear_error();
+    if (!lo || !hi) QKD_FAIL(QKDREC_ERR_ARG, "lo/hi NULL");
+    if (!(snr > 0.0) || !(va > 0.0) || !isfinite(snr) || !isfinite(va))
+        QKD_FAIL(QKDREC_ERR_ARG, "snr=%g va=%g must be positive", snr, va);
+    const double sy = sqrt(va + 1.0 / snr);   // model sigma_y of y = x + n
+    *lo = -4.0 * sy;
+    *hi = 4.0 * sy;
     return QKDREC_OK;
 }
 

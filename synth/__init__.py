@@ -48,6 +48,12 @@ def _lib():
         lib.synth_break_short_cycles.argtypes = [
             ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_uint64, ctypes.c_int32]
+        lib.synth_philox_permutation.restype = None
+        lib.synth_philox_permutation.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
+        lib.synth_make_regular_code.restype = ctypes.c_int64
+        lib.synth_make_regular_code.argtypes = [
+            ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+            ctypes.c_void_p, ctypes.c_void_p]
         _LIB = lib
         return lib
 
@@ -137,6 +143,26 @@ def make_regular_code(seed: int, n: int, m_checks: int, dv: int = 3, max_passes:
         ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), int(max_passes))
     if residual < 0:
         raise MemoryError("code construction")
+    return row_ptr, col_idx, int(residual)
+
+
+def philox_permutation_c(seed: int, count: int) -> np.ndarray:
+    """The C helper's Philox-4x64-10 permutation of 0..count-1 (the same draws as
+    numpy's Generator(Philox(key=seed)).permutation(count))."""
+    out = np.empty(int(count), dtype=np.int32)
+    _lib().synth_philox_permutation(ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), int(count), out.ctypes.data)
+    return out
+
+
+def make_regular_code_c(seed: int, n: int, m_checks: int, dv: int = 3, max_passes: int = 100):
+    """make_regular_code done entirely by the C helper (permutation included)."""
+    n, M = int(n), int(m_checks)
+    row_ptr = np.zeros(M + 1, dtype=np.int32)
+    col_idx = np.zeros(dv * n, dtype=np.int32)
+    residual = _lib().synth_make_regular_code(ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), n, M, int(dv),
+                                              int(max_passes), row_ptr.ctypes.data, col_idx.ctypes.data)
+    if residual < 0:
+        raise ValueError("code construction failed (sizes or memory)")
     return row_ptr, col_idx, int(residual)
 
 

@@ -17,6 +17,17 @@
  *   - repeated (check, variable) pairs still left (dense codes) are then
  *     swapped away on their own, so H is always a set of distinct pairs.
  * Swapping the variable ends of two edges keeps every node degree.
+ *
+ * The socket permutation can also be drawn here (synth_philox_permutation):
+ * Philox-4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of two 64x64
+ * -> 128-bit products with the Weyl key schedule) keyed by (seed, 0) with a
+ * counter that starts at 1, its 64-bit outputs taken in order and split into
+ * two 32-bit draws low half first; a Fisher-Yates shuffle of 0..E-1 from the
+ * last position down, position i swapped with a draw in [0, i] taken by masked
+ * rejection (the smallest all-ones mask covering i; 32-bit draws while
+ * i < 2^32).  These are the stream conventions of numpy's Philox bit generator
+ * and Generator.permutation, so the C and numpy constructions give the same
+ * matrix for the same seed (checked in the tests).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -27,6 +38,81 @@ static uint64_t splitmix64(uint64_t *s) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------------ Philox-4x64-10 */
+typedef struct {
+    uint64_t key[2], ctr[4], buf[4];
+    int pos;               /* next unread output of buf (4 = empty) */
+    int has32;             /* a high 32-bit half is waiting */
+    uint32_t half;
+} synth_philox;
+
+static void philox_block(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+    uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B97F4A7C15ULL; k1 += 0xBB67AE8584CAA73BULL; }
+        const unsigned __int128 p0 = (unsigned __int128)0xD2E7470EE14C6C93ULL * c0;
+        const unsigned __int128 p1 = (unsigned __int128)0xCA5A826395121157ULL * c2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void philox_init(synth_philox *g, uint64_t seed) {
+    memset(g, 0, sizeof(*g));
+    g->key[0] = seed;
+    g->pos = 4;
+}
+
+static uint64_t philox_next64(synth_philox *g) {
+    if (g->pos == 4) {
+        /* 256-bit counter incremented before each block */
+        for (int i = 0; i < 4; ++i)
+            if (++g->ctr[i] != 0) break;
+        philox_block(g->ctr, g->key, g->buf);
+        g->pos = 0;
+    }
+    return g->buf[g->pos++];
+}
+
+static uint32_t philox_next32(synth_philox *g) {
+    if (g->has32) { g->has32 = 0; return g->half; }
+    const uint64_t v = philox_next64(g);
+    g->has32 = 1;
+    g->half = (uint32_t)(v >> 32);
+    return (uint32_t)v;
+}
+
+/* uniform integer in [0, hi] by masked rejection */
+static uint64_t philox_interval(synth_philox *g, uint64_t hi) {
+    if (hi == 0) return 0;
+    uint64_t mask = hi;
+    for (int sh = 1; sh < 64; sh <<= 1) mask |= mask >> sh;
+    uint64_t v;
+    if (hi <= 0xFFFFFFFFULL) {
+        do { v = philox_next32(g) & mask; } while (v > hi);
+    } else {
+        do { v = philox_next64(g) & mask; } while (v > hi);
+    }
+    return v;
+}
+
+/* perm[0..E) = a uniformly random permutation of 0..E-1 drawn from `seed` */
+void synth_philox_permutation(uint64_t seed, int64_t E, int32_t *perm) {
+    synth_philox g;
+    philox_init(&g, seed);
+    for (int64_t i = 0; i < E; ++i) perm[i] = (int32_t)i;
+    for (int64_t i = E - 1; i > 0; --i) {
+        const int64_t j = (int64_t)philox_interval(&g, (uint64_t)i);
+        const int32_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    }
 }
 
 /* uniform integer in [0, bound) by rejection (no modulo bias) */
@@ -146,4 +232,26 @@ int64_t synth_break_short_cycles(int32_t n, int32_t M, const int32_t *rp, int32_
     }
     free(vptr); free(vedge); free(vfill); free(stamp); free(stamp_chk); free(bad);
     return ncyc;
+}
+
+/*
+ * The whole construction: degrees, the Philox socket permutation, then the
+ * cycle-breaking passes above.  rp [M + 1] and ci [dv n] are written.
+ * Returns the residual detection count (0 = girth >= 6), or -1 on bad sizes
+ * or allocation failure.
+ */
+int64_t synth_make_regular_code(uint64_t seed, int32_t n, int32_t M, int32_t dv, int32_t max_passes,
+                                int32_t *rp, int32_t *ci) {
+    const int64_t E = (int64_t)dv * n;
+    if (n <= 0 || dv <= 0 || M <= 0 || M > E || E > INT32_MAX) return -1;
+    const int64_t d_lo = E / M, n_hi = E - (int64_t)M * d_lo;
+    rp[0] = 0;
+    for (int32_t c = 0; c < M; ++c) rp[c + 1] = rp[c] + (int32_t)(d_lo + (c < n_hi ? 1 : 0));
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)E);
+    if (!perm) return -1;
+    synth_philox_permutation(seed, E, perm);
+    /* socket s belongs to variable s / dv */
+    for (int64_t e = 0; e < E; ++e) ci[e] = perm[e] / dv;
+    free(perm);
+    return synth_break_short_cycles(n, M, rp, ci, seed, max_passes);
 }

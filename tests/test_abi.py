@@ -88,6 +88,63 @@ def test_host_capacity_matches_oracle(L):
                 assert abs(c - ref) < 1e-9, (snr, m, j, lab)
 
 
-def test_rate_rule_matches_oracle():
+def test_rate_rule_matches_oracle(L):
     for c in np.linspace(-0.1, 1.2, 1301):
-        assert q.code_rate(c) == oracle.code_rate(c)
+        assert q.qkdrec_code_rate(c) == oracle.code_rate(c)
+    # the nearest multiple of 1/64, ties up, capped at 63/64; 0 = disclosed
+    assert q.qkdrec_code_rate(0.5 / 0.95) == 0.5
+    assert q.qkdrec_code_rate((10.5 / 64) / 0.95) == 11 / 64
+    assert q.qkdrec_code_rate(2.0) == 63 / 64 and q.qkdrec_code_rate(-1.0) == 0.0
+    assert q.qkdrec_code_rate(0.3, fraction=0.9, denom=128) == oracle.code_rate(0.3, 0.9, 128)
+    r = ctypes.c_double()
+    assert L.qkdrec_code_rate(0.5, 0.95, 1, ctypes.byref(r)) == q.ERR_ARG
+    assert L.qkdrec_code_rate(float("nan"), 0.95, 64, ctypes.byref(r)) == q.ERR_ARG
+    assert L.qkdrec_code_rate(0.5, 0.95, 64, None) == q.ERR_ARG
+
+
+def test_quantiser_range_and_check_count_match_the_workload_helpers(L):
+    for snr in (2.0, 3.0, 7.3, 15.0):
+        for va in (1.0, 2.5):
+            lo, hi = q.qkdrec_quantiser_range(snr, va)
+            rlo, rhi = oracle.quantiser_range(snr, va)
+            assert lo == rlo and hi == rhi
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    assert L.qkdrec_quantiser_range(0.0, 1.0, ctypes.byref(lo), ctypes.byref(hi)) == q.ERR_ARG
+    import synth
+    for n in (64, 4096, 1 << 20):
+        for k in range(1, 64):
+            assert q.qkdrec_checks_for_rate(n, k / 64) == synth.checks_for_rate(n, k / 64)
+    m = ctypes.c_int32()
+    assert L.qkdrec_checks_for_rate(64, 1.0, ctypes.byref(m)) == q.ERR_ARG
+
+
+@pytest.mark.parametrize("seed,n,rate,dv", [(2012, 4096, 0.75, 3), (2000 + 100 * 14 + 3, 1 << 14, 54 / 64, 3),
+                                            (11, 1024, 0.5, 4), (5000, 16384, 0.5, 3), (7, 256, 60 / 64, 3)])
+def test_make_regular_code_through_the_abi_equals_the_input_generator(L, seed, n, rate, dv):
+    """The library builds the same seeded slice code as the generator the tests and
+    the bench construct their inputs with (numpy Philox permutation + C swaps)."""
+    import synth
+    M = synth.checks_for_rate(n, rate)
+    rp, ci, left = q.qkdrec_make_regular_code(seed, n, M, dv)
+    rp_ref, ci_ref, left_ref = synth.make_regular_code(seed, n, M, dv)
+    assert np.array_equal(rp, rp_ref) and np.array_equal(ci, ci_ref) and left == left_ref
+    cols, rows = synth.degrees(rp, ci, n)
+    assert np.all(cols == dv) and rows.max() - rows.min() <= 1 and rp[-1] == dv * n
+    # a set of (check, variable) pairs: what qkdrec_code_create accepts
+    for c in range(0, M, max(1, M // 50)):
+        row = ci[rp[c]:rp[c + 1]]
+        assert len(np.unique(row)) == len(row)
+
+
+def test_make_regular_code_argument_errors(L):
+    P = ctypes.POINTER(ctypes.c_int32)
+    rp, ci, left = P(), P(), ctypes.c_int32()
+    assert L.qkdrec_make_regular_code(1, 0, 10, 3, ctypes.byref(rp), ctypes.byref(ci), None) == q.ERR_ARG
+    assert L.qkdrec_make_regular_code(1, 64, 0, 3, ctypes.byref(rp), ctypes.byref(ci), None) == q.ERR_ARG
+    assert L.qkdrec_make_regular_code(1, 64, 193, 3, ctypes.byref(rp), ctypes.byref(ci), None) == q.ERR_ARG
+    assert L.qkdrec_make_regular_code(1, 4, 1, 3, ctypes.byref(rp), ctypes.byref(ci), None) == q.ERR_ARG  # degree 12 > n
+    assert L.qkdrec_make_regular_code(1, 64, 32, 3, None, ctypes.byref(ci), None) == q.ERR_ARG
+    assert L.qkdrec_make_regular_code(1, 64, 32, 3, ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(left)) == q.OK
+    L.qkdrec_free(ctypes.cast(rp, ctypes.c_void_p))
+    L.qkdrec_free(ctypes.cast(ci, ctypes.c_void_p))
+    L.qkdrec_free(None)

@@ -88,3 +88,19 @@ def test_quasi_cyclic_code_structure(Z, nb):
     H = csr_matrix((np.ones(ci.size, dtype=np.int32), ci, rp), shape=(M, n))
     overlap = (H @ H.T).tocoo()
     assert overlap.data[overlap.row != overlap.col].max(initial=0) <= 1
+
+
+def test_c_philox_permutation_matches_numpy():
+    """The C generator's Philox-4x64-10 stream and Fisher-Yates shuffle draw the
+    permutation numpy's Generator(Philox(seed)) draws (so the library's code
+    construction and the generator's agree)."""
+    for seed, count in ((0, 1), (7, 10), (2003, 3 * 4096), (2**40 + 5, 99991), (2**64 - 1, 777)):
+        assert np.array_equal(synth.philox_permutation_c(seed, count), synth.philox(seed).permutation(count))
+
+
+def test_c_construction_equals_numpy_construction():
+    for seed, n, rate in ((2012, 4096, 0.75), (9, 2048, 40 / 64), (31337, 8192, 0.25)):
+        M = synth.checks_for_rate(n, rate)
+        a = synth.make_regular_code(seed, n, M)
+        b = synth.make_regular_code_c(seed, n, M)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
