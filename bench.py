@@ -817,7 +817,7 @@ def run_ours(args):
     lo_hi = {snr: q.quantiser_range(snr) for snr in SNRS}
     bob = {}
 
-    def step(xs, ys):
+    def step(xs, ys, opts=opts):
         for snr in SNRS:
             lo, hi = lo_hi[snr]
             sn = snr ** -0.5
@@ -885,6 +885,22 @@ def run_ours(args):
             fer[f"snr{int(snr)}_n2^{ln}"] = errs
             mean_iters[f"snr{int(snr)}_n2^{ln}"] = its
 
+    # per-result error against the FP64 oracle on a sample of sub-blocks, and (for the
+    # low-precision forms) the FER of the plain FP32 sum-product form on the same block
+    err_oracle = None if args.soft_chain or world > 1 else error_vs_oracle(
+        q, torch, dev, codes, codes_h, rate_of, host_x, host_y, opts)
+    fer_plain = None
+    if args.decoder != "sp_f32" and not args.soft_chain:
+        plain = q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=MAX_ITER, early_stop=True)
+        step(dx, dy, plain)
+        fer_plain = {}
+        for snr in SNRS:
+            for ln in LOGNS:
+                n, F = 1 << ln, N_SAMPLES >> ln
+                fer_plain[f"snr{int(snr)}_n2^{ln}"] = [
+                    round(int((alice[(snr, ln)][j].view(F, n) != bob[snr][j].view(F, n)).any(dim=1).sum()) / F, 4)
+                    for j in range(M_SLICES) if rate_of[(snr, ln, j)] > 0]
+
     # end to end through the public API: pinned host inputs -> device, result flags back
     t_e2e = None
     h2d = sum(host_x[s].numel() * 4 + host_y[s].numel() * 4 for s in SNRS)
@@ -936,6 +952,8 @@ def run_ours(args):
                    # the step time over 7 x the edge-updates executed (the paper's GPU: 3.2e-9 s)
                    "equivalent_c_h_s": (ms_step / 1e3) / (7 * edge_updates * world) if edge_updates else None,
                    "fer_per_slice": fer, "mean_iters_per_slice": mean_iters,
+                   "fer_plain_sp_f32_per_slice": fer_plain,
+                   "error_vs_oracle": err_oracle,
                    "code_residual_4cycles": residual, "setup_s": round(setup_s, 1)},
         "roofline": roof,
         "kernels": kernels,
@@ -947,6 +965,74 @@ def run_ours(args):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def error_vs_oracle(q, torch, dev, codes, codes_h, rate_of, host_x, host_y, opts, frames=8, iters=4):
+    """Per-result error of the decoder form against the FP64 oracle on a sample:
+    the first `frames` sub-blocks of n = 2^12 of every decoded slice at both SNRs,
+    with Bob's lower slices as the reconciled ones.  Each side computes its own
+    inputs (GPU: quantiser, slice LLR and syndrome kernels; oracle: its own FP64
+    quantiser, LLRs and syndromes from the same synthetic x, y).
+      llr_*         channel LLRs, |gpu - oracle|
+      post*_        posteriors after `iters` iterations without stopping test, same
+                    algorithm (FP64 on the oracle side), relative |gpu - oracle| /
+                    max(|oracle|, 1), and the fraction of hard decisions that differ
+      decoded_*     full decodes as in the bench (stopping test, <= MAX_ITER, the
+                    FP32 re-decode of failed frames): decoded bits and frames that
+                    differ from the oracle's FP64 decode of the same algorithm."""
+    import oracle
+    ln, n = 12, 1 << 12
+    cnt = frames * n
+    algo = opts.algo
+    o_alg = ("i" + algo) if opts.prec == "i8" else algo
+    fixed = q.DecodeOpts(algo=algo, prec=opts.prec, max_iter=iters, early_stop=False)
+    acc = dict(llr_max_abs=0.0, llr_mean_abs=[], post_max_rel=0.0, post_mean_rel=[], bits_differ=[],
+               decoded_bits_differ=[], decoded_frames_differ=[])
+    for snr in SNRS:
+        lo, hi = oracle.quantiser_range(snr)
+        sn = snr ** -0.5
+        x = host_x[snr][:cnt].numpy()
+        y = host_y[snr][:cnt].numpy()
+        _, bob_o = oracle.quantise(y, M_SLICES, lo, hi)
+        xd = torch.from_numpy(x).to(dev)
+        _, bob_g = q.qkdrec_quantise_slices(torch.from_numpy(y).to(dev), M_SLICES, lo, hi, want_idx=False)
+        for j in range(M_SLICES):
+            r = rate_of[(snr, ln, j)]
+            if r <= 0:
+                continue
+            rp, ci = codes_h[(ln, j, r)][:2]
+            c = codes[(ln, j, r)]
+            llr_g = q.qkdrec_slice_llr(xd, M_SLICES, j, lo, hi, sn, bob_g[:j] if j else None)
+            llr_o = oracle.slice_llr(x, bob_o[:j] if j else None, j, M_SLICES, lo, hi, sn)
+            d = np.abs(llr_g.cpu().numpy().astype(np.float64) - llr_o)
+            acc["llr_max_abs"] = max(acc["llr_max_abs"], float(d.max()))
+            acc["llr_mean_abs"].append(float(d.mean()))
+            syn_g = q.qkdrec_syndrome(c, bob_g[j].view(frames, n))
+            syn_o = oracle.syndrome(rp, ci, bob_o[j].reshape(frames, n))
+            g4 = q.qkdrec_decode_batch(c, llr_g.view(frames, n), syn_g, fixed, want_post=True)
+            o4 = oracle.decode(rp, ci, llr_o.reshape(frames, n), syn_o, o_alg, max_iter=iters, early_stop=False)
+            rel = np.abs(g4["post"].cpu().numpy() - o4["post"]) / np.maximum(np.abs(o4["post"]), 1.0)
+            acc["post_max_rel"] = max(acc["post_max_rel"], float(rel.max()))
+            acc["post_mean_rel"].append(float(rel.mean()))
+            acc["bits_differ"].append(float(np.mean(g4["bits"].cpu().numpy() != o4["bits"])))
+            gf = q.qkdrec_decode_batch(c, llr_g.view(frames, n), syn_g, opts)
+            of = oracle.decode(rp, ci, llr_o.reshape(frames, n), syn_o, o_alg, max_iter=MAX_ITER)
+            if opts.fallback_f32:
+                # the oracle re-decodes its failed frames with the same FP32 rule
+                o2 = "sp_flood" if opts.fallback_f32 == "sp" else algo
+                bad = ~of["converged"].astype(bool)
+                if bad.any():
+                    redo = oracle.decode(rp, ci, llr_o.reshape(frames, n)[bad], syn_o[bad], o2, max_iter=MAX_ITER)
+                    of["bits"][bad] = redo["bits"]
+            gb = gf["bits"].cpu().numpy()
+            acc["decoded_bits_differ"].append(float(np.mean(gb != of["bits"])))
+            acc["decoded_frames_differ"].append(float(np.mean(np.any(gb != of["bits"], axis=1))))
+    mean = lambda v: float(np.mean(v)) if v else 0.0
+    return {"sample": f"{frames} sub-blocks of n={n} per decoded slice at SNR 3 and 15, Bob's lower slices",
+            "iterations": iters, "llr_max_abs": acc["llr_max_abs"], "llr_mean_abs": mean(acc["llr_mean_abs"]),
+            "post_max_rel": acc["post_max_rel"], "post_mean_rel": mean(acc["post_mean_rel"]),
+            "bits_differ": mean(acc["bits_differ"]), "decoded_bits_differ": mean(acc["decoded_bits_differ"]),
+            "decoded_frames_differ": mean(acc["decoded_frames_differ"])}
 
 
 def source_region_sha(path, start, end):

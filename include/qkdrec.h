@@ -420,15 +420,20 @@ qkdrec_status qkdrec_woms_backward(qkdrec_code_t code, const float *llr, const u
  * allocation (which may synchronise the device) is not allowed.
  * It runs the same decoder on a fixed workspace of
  * qkdrec_decode_static_capacity() bytes (32 MiB) compiled into the library as
- * a device array; every device that loads the library holds that array until
- * the process exits.  The caller still passes the inputs and outputs, exactly
+ * a device array; every device that uses it holds that array until the process
+ * exits.  The caller still passes the inputs and outputs, exactly
  * as for qkdrec_decode_batch.
  *  - A request whose workspace (qkdrec_decode_workspace_size) is larger than
  *    the array fails with QKDREC_ERR_ARG before anything is enqueued; split
  *    the frames over several calls.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) and caches it; make that first call before any
- *    stream capture.
+ *  - Each call made outside stream capture looks up the array's device
+ *    address (cudaGetSymbolAddress) and keeps it; a call made while its stream
+ *    is capturing uses the address the last such call found on that device, so
+ *    make the first call on a device before any stream capture (otherwise
+ *    QKDREC_ERR_ARG).  Under lazy module loading (the CUDA default) the array's
+ *    memory is committed by the first call on each device, not when the
+ *    library is loaded; if the device has no room left for it then, that call
+ *    fails with QKDREC_ERR_NOMEM.
  *  - All calls share the one array.  Calls whose work overlaps on the GPU
  *    (other streams, other host threads) race and corrupt each other's
  *    results: serialise them.  Each call initialises every part of the array

@@ -18,7 +18,8 @@ decoders in bp.c), written from the paper's definitions:
   Sec. III-B "closest to the capacity"); chain rule and Slepian-Wolf bound
   (Eqs. beta2, SWB);
 * syndrome s_j = H_j S_j (Sec. II Step 5, Sec. III-B step 2);
-* BP decoders (Sec. III-C) -- see bp.c.
+* BP decoders (Sec. III-C) -- see bp.c; forward error radii of the FP16- and
+  FP32-message forms around them -- see bound.c.
 
 Readings where the paper is silent are listed in the module constants and in
 the function docstrings (quantiser range +-4 sigma_y, tie rule, LLR clip, SP
@@ -53,12 +54,12 @@ def _lib():
     with _LOCK:
         if _LIB is not None:
             return _LIB
-        src = os.path.join(_HERE, "bp.c")
+        srcs = [os.path.join(_HERE, "bp.c"), os.path.join(_HERE, "bound.c")]
         so = os.path.join(_BUILD, "liboracle_bp.so")
-        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        if not os.path.exists(so) or os.path.getmtime(so) < max(os.path.getmtime(f) for f in srcs):
             os.makedirs(_BUILD, exist_ok=True)
             tmp = so + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", src, "-o", tmp, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", *srcs, "-o", tmp, "-lm"])
             os.replace(tmp, so)
         lib = ctypes.CDLL(so)
         P = ctypes.c_void_p
@@ -70,6 +71,8 @@ def _lib():
         lib.oracle_ioms.argtypes = [I, I, I, P, P, I, P, P, P, P, I, I, D, I, P, P, P, P]
         lib.oracle_woms.argtypes = [I, I, P, P, P, P, P, I, I, P, P, P, P, P, P]
         lib.oracle_woms.restype = I
+        lib.oracle_lowp_bound.argtypes = [I, I, I, I, P, P, I, P, P, P, P, I, I, D, D, P, P]
+        lib.oracle_lowp_bound.restype = I
         for f in (lib.oracle_sp_flood, lib.oracle_oms_flood, lib.oracle_oms_layered, lib.oracle_ioms):
             f.restype = I
         _LIB = lib
@@ -414,6 +417,38 @@ def decode(row_ptr, col_idx, llr, synd, algo: str = "sp_flood", max_iter: int = 
     if rc != 0:
         raise MemoryError("oracle decoder allocation")
     return dict(bits=bits, iters=iters, converged=conv, post=post)
+
+
+def decode_bound(row_ptr, col_idx, llr, synd, algo: str, iters: int, f16: bool = True, offset: float = 0.5,
+                 phi_rel: float = 4e-6, layers=None):
+    """Posteriors after exactly `iters` iterations (no stopping test) with a forward
+    error radius per posterior (bound.c): (post float64 [F][n], radius float64 [F][n]).
+
+    post is the FP64 result of decode(..., max_iter=iters, early_stop=False); radius
+    bounds |L~ - L| for a decoder that runs the same rules in FP32 with the edge
+    messages stored in binary16 (f16=True) or binary32 (f16=False) and, for
+    sum-product, evaluates phi to a relative error of at most phi_rel.
+    algo: "sp_flood" | "oms_flood" | "oms_layered"."""
+    rp, ci, llr, synd, F, n, M, _, _, _, post = _prep(row_ptr, col_idx, llr, synd)
+    rad = np.zeros_like(post)
+    a = {"sp_flood": 0, "oms_flood": 1, "oms_layered": 2}[algo]
+    lptr = lchk = None
+    nl = 0
+    if a == 2:
+        if layers is None:
+            layers = greedy_layers(rp, ci, n)
+        _, lptr, lchk = layers
+        lptr = np.ascontiguousarray(lptr, dtype=np.int32)
+        lchk = np.ascontiguousarray(lchk, dtype=np.int32)
+        nl = lptr.shape[0] - 1
+    if F == 0:
+        return post, rad
+    P = lambda x: x.ctypes.data if x is not None else None
+    rc = _lib().oracle_lowp_bound(a, 1 if f16 else 0, n, M, P(rp), P(ci), nl, P(lptr), P(lchk), P(llr),
+                                  P(synd), F, int(iters), float(offset), float(phi_rel), P(post), P(rad))
+    if rc != 0:
+        raise MemoryError("oracle bound allocation")
+    return post, rad
 
 
 # ------------------------------------------------ weighted min-sum and gradient (a7)

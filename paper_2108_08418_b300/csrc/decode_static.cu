@@ -12,22 +12,36 @@ namespace qkd {
 constexpr size_t kStaticWorkspaceBytes = 32u << 20;
 static __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
 
-// The array's device address, looked up once per device.  In host code the
-// symbol is only a host-side stand-in, so the kernels get this address.
+// The array's device address.  In host code the symbol is only a host-side
+// stand-in, so the kernels get the address cudaGetSymbolAddress returns.  It
+// is looked up again on every call made outside stream capture (a device
+// reset reloads the module, and the array may move); a call made while its
+// stream is capturing uses the address the last uncaptured call on that
+// device found, so the first call on a device must come before any capture.
+// Under lazy module loading the lookup is what loads the module, so the
+// array's memory is committed at the first call on each device.
 static std::mutex g_static_mu;
 static void *g_static_ptr[64] = {nullptr};
 
-static qkdrec_status static_workspace(void **out) {
+static qkdrec_status static_workspace(cudaStream_t st, void **out) {
     int dev = 0;
     QKD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "device index %d above 63", dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    QKD_CUDA(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_workspace);
+        if (e == cudaErrorMemoryAllocation)
+            QKD_FAIL(QKDREC_ERR_NOMEM, "the built-in workspace (%zu bytes) could not be committed on device %d: %s",
+                     kStaticWorkspaceBytes, dev, cudaGetErrorString(e));
         if (e != cudaSuccess || !p)
             QKD_FAIL(QKDREC_ERR_CUDA, "cudaGetSymbolAddress(static workspace): %s", cudaGetErrorString(e));
         g_static_ptr[dev] = p;
+    } else if (!g_static_ptr[dev]) {
+        QKD_FAIL(QKDREC_ERR_ARG, "first call on device %d made during stream capture; call once outside capture first",
+                 dev);
     }
     *out = g_static_ptr[dev];
     return QKDREC_OK;
@@ -57,7 +71,7 @@ qkdrec_status qkdrec_decode_batch_static(qkdrec_code_t code, const float *llr, c
                  need, kStaticWorkspaceBytes);
     if (F == 0) return QKDREC_OK;
     void *ws = nullptr;
-    if ((s = static_workspace(&ws)) != QKDREC_OK) return s;
+    if ((s = static_workspace(as_stream(stream), &ws)) != QKDREC_OK) return s;
     return qkdrec_decode_batch(code, llr, synd, F, opts, bits_out, iters_out, conv_out, post_out, ws,
                                kStaticWorkspaceBytes, stream);
 }

@@ -193,6 +193,76 @@ def test_integer_min_sum_hand_example():
     assert np.array_equal(out["post"][0], np.array([1, -1, 2]) * 0.5)
 
 
+def saturating_codes():
+    """Hand codes where the 6-bit clip and the int16 posterior saturation both fire.
+    A: n = 2, 1100 checks {0, 1}.  B: A plus a last check {0, 1, 2}.  Every check
+    of A meets every other, so the first-fit layers are one check each, in index
+    order; B's last check is the last layer."""
+    K = 1100
+    rpA = np.arange(0, 2 * K + 1, 2, dtype=np.int32)
+    ciA = np.tile(np.array([0, 1], np.int32), K)
+    rpB = np.append(rpA, 2 * K + 3).astype(np.int32)
+    ciB = np.append(ciA, np.array([0, 1, 2], np.int32))
+    return (rpA, ciA, 2), (rpB, ciB, 3)
+
+
+@pytest.mark.parametrize("layered", [False, True])
+def test_integer_min_sum_saturation_by_hand(layered):
+    """Step 0.5, llr 20 -> 40 LSB, clipped to q = 31.  Code A, syndrome 0:
+    every check sends 31 - 1 = 30 to both variables.  Layered: after the k-th
+    check L = 31 + 30 k (the v->c value stays clipped at 31 while L grows, so
+    L = q_full + m uses the UNclipped q), saturating at 32767 after 1092 checks;
+    flooding: L = 31 + 1100 * 30 added in edge order, saturating likewise.  A
+    second iteration keeps 32767 (q_full = 32767 - 30, clipped to 31, + 30).
+    Clipping q before forming L would give 61; no clip would give a message of
+    32766 that int8 cannot hold; no saturation would give 33031."""
+    (rp, ci, n), _ = saturating_codes()
+    algo = "ioms_layered" if layered else "ioms_flood"
+    s = np.zeros((1, len(rp) - 1), np.uint8)
+    for it in (1, 2):
+        out = oracle.decode(rp, ci, np.array([[20.0, 20.0]]), s, algo, max_iter=it, early_stop=False,
+                            llr_step=0.5)
+        assert np.array_equal(out["post"][0], [32767 * 0.5, 32767 * 0.5])
+    # with the second variable negative the messages cancel to zero after one check
+    out = oracle.decode(rp, ci, np.array([[20.0, -20.0]]), s, algo, max_iter=1, early_stop=False, llr_step=0.5)
+    # layered: check 0 sends -30 / +30 -> L = (1, -1); every later check then sends
+    # max(1 - 1, 0) = 0.  Flooding: all 1100 checks send -30 / +30 from q = (31, -31).
+    expect = [1, -1] if layered else [-32767, 32767]
+    assert np.array_equal(out["post"][0], np.array(expect) * 0.5)
+
+
+@pytest.mark.parametrize("layered", [False, True])
+def test_integer_min_sum_clip_then_saturation_by_hand(layered):
+    """Code B, llr (20, 20, -2) -> (31, 31, -4).  Iteration 1: the 1100 checks
+    {0, 1} drive L0 = L1 to 32767; the last check sees q_full = (32767, 32767, -4),
+    clipped q = (31, 31, -4): to v0 and v1 sign(31 * -4) (min(31, 4) - 1) = -3, to
+    v2 +(31 - 1) = 30.  So L = (32764, 32764, 26) in both schedules (flooding adds
+    the last check's -3 after the 1100 saturating +30s, in edge order)."""
+    _, (rp, ci, n) = saturating_codes()
+    algo = "ioms_layered" if layered else "ioms_flood"
+    s = np.zeros((1, len(rp) - 1), np.uint8)
+    out = oracle.decode(rp, ci, np.array([[20.0, 20.0, -2.0]]), s, algo, max_iter=1, early_stop=False,
+                        llr_step=0.5)
+    assert np.array_equal(out["post"][0], np.array([32764, 32764, 26]) * 0.5)
+    assert np.array_equal(out["bits"][0], [0, 0, 0])
+
+
+def test_layered_integer_min_sum_equals_float_min_sum_on_a_real_code():
+    """Below the clip and saturation limits the layered integer decoder is the
+    float offset min-sum (offset 0.5) on the 0.5 grid, on a real regular code
+    (not only trees): LLRs on the grid with |llr| <= 3, so every |q| stays
+    below 31 for two iterations (|L| <= 3 + 3 * 3) and nothing saturates."""
+    rp, ci, n = (*synth.make_regular_code(77, 256, 128)[:2], 256)
+    g = np.random.default_rng(5)
+    llr = g.integers(-6, 7, size=(4, n)) * 0.5
+    s = g.integers(0, 2, size=(4, len(rp) - 1)).astype(np.uint8)
+    for it in (1, 2):
+        oi = oracle.decode(rp, ci, llr, s, "ioms_layered", max_iter=it, early_stop=False, llr_step=0.5)
+        of = oracle.decode(rp, ci, llr, s, "oms_layered", max_iter=it, early_stop=False, offset=0.5)
+        assert np.abs(of["post"]).max() < 31 * 0.5
+        assert np.array_equal(oi["post"], of["post"])
+
+
 def test_layer_partition_valid_and_first_fit():
     rp, ci, _, _, _, _ = _random_frames(9, n=256)
     n = 256
