@@ -539,7 +539,10 @@ def run_uneven(args):
         "cpu_baseline": cpu,
         "e2e": ({"value": good_bits / (t_e2e_max / args.steps / 1e3), "unit": "bit/s",
                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                 "ms_per_step": t_e2e_max / args.steps} if t_e2e else None),
+                 "ms_per_step": t_e2e_max / args.steps,
+                 "api": "qkdrec_reconcile with host x, y and host outputs (Alice's slices packed 8 per byte, "
+                        "converged flags, iteration counts of every point)",
+                 "same_result_as_device_run": e2e_same} if t_e2e else None),
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }
@@ -801,48 +804,77 @@ def run_ours(args):
     # low-precision forms re-decode the frames they leave unsatisfied in FP32
     opts = q.DecodeOpts(algo=algo, prec=prec, max_iter=MAX_ITER, early_stop=True,
                         fallback_f32=(args.fallback if prec != "f32" else False))
-    ws_bytes = max(q.qkdrec_decode_workspace_size(c, N_SAMPLES >> k[0], opts) for k, c in codes.items())
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-    # per point: Alice's reconciled planes and decoder side outputs
-    alice = {(snr, ln): torch.empty((M_SLICES, N_SAMPLES), dtype=torch.uint8, device=dev)
-             for snr in SNRS for ln in LOGNS}
-    iters = {(snr, ln, j): torch.empty(N_SAMPLES >> ln, dtype=torch.int32, device=dev)
-             for snr in SNRS for ln in LOGNS for j in range(M_SLICES)}
-    conv = {(snr, ln, j): torch.empty(N_SAMPLES >> ln, dtype=torch.uint8, device=dev)
-            for snr in SNRS for ln in LOGNS for j in range(M_SLICES)}
-    llr = torch.empty(N_SAMPLES, dtype=torch.float32, device=dev)
-    # soft chaining: the lower slices enter slice j's LLRs through their decoder posteriors
-    post = torch.empty((M_SLICES, N_SAMPLES), dtype=torch.float32, device=dev) if args.soft_chain else None
-    setup_s = time.time() - t_setup
+    plain = q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=MAX_ITER, early_stop=True)
     lo_hi = {snr: q.quantiser_range(snr) for snr in SNRS}
-    bob = {}
+    # per point (SNR, n): Alice's reconciled slices packed 8 to a byte, flags, iterations
+    alice_pk = {(snr, ln): torch.empty((M_SLICES, N_SAMPLES // 8), dtype=torch.uint8, device=dev)
+                for snr in SNRS for ln in LOGNS}
+    conv_pt = {(snr, ln): torch.empty((M_SLICES, N_SAMPLES >> ln), dtype=torch.uint8, device=dev)
+               for snr in SNRS for ln in LOGNS}
+    its_pt = {(snr, ln): torch.empty((M_SLICES, N_SAMPLES >> ln), dtype=torch.int32, device=dev)
+              for snr in SNRS for ln in LOGNS}
+    iters = {(snr, ln, j): its_pt[(snr, ln)][j] for snr in SNRS for ln in LOGNS for j in range(M_SLICES)}
+    conv = {(snr, ln, j): conv_pt[(snr, ln)][j] for snr in SNRS for ln in LOGNS for j in range(M_SLICES)}
 
-    def step(xs, ys, opts=opts):
+    def slice_codes(snr, ln):
+        return [codes[(ln, j, rate_of[(snr, ln, j)])] if rate_of[(snr, ln, j)] > 0 else None
+                for j in range(M_SLICES)]
+
+    def points(snr, outs):
+        return [dict(n=1 << ln, codes=slice_codes(snr, ln), alice_packed=outs[0][(snr, ln)],
+                     converged=outs[1][(snr, ln)], iters=outs[2][(snr, ln)]) for ln in LOGNS]
+
+    dev_outs = (alice_pk, conv_pt, its_pt)
+    rws = torch.empty(max(q.qkdrec_reconcile_workspace_size(N_SAMPLES, M_SLICES, o, points(snr, dev_outs))
+                          for snr in SNRS for o in (opts, plain)), dtype=torch.uint8, device=dev)
+    if args.soft_chain:
+        # soft chaining (slice j's LLRs from the lower slices' decoder posteriors) runs
+        # through the single-step calls
+        ws = torch.empty(max(q.qkdrec_decode_workspace_size(c, N_SAMPLES >> k[0], opts) for k, c in codes.items()),
+                         dtype=torch.uint8, device=dev)
+        alice = torch.empty((M_SLICES, N_SAMPLES), dtype=torch.uint8, device=dev)
+        llr = torch.empty(N_SAMPLES, dtype=torch.float32, device=dev)
+        post = torch.empty((M_SLICES, N_SAMPLES), dtype=torch.float32, device=dev)
+    setup_s = time.time() - t_setup
+
+    def step_soft(xs, ys, opts, outs):
         for snr in SNRS:
             lo, hi = lo_hi[snr]
             sn = snr ** -0.5
-            _, bits = q.qkdrec_quantise_slices(ys[snr], M_SLICES, lo, hi, want_idx=False)
-            bob[snr] = bits
+            x_s = xs[snr] if xs[snr].is_cuda else xs[snr].to(dev, non_blocking=True)
+            y_s = ys[snr] if ys[snr].is_cuda else ys[snr].to(dev, non_blocking=True)
+            _, bits = q.qkdrec_quantise_slices(y_s, M_SLICES, lo, hi, want_idx=False)
             for ln in LOGNS:
                 n, F = 1 << ln, N_SAMPLES >> ln
-                a = alice[(snr, ln)]
                 for j in range(M_SLICES):
                     r = rate_of[(snr, ln, j)]
                     if r <= 0:
-                        a[j].copy_(bits[j])          # disclosed slice: Bob's bits in the clear
-                        if post is not None:
-                            q.qkdrec_bits_to_llr(bits[j], out=post[j])
+                        alice[j].copy_(bits[j])          # disclosed slice: Bob's bits in the clear
+                        q.qkdrec_bits_to_llr(bits[j], out=post[j])
+                        conv_pt[(snr, ln)][j].fill_(1)
+                        its_pt[(snr, ln)][j].zero_()
                         continue
                     c = codes[(ln, j, r)]
                     synd = q.qkdrec_syndrome(c, bits[j].view(F, n))
-                    if post is not None:
-                        q.qkdrec_slice_llr_soft(xs[snr], M_SLICES, j, lo, hi, sn, post[:j] if j else None, out=llr)
-                    else:
-                        q.qkdrec_slice_llr(xs[snr], M_SLICES, j, lo, hi, sn, a[:j] if j else None, out=llr)
+                    q.qkdrec_slice_llr_soft(x_s, M_SLICES, j, lo, hi, sn, post[:j] if j else None, out=llr)
                     q.qkdrec_decode_batch(c, llr.view(F, n), synd, opts, workspace=ws,
-                                          out=dict(bits=a[j].view(F, n), iters=iters[(snr, ln, j)],
-                                                   converged=conv[(snr, ln, j)],
-                                                   post=post[j].view(F, n) if post is not None else None))
+                                          out=dict(bits=alice[j].view(F, n), iters=its_pt[(snr, ln)][j],
+                                                   converged=conv_pt[(snr, ln)][j], post=post[j].view(F, n)))
+                for j in range(M_SLICES):
+                    q.qkdrec_pack_bits(alice[j], out=alice_pk[(snr, ln)][j])
+                if outs is not dev_outs:
+                    for k in range(3):
+                        outs[k][(snr, ln)].copy_(dev_outs[k][(snr, ln)], non_blocking=True)
+
+    def step(xs, ys, opts=opts, outs=dev_outs):
+        """One reverse reconciliation of both blocks at every sub-block length."""
+        if args.soft_chain:
+            step_soft(xs, ys, opts, outs)
+            return
+        for snr in SNRS:
+            lo, hi = lo_hi[snr]
+            q.qkdrec_reconcile(xs[snr], ys[snr], M_SLICES, lo, hi, snr ** -0.5, opts, points(snr, outs),
+                               workspace=rws, device=dev)
 
     def barrier():
         if world > 1:
@@ -866,7 +898,19 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
 
-    # correctness of the last step: frames whose decoded word equals Bob's
+    # correctness of the last step: sub-blocks whose decoded word equals Bob's
+    # (Bob's slices packed the same way, outside the timed region)
+    bob_pk = {}
+    for snr in SNRS:
+        lo, hi = lo_hi[snr]
+        _, bits = q.qkdrec_quantise_slices(dy[snr], M_SLICES, lo, hi, want_idx=False)
+        bob_pk[snr] = torch.stack([q.qkdrec_pack_bits(bits[j]) for j in range(M_SLICES)])
+        del bits
+
+    def frame_errors(snr, ln, j, packed):
+        n, F = 1 << ln, N_SAMPLES >> ln
+        return int((packed[(snr, ln)][j].view(F, n // 8) != bob_pk[snr][j].view(F, n // 8)).any(dim=1).sum())
+
     good_bits, raw_bits, fer, mean_iters = 0, 0, {}, {}
     edge_updates = sum(v["units"] for k, v in stats.items() if k.startswith(("check_flood", "layer_oms"))) / args.steps
     for snr in SNRS:
@@ -876,14 +920,25 @@ def run_ours(args):
             for j in range(M_SLICES):
                 if rate_of[(snr, ln, j)] <= 0:
                     continue
-                bad = (alice[(snr, ln)][j].view(F, n) != bob[snr][j].view(F, n)).any(dim=1)
-                nbad = int(bad.sum().item())
+                nbad = frame_errors(snr, ln, j, alice_pk)
                 good_bits += n * (F - nbad)
                 raw_bits += N_SAMPLES
                 errs.append(round(nbad / F, 4))
                 its.append(round(float(iters[(snr, ln, j)].float().mean().item()), 2))
             fer[f"snr{int(snr)}_n2^{ln}"] = errs
             mean_iters[f"snr{int(snr)}_n2^{ln}"] = its
+    # how full the decoders' frame blocks stay: frame-iterations done over what
+    # the blocks (32 frames, kept until their last frame stops) occupy
+    occ_num = occ_den = 0.0
+    for (snr, ln, j), it in iters.items():
+        if rate_of[(snr, ln, j)] <= 0:
+            continue
+        e = codes[(ln, j, rate_of[(snr, ln, j)])].E
+        t = it.to(torch.float64) + 1.0
+        pad = (-t.numel()) % 32
+        tb = torch.cat([t, torch.zeros(pad, dtype=t.dtype, device=t.device)]).view(-1, 32)
+        occ_num += float(tb.sum()) * e
+        occ_den += float(tb.max(dim=1).values.sum()) * 32 * e
 
     # per-result error against the FP64 oracle on a sample of sub-blocks, and (for the
     # low-precision forms) the FER of the plain FP32 sum-product form on the same block
@@ -891,34 +946,33 @@ def run_ours(args):
         q, torch, dev, codes, codes_h, rate_of, host_x, host_y, opts)
     fer_plain = None
     if args.decoder != "sp_f32" and not args.soft_chain:
-        plain = q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=MAX_ITER, early_stop=True)
         step(dx, dy, plain)
-        fer_plain = {}
-        for snr in SNRS:
-            for ln in LOGNS:
-                n, F = 1 << ln, N_SAMPLES >> ln
-                fer_plain[f"snr{int(snr)}_n2^{ln}"] = [
-                    round(int((alice[(snr, ln)][j].view(F, n) != bob[snr][j].view(F, n)).any(dim=1).sum()) / F, 4)
-                    for j in range(M_SLICES) if rate_of[(snr, ln, j)] > 0]
+        fer_plain = {f"snr{int(snr)}_n2^{ln}": [round(frame_errors(snr, ln, j, alice_pk) / (N_SAMPLES >> ln), 4)
+                                                 for j in range(M_SLICES) if rate_of[(snr, ln, j)] > 0]
+                     for snr in SNRS for ln in LOGNS}
 
-    # end to end through the public API: pinned host inputs -> device, result flags back
+    # end to end through the public API: the same call with HOST buffers -- x, y read
+    # from pinned host memory and Alice's packed slices, flags and iteration counts of
+    # every point written back to pinned host memory, inside the timed region
     t_e2e = None
+    host_outs = tuple({k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in d.items()}
+                      for d in dev_outs)
     h2d = sum(host_x[s].numel() * 4 + host_y[s].numel() * 4 for s in SNRS)
-    d2h = sum(v.numel() for v in conv.values())
+    d2h = sum(t.numel() * t.element_size() for d in host_outs for t in d.values())
     if not args.no_e2e:
         barrier()
         e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e2.record(stream)
         for _ in range(args.steps):
-            xs = {s: host_x[s].to(dev, non_blocking=True) for s in SNRS}
-            ys = {s: host_y[s].to(dev, non_blocking=True) for s in SNRS}
-            step(xs, ys)
-            flags = [v.to("cpu", non_blocking=True) for v in conv.values()]
+            step(host_x, host_y, opts, host_outs)
             torch.cuda.current_stream(dev).synchronize()
-            _ = [int(f.sum()) for f in flags]
         e3.record(stream)
         barrier()
         t_e2e = e2.elapsed_time(e3)
+        # the host copies hold the same result as the device-timed run
+        e2e_same = all(torch.equal(host_outs[0][k].to(dev), alice_pk[k]) for k in alice_pk)
+    else:
+        e2e_same = None
 
     # aggregate over ranks
     (good_bits, raw_bits), (ms, t_e2e_max) = reduce_over_ranks([good_bits, raw_bits], [ms, t_e2e or 0.0], dev,
@@ -953,6 +1007,7 @@ def run_ours(args):
                    "equivalent_c_h_s": (ms_step / 1e3) / (7 * edge_updates * world) if edge_updates else None,
                    "fer_per_slice": fer, "mean_iters_per_slice": mean_iters,
                    "fer_plain_sp_f32_per_slice": fer_plain,
+                   "frame_block_occupancy": occ_num / occ_den if occ_den else None,
                    "error_vs_oracle": err_oracle,
                    "code_residual_4cycles": residual, "setup_s": round(setup_s, 1)},
         "roofline": roof,
@@ -960,7 +1015,10 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": ({"value": good_bits / (t_e2e_max / args.steps / 1e3), "unit": "bit/s",
                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                 "ms_per_step": t_e2e_max / args.steps} if t_e2e else None),
+                 "ms_per_step": t_e2e_max / args.steps,
+                 "api": "qkdrec_reconcile with host x, y and host outputs (Alice's slices packed 8 per byte, "
+                        "converged flags, iteration counts of every point)",
+                 "same_result_as_device_run": e2e_same} if t_e2e else None),
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }
@@ -1147,6 +1205,9 @@ def run_reference_uneven(args, world, cores):
 
 # ------------------------------------------------------- profiling case
 CASES = {
+    # the slice LLR kernel on 2^24 samples of the sweep's data (SNR 3, slice 2, Bob's
+    # lower slices): the small case for ncu
+    "slice_llr": dict(llr=(3.0, 2), count=1 << 24),
     # one slice decode of the sweep at n = 2^16 and 512 frames (edge messages 400 MB,
     # larger than L2; ~1 GB on the device): the small case for ncu --set full
     "decode_sp_f32": dict(logn=16, frames=512, rate=0.84375, algo="sp_flood", prec="f32", iters=5),
@@ -1226,6 +1287,18 @@ def run_case(args):
     from paper_2108_08418_b300 import build as qbuild
     qbuild.build()
     c = CASES[args.case]
+    if "llr" in c:
+        snr, j = c["llr"]
+        lo, hi = q.qkdrec_quantiser_range(snr)
+        x, y = synth.gaussian_pair(DATA_SEED[snr], c["count"], snr)
+        xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        _, bits = q.qkdrec_quantise_slices(yd, M_SLICES, lo, hi, want_idx=False)
+        out = torch.empty_like(xd)
+        for _ in range(args.warmup + args.steps):
+            q.qkdrec_slice_llr(xd, M_SLICES, j, lo, hi, snr ** -0.5, bits[:j] if j else None, out=out)
+        torch.cuda.synchronize()
+        print(f"case {args.case}: {c['count']} samples, slice {j} at SNR {snr}", flush=True)
+        return
     if "groups" in c:
         run_plan_case(args, c)
         return

@@ -282,6 +282,72 @@ qkdrec_status qkdrec_slice_llr_soft(const float *x, int64_t count, int32_t m_sli
  * DEVICE float [count]; for slices that are disclosed rather than decoded. */
 qkdrec_status qkdrec_bits_to_llr(const uint8_t *bits, int64_t count, float *llr_out, void *stream);
 
+/* ------------------------------------------- whole reconciliation of a block */
+
+/*
+ * One sub-block partition of a block (Sec. III-A: the block of N samples is
+ * decoded as N_d = N / N_R sub-blocks of length N_R = n, all sharing the
+ * slice's parity-check matrix).
+ *   n             sub-block length: a positive multiple of 32 dividing count.
+ *   codes         HOST array [m_slices]: the code of slice j (length n), or
+ *                 NULL for a slice that is disclosed (rate 0: Bob's bits are
+ *                 sent in the clear, Sec. II Step 5).
+ *   alice_packed  out [m_slices][count / 8]: Alice's reconciled slices, sample i
+ *                 of slice j in bit i % 8 of byte j count / 8 + i / 8.
+ *   converged     out [m_slices][count / n] (may be NULL): 1 iff the decoded
+ *                 sub-block satisfies Bob's syndrome (1 for disclosed slices).
+ *   iters         out int32 [m_slices][count / n] (may be NULL): iterations
+ *                 (0 for disclosed slices).
+ * Each output may be HOST or DEVICE memory (told apart with
+ * cudaPointerGetAttributes); host outputs are written by copies on the stream,
+ * so they are complete after the caller synchronises the stream.
+ */
+typedef struct {
+    int32_t n;
+    const qkdrec_code_t *codes;
+    uint8_t *alice_packed;
+    uint8_t *converged;
+    int32_t *iters;
+} qkdrec_point;
+
+/* DEVICE workspace bytes qkdrec_reconcile needs for these arguments (the
+ * sizes of the codes, the frame counts and the decoder options). */
+qkdrec_status qkdrec_reconcile_workspace_size(int64_t count, int32_t m_slices, const qkdrec_decode_opts *opts,
+                                              const qkdrec_point *points, int32_t n_points, size_t *bytes);
+
+/*
+ * Reverse slice reconciliation of one block of count quadrature pairs, end to
+ * end (Sec. II Steps 4-5, Sec. III-B steps 1-5, Sec. III-A):
+ *   Bob quantises y (qkdrec_quantise_slices with lo, hi, label) into m_slices
+ *   bit planes; for every partition in `points` and every decoded slice j
+ *   (LSB first) he forms the syndromes of the sub-blocks; Alice computes the
+ *   slice LLRs from x and her already reconciled slices 0..j-1
+ *   (qkdrec_slice_llr with sigma_n) and decodes every sub-block
+ *   (qkdrec_decode_batch with opts; the FP32 re-decode of opts applies).
+ *   Disclosed slices take Bob's bits.  The slices are packed eight to a byte.
+ *   The partitions are independent reconciliations of the same block (the
+ *   sub-block lengths N_R of the paper's Sec. IV-V comparison).
+ *   x, y        float [count], HOST or DEVICE; host memory is copied into the
+ *               workspace on the stream (pinned memory lets the copy overlap).
+ *   bob_packed  out [m_slices][count / 8] (may be NULL, HOST or DEVICE): Bob's
+ *               slices, packed like alice_packed, for checking the result.
+ *   workspace   DEVICE, >= qkdrec_reconcile_workspace_size bytes, 256-byte
+ *               aligned, clobbered.  Nothing is allocated.
+ * Asynchronous on `stream`; all argument checks happen before anything is
+ * enqueued.  Errors: QKDREC_ERR_ARG (sizes, NULLs, a code whose length is not
+ * its partition's n, workspace too small), the errors of the calls above.
+ */
+qkdrec_status qkdrec_reconcile(const float *x, const float *y, int64_t count, int32_t m_slices, double lo,
+                               double hi, double sigma_n, qkdrec_label label, const qkdrec_decode_opts *opts,
+                               const qkdrec_point *points, int32_t n_points, uint8_t *bob_packed,
+                               void *workspace, size_t workspace_bytes, void *stream);
+
+/* Bits (DEVICE uint8 [count], values 0/1) -> DEVICE packed [count / 8], bit
+ * i % 8 of byte i / 8; count a multiple of 32, bits 16-byte and packed 4-byte
+ * aligned.  qkdrec_unpack_bits is the inverse (writes 0/1 bytes). */
+qkdrec_status qkdrec_pack_bits(const uint8_t *bits, int64_t count, uint8_t *packed, void *stream);
+qkdrec_status qkdrec_unpack_bits(const uint8_t *packed, int64_t count, uint8_t *bits, void *stream);
+
 /* ------------------------------------------------ uneven batches (one launch) */
 
 /*

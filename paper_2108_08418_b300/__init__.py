@@ -40,7 +40,8 @@ EXPORTED = [
     "qkdrec_plan_get_tuning", "qkdrec_plan_autotune", "qkdrec_slice_llr_soft", "qkdrec_bits_to_llr",
     "qkdrec_code_set_qc", "qkdrec_qc_timeouts",
     "qkdrec_make_regular_code", "qkdrec_free", "qkdrec_code_rate", "qkdrec_checks_for_rate",
-    "qkdrec_quantiser_range",
+    "qkdrec_quantiser_range", "qkdrec_reconcile", "qkdrec_reconcile_workspace_size", "qkdrec_pack_bits",
+    "qkdrec_unpack_bits",
 ]
 SELFTEST = ["qkdrec_selftest_phi"]
 
@@ -68,6 +69,11 @@ class TuningC(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PointC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("codes", ctypes.c_void_p), ("alice_packed", ctypes.c_void_p),
+                ("converged", ctypes.c_void_p), ("iters", ctypes.c_void_p)]
 
 
 class DecodeOptsC(ctypes.Structure):
@@ -107,6 +113,10 @@ def lib():
         "qkdrec_slice_capacity": (U, [D, I32, I32, D, D, U, D, P]),
         "qkdrec_make_regular_code": (U, [U64, I32, I32, I32, P, P, P]),
         "qkdrec_free": (None, [P]),
+        "qkdrec_reconcile_workspace_size": (U, [I64, I32, P, P, I32, P]),
+        "qkdrec_reconcile": (U, [P, P, I64, I32, D, D, D, U, P, P, I32, P, P, ctypes.c_size_t, P]),
+        "qkdrec_pack_bits": (U, [P, I64, P, P]),
+        "qkdrec_unpack_bits": (U, [P, I64, P, P]),
         "qkdrec_code_rate": (U, [D, D, I32, P]),
         "qkdrec_checks_for_rate": (U, [I32, D, P]),
         "qkdrec_quantiser_range": (U, [D, D, P, P]),
@@ -401,6 +411,93 @@ def qkdrec_decode_batch_static(code: Code, llr, synd, opts: DecodeOpts | None = 
                                             ctypes.c_void_p(out["converged"].data_ptr()),
                                             ctypes.c_void_p(post.data_ptr()) if post is not None else None,
                                             _stream(llr)))
+    return out
+
+
+# ------------------------------------------------- whole reconciliation of a block
+def _ptr(t, dtype, name):
+    """Address of a contiguous tensor on the host or a CUDA device (the C side tells them apart)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _Points:
+    """qkdrec_point array for a list of dicts(n, codes, alice_packed, converged=None, iters=None)."""
+
+    def __init__(self, points, m_slices):
+        torch = _torch()
+        self.keep = []
+        self.arr = (PointC * len(points))()
+        for i, p in enumerate(points):
+            if len(p["codes"]) != m_slices:
+                raise ValueError("one code (or None) per slice")
+            codes = (ctypes.c_void_p * m_slices)(*[c.handle.value if c is not None else None for c in p["codes"]])
+            self.keep.append(codes)
+            conv, its = p.get("converged"), p.get("iters")
+            self.arr[i] = PointC(int(p["n"]), ctypes.cast(codes, ctypes.c_void_p).value,
+                                 _ptr(p["alice_packed"], torch.uint8, "alice_packed").value,
+                                 _ptr(conv, torch.uint8, "converged").value if conv is not None else None,
+                                 _ptr(its, torch.int32, "iters").value if its is not None else None)
+
+
+def qkdrec_reconcile_workspace_size(count: int, m_slices: int, opts: DecodeOpts, points) -> int:
+    o = opts.c()
+    pts = _Points(points, m_slices)
+    b = ctypes.c_size_t()
+    _check(lib().qkdrec_reconcile_workspace_size(int(count), int(m_slices), ctypes.byref(o), pts.arr, len(points),
+                                                 ctypes.byref(b)))
+    return b.value
+
+
+def qkdrec_reconcile(x, y, m_slices: int, lo: float, hi: float, sigma_n: float, opts: DecodeOpts, points,
+                     bob_packed=None, label: str = "gray", workspace=None, device=None):
+    """Reverse slice reconciliation of one block (see include/qkdrec.h).  x, y: float32
+    [count] on the host (pinned for overlap) or the device; points: dicts with n, codes
+    (Code or None per slice), alice_packed uint8 [m][count/8], optional converged uint8
+    [m][count/n] and iters int32 [m][count/n], each on the host or the device.  Runs on
+    torch's current stream of `device` (default: the current CUDA device)."""
+    torch = _torch()
+    count = x.numel()
+    if y.numel() != count:
+        raise ValueError("x and y must have the same length")
+    dev = torch.device(device) if device is not None else (x.device if x.is_cuda else
+                                                           torch.device("cuda", torch.cuda.current_device()))
+    o = opts.c()
+    pts = _Points(points, m_slices)
+    if workspace is None:
+        workspace = torch.empty(max(qkdrec_reconcile_workspace_size(count, m_slices, opts, points), 256),
+                                dtype=torch.uint8, device=dev)
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    with torch.cuda.device(dev):
+        _check(lib().qkdrec_reconcile(_ptr(x, torch.float32, "x"), _ptr(y, torch.float32, "y"), count,
+                                      int(m_slices), float(lo), float(hi), float(sigma_n), _LABELS[label],
+                                      ctypes.byref(o), pts.arr, len(points),
+                                      _ptr(bob_packed, torch.uint8, "bob_packed") if bob_packed is not None else None,
+                                      ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), st))
+    return workspace
+
+
+def qkdrec_pack_bits(bits, out=None):
+    """0/1 bytes (CUDA uint8 [count], count % 32 == 0) -> packed uint8 [count/8], bit i%8 of byte i/8."""
+    torch = _torch()
+    count = bits.numel()
+    if out is None:
+        out = torch.empty(count // 8, dtype=torch.uint8, device=bits.device)
+    _check(lib().qkdrec_pack_bits(_dev(bits, torch.uint8, "bits"), count, _dev(out, torch.uint8, "out"),
+                                  _stream(bits)))
+    return out
+
+
+def qkdrec_unpack_bits(packed, count=None, out=None):
+    """Inverse of qkdrec_pack_bits."""
+    torch = _torch()
+    count = packed.numel() * 8 if count is None else int(count)
+    if out is None:
+        out = torch.empty(count, dtype=torch.uint8, device=packed.device)
+    _check(lib().qkdrec_unpack_bits(_dev(packed, torch.uint8, "packed"), count, _dev(out, torch.uint8, "out"),
+                                    _stream(packed)))
     return out
 
 

@@ -89,4 +89,18 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Bob's syndromes as the decoder takes them: bytes [F][M], or packed words
+// [M][W] (bit f % 32 of word f / 32 of check c at packed[c W + f / 32]).
+struct SyndIn {
+    const uint8_t *bytes = nullptr;
+    const uint32_t *packed = nullptr;
+    int64_t W = 0;
+};
+
+// qkdrec_decode_batch with either syndrome form (argument checks included).
+qkdrec_status decode_batch_impl(qkdrec_code_t code, const float *llr, const SyndIn &synd, int32_t F,
+                                const qkdrec_decode_opts *opts, uint8_t *bits_out, int32_t *iters_out,
+                                uint8_t *conv_out, float *post_out, void *workspace, size_t workspace_bytes,
+                                void *stream);
+
 }  // namespace qkd

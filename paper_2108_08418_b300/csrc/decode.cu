@@ -946,6 +946,25 @@ __global__ void prep_synd(const uint8_t *__restrict__ synd, int32_t F, int32_t M
     }
 }
 
+// packed syndromes [M][W_in] -> sbits [M][W] of this pass's layout (frames of
+// a compacted pass gathered through fmap; positions past the placed frames 0)
+__global__ void prep_synd_packed(const uint32_t *__restrict__ packed, int64_t W_in, int32_t F, int32_t M, int64_t W,
+                                 uint32_t *__restrict__ sbits, const int32_t *fmap = nullptr,
+                                 const int32_t *fcnt = nullptr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cbeg = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 64;
+    const int64_t Fv = frames_placed(F, fcnt);
+    for (int64_t w = blockIdx.y; w < W; w += gridDim.y) {
+        const int64_t f = w * 32 + lane;
+        const int64_t g = f < Fv ? frame_at(f, fmap) : 0;
+        for (int64_t c = cbeg; c < cbeg + 64 && c < M; ++c) {
+            const uint32_t bit = (f < Fv) ? (__ldg(packed + c * W_in + (g >> 5)) >> (g & 31)) & 1u : 0u;
+            const uint32_t word = __ballot_sync(0xffffffffu, bit);
+            if (lane == 0) sbits[c * W + w] = word;
+        }
+    }
+}
+
 // per-frame state; `mask` marks the frames this decode owns (all real frames,
 // or only the frames a low-precision pass left unsatisfied, in place or
 // compacted to the first *fcnt positions)
@@ -1168,7 +1187,7 @@ static qkdrec_status rebuild_blocks(const Layout &l, char *ws, cudaStream_t st) 
 // posteriors, packed syndromes, zero messages.
 // compact: decode the frames with conv_prev[f] == 0 packed to the front (a
 // re-decode then touches only the frame blocks that hold them)
-static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
+static qkdrec_status prepare(const CodeDev &d, const float *llr, const SyndIn &synd, int32_t F,
                              const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, bool compact,
                              char *ws, const Layout &l, cudaStream_t st, DecArgs &a, Prepared &pr) {
     a.rp = d.rp;
@@ -1229,7 +1248,12 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const uint8_t *
     {
         prof::Scope ps(prof::kPrep, st);
         dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)std::min<int64_t>(l.W, 65535));
-        prep_synd<<<grd, 256, 0, st>>>(synd, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits), fmap, fcnt);
+        if (synd.packed)
+            prep_synd_packed<<<grd, 256, 0, st>>>(synd.packed, synd.W, F, d.M, l.W,
+                                                  reinterpret_cast<uint32_t *>(ws + l.sbits), fmap, fcnt);
+        else
+            prep_synd<<<grd, 256, 0, st>>>(synd.bytes, F, d.M, l.W, reinterpret_cast<uint32_t *>(ws + l.sbits), fmap,
+                                           fcnt);
     }
     QKD_LAUNCHED("prep_synd");
     const size_t ms = prec == kF32 ? 4 : (prec == kF16 ? 2 : 1);
@@ -1314,7 +1338,7 @@ static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaSt
 }
 
 // One flooding decode pass over the frames selected by conv_prev (NULL = all).
-static qkdrec_status run_flood(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
+static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn &synd, int32_t F,
                                const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, bool compact,
                                uint8_t *bits_out, int32_t *iters_out, uint8_t *conv_out,
                                float *post_out, char *ws, cudaStream_t st) {
@@ -1382,6 +1406,48 @@ __global__ void phi_selftest_kernel(const float *__restrict__ x, int64_t count, 
         out[i] = phi_clamped(x[i]);
 }
 
+qkdrec_status decode_batch_impl(qkdrec_code_t code, const float *llr, const SyndIn &synd, int32_t F,
+                                const qkdrec_decode_opts *opts, uint8_t *bits_out, int32_t *iters_out,
+                                uint8_t *conv_out, float *post_out, void *workspace, size_t workspace_bytes,
+                                void *stream) {
+    clear_error();
+    if (!code) QKD_FAIL(QKDREC_ERR_ARG, "code is NULL");
+    if (F < 0) QKD_FAIL(QKDREC_ERR_ARG, "F < 0");
+    if (!opts_ok(opts)) QKD_FAIL(QKDREC_ERR_ARG, "bad decode options");
+    const qkdrec_decode_opts o = *opts;
+    if (o.prec == QKDREC_I8SAT && o.algo == QKDREC_SP_FLOOD)
+        QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "integer messages need an offset min-sum algorithm");
+    if (F == 0) return QKDREC_OK;
+    if (F > kMaxFrames) QKD_FAIL(QKDREC_ERR_ARG, "F=%d above the %d frames of one launch", F, kMaxFrames);
+    if (!llr || !(synd.bytes || synd.packed) || !bits_out || !iters_out || !conv_out)
+        QKD_FAIL(QKDREC_ERR_ARG, "NULL input/output");
+    if (synd.packed && synd.W < ceil_div(F, 32)) QKD_FAIL(QKDREC_ERR_ARG, "packed syndrome rows too short");
+    if (!workspace) QKD_FAIL(QKDREC_ERR_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) QKD_FAIL(QKDREC_ERR_ARG, "workspace not 256-byte aligned");
+    const size_t need = workspace_for(code->d, F, &o);
+    if (workspace_bytes < need) QKD_FAIL(QKDREC_ERR_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, need);
+    const CodeDev &d = code->d;
+    cudaStream_t st = as_stream(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    qkdrec_status s;
+    auto pass = [&](const qkdrec_decode_opts &po, int prec, const uint8_t *conv_prev, bool compact) {
+        if (po.algo == QKDREC_OMS_LAYERED)
+            return run_layered(d, llr, synd, F, po, prec, conv_prev, compact, bits_out, iters_out, conv_out,
+                               post_out, ws, st);
+        return run_flood(d, llr, synd, F, po, prec, conv_prev, compact, bits_out, iters_out, conv_out, post_out,
+                         ws, st);
+    };
+    if ((s = pass(o, o.prec, nullptr, false)) != QKDREC_OK) return s;
+    // FP32 re-decode of the frames a low-precision pass left unsatisfied,
+    // compacted to the front so that it costs what the failed frames need
+    if (o.fallback_f32 && o.prec != QKDREC_F32) {
+        qkdrec_decode_opts o2 = o;
+        if (o.fallback_f32 == 2) o2.algo = QKDREC_SP_FLOOD;
+        if ((s = pass(o2, QKDREC_F32, conv_out, true)) != QKDREC_OK) return s;
+    }
+    return QKDREC_OK;
+}
+
 }  // namespace qkd
 
 using namespace qkd;
@@ -1424,40 +1490,10 @@ qkdrec_status qkdrec_decode_batch(qkdrec_code_t code, const float *llr, const ui
                                   const qkdrec_decode_opts *opts, uint8_t *bits_out, int32_t *iters_out,
                                   uint8_t *conv_out, float *post_out, void *workspace,
                                   size_t workspace_bytes, void *stream) {
-    clear_error();
-    if (!code) QKD_FAIL(QKDREC_ERR_ARG, "code is NULL");
-    if (F < 0) QKD_FAIL(QKDREC_ERR_ARG, "F < 0");
-    if (!opts_ok(opts)) QKD_FAIL(QKDREC_ERR_ARG, "bad decode options");
-    const qkdrec_decode_opts o = *opts;
-    if (o.prec == QKDREC_I8SAT && o.algo == QKDREC_SP_FLOOD)
-        QKD_FAIL(QKDREC_ERR_UNSUPPORTED, "integer messages need an offset min-sum algorithm");
-    if (F == 0) return QKDREC_OK;
-    if (F > kMaxFrames) QKD_FAIL(QKDREC_ERR_ARG, "F=%d above the %d frames of one launch", F, kMaxFrames);
-    if (!llr || !synd || !bits_out || !iters_out || !conv_out) QKD_FAIL(QKDREC_ERR_ARG, "NULL input/output");
-    if (!workspace) QKD_FAIL(QKDREC_ERR_ARG, "workspace is NULL");
-    if (reinterpret_cast<uintptr_t>(workspace) % 256) QKD_FAIL(QKDREC_ERR_ARG, "workspace not 256-byte aligned");
-    const size_t need = workspace_for(code->d, F, &o);
-    if (workspace_bytes < need) QKD_FAIL(QKDREC_ERR_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, need);
-    const CodeDev &d = code->d;
-    cudaStream_t st = as_stream(stream);
-    char *ws = reinterpret_cast<char *>(workspace);
-    qkdrec_status s;
-    auto pass = [&](const qkdrec_decode_opts &po, int prec, const uint8_t *conv_prev, bool compact) {
-        if (po.algo == QKDREC_OMS_LAYERED)
-            return run_layered(d, llr, synd, F, po, prec, conv_prev, compact, bits_out, iters_out, conv_out,
-                               post_out, ws, st);
-        return run_flood(d, llr, synd, F, po, prec, conv_prev, compact, bits_out, iters_out, conv_out, post_out,
-                         ws, st);
-    };
-    if ((s = pass(o, o.prec, nullptr, false)) != QKDREC_OK) return s;
-    // FP32 re-decode of the frames a low-precision pass left unsatisfied,
-    // compacted to the front so that it costs what the failed frames need
-    if (o.fallback_f32 && o.prec != QKDREC_F32) {
-        qkdrec_decode_opts o2 = o;
-        if (o.fallback_f32 == 2) o2.algo = QKDREC_SP_FLOOD;
-        if ((s = pass(o2, QKDREC_F32, conv_out, true)) != QKDREC_OK) return s;
-    }
-    return QKDREC_OK;
+    SyndIn si;
+    si.bytes = synd;
+    return decode_batch_impl(code, llr, si, F, opts, bits_out, iters_out, conv_out, post_out, workspace,
+                             workspace_bytes, stream);
 }
 
 }  // extern "C"

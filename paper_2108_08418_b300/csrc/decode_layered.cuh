@@ -313,7 +313,7 @@ static qkdrec_status launch_layer_qc(DecArgs a, const CodeDev &d, int32_t row, c
     return QKDREC_OK;
 }
 
-qkdrec_status run_layered(const CodeDev &d, const float *llr, const uint8_t *synd, int32_t F,
+qkdrec_status run_layered(const CodeDev &d, const float *llr, const SyndIn &synd, int32_t F,
                           const qkdrec_decode_opts &o, int prec, const uint8_t *conv_prev, bool compact,
                           uint8_t *bits_out, int32_t *iters_out, uint8_t *conv_out, float *post_out,
                           char *ws, cudaStream_t st) {

@@ -1,0 +1,216 @@
+// qkdrec_reconcile: one block of quadrature pairs through the whole reverse
+// slice reconciliation (Sec. II Steps 4-5, Sec. III-A/B): Bob's quantiser and
+// slices, his syndromes, then per slice Alice's soft information from x and her
+// already reconciled lower slices and the BP decode of every sub-block; the
+// reconciled slices leave packed eight bits to a byte.
+#include <algorithm>
+
+#include "common.cuh"
+#include "profile.cuh"
+
+namespace qkd {
+
+__global__ void pack_frames_kernel(const uint8_t *__restrict__ bits, int32_t n, int32_t F, int64_t Wt,
+                                   uint32_t *__restrict__ bitsT);
+__global__ void syndrome_packed_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                       const uint32_t *__restrict__ bitsT, int32_t n, int32_t M, int64_t Wt,
+                                       int64_t W, uint32_t *__restrict__ sbits, unsigned long long *prof);
+
+// Memory a pointer refers to, for the host-or-device arguments.
+static bool device_reachable(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // plain host memory on some drivers: clear the sticky-free error
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct RecLayout {
+    size_t xs, ys, bob, alice, llr, bitsT, sbits, dec, pk, cv, it, total;
+    size_t dec_bytes;
+    int32_t fmax;
+};
+
+static qkdrec_status rec_layout(int64_t count, int32_t m, const qkdrec_decode_opts *opts, const qkdrec_point *pts,
+                                int32_t np, RecLayout &l) {
+    size_t bitsT = 0, sbits = 0, dec = 0;
+    int32_t fmax = 0;
+    for (int32_t p = 0; p < np; ++p) {
+        const int32_t n = pts[p].n;
+        const int64_t F = count / n, W = ceil_div(F, 32);
+        fmax = std::max<int32_t>(fmax, (int32_t)F);
+        bitsT = std::max<size_t>(bitsT, (size_t)W * n * 4);
+        for (int32_t j = 0; j < m; ++j) {
+            const qkdrec_code_t c = pts[p].codes[j];
+            if (!c) continue;
+            size_t b = 0;
+            qkdrec_status s = qkdrec_decode_workspace_size(c, (int32_t)F, opts, &b);
+            if (s != QKDREC_OK) return s;
+            dec = std::max(dec, b);
+            sbits = std::max<size_t>(sbits, (size_t)c->d.M * W * 4);
+        }
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1), 256); return o; };
+    l.xs = take((size_t)count * 4);
+    l.ys = take((size_t)count * 4);
+    l.bob = take((size_t)m * count);
+    l.alice = take((size_t)m * count);
+    l.llr = take((size_t)count * 4);
+    l.bitsT = take(bitsT);
+    l.sbits = take(sbits);
+    l.dec = take(dec);
+    l.dec_bytes = dec;
+    l.pk = take((size_t)m * count / 8);
+    l.cv = take((size_t)m * fmax);
+    l.it = take((size_t)m * fmax * 4);
+    l.total = off;
+    l.fmax = fmax;
+    return QKDREC_OK;
+}
+
+static qkdrec_status rec_check(int64_t count, int32_t m, const qkdrec_decode_opts *opts, const qkdrec_point *pts,
+                               int32_t np) {
+    if (count <= 0 || count % 32) QKD_FAIL(QKDREC_ERR_ARG, "count=%lld must be a positive multiple of 32",
+                                           (long long)count);
+    if (m < 1 || m > 8) QKD_FAIL(QKDREC_ERR_ARG, "m_slices=%d outside [1, 8]", m);
+    if (!opts) QKD_FAIL(QKDREC_ERR_ARG, "opts is NULL");
+    if (np < 1 || !pts) QKD_FAIL(QKDREC_ERR_ARG, "need at least one sub-block length");
+    for (int32_t p = 0; p < np; ++p) {
+        const int32_t n = pts[p].n;
+        if (n <= 0 || n % 32 || count % n)
+            QKD_FAIL(QKDREC_ERR_ARG, "point %d: n=%d must be a positive multiple of 32 dividing count", p, n);
+        if (count / n > (int64_t)65535 * 32) QKD_FAIL(QKDREC_ERR_ARG, "point %d: too many frames", p);
+        if (!pts[p].codes || !pts[p].alice_packed) QKD_FAIL(QKDREC_ERR_ARG, "point %d: codes/alice_packed NULL", p);
+        for (int32_t j = 0; j < m; ++j) {
+            const qkdrec_code_t c = pts[p].codes[j];
+            if (c && c->d.n != n) QKD_FAIL(QKDREC_ERR_ARG, "point %d slice %d: code length %d != n=%d", p, j, c->d.n, n);
+        }
+    }
+    return QKDREC_OK;
+}
+
+// dst (host or device) <- src (device, in the workspace), on the stream
+static qkdrec_status put(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    if (!dst || !bytes) return QKDREC_OK;
+    QKD_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return QKDREC_OK;
+}
+
+}  // namespace qkd
+
+using namespace qkd;
+
+extern "C" {
+
+qkdrec_status qkdrec_reconcile_workspace_size(int64_t count, int32_t m_slices, const qkdrec_decode_opts *opts,
+                                              const qkdrec_point *points, int32_t n_points, size_t *bytes) {
+    clear_error();
+    if (!bytes) QKD_FAIL(QKDREC_ERR_ARG, "bytes is NULL");
+    qkdrec_status s = rec_check(count, m_slices, opts, points, n_points);
+    if (s != QKDREC_OK) return s;
+    RecLayout l;
+    if ((s = rec_layout(count, m_slices, opts, points, n_points, l)) != QKDREC_OK) return s;
+    *bytes = l.total;
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_reconcile(const float *x, const float *y, int64_t count, int32_t m, double lo, double hi,
+                               double sigma_n, qkdrec_label label, const qkdrec_decode_opts *opts,
+                               const qkdrec_point *points, int32_t n_points, uint8_t *bob_packed, void *workspace,
+                               size_t workspace_bytes, void *stream) {
+    clear_error();
+    qkdrec_status s = rec_check(count, m, opts, points, n_points);
+    if (s != QKDREC_OK) return s;
+    if (!x || !y) QKD_FAIL(QKDREC_ERR_ARG, "x/y NULL");
+    if (!(lo < hi) || !(sigma_n > 0)) QKD_FAIL(QKDREC_ERR_ARG, "need lo < hi and sigma_n > 0");
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256)
+        QKD_FAIL(QKDREC_ERR_ARG, "workspace NULL or not 256-byte aligned");
+    RecLayout l;
+    if ((s = rec_layout(count, m, opts, points, n_points, l)) != QKDREC_OK) return s;
+    if (workspace_bytes < l.total)
+        QKD_FAIL(QKDREC_ERR_ARG, "workspace %zu bytes < %zu needed", workspace_bytes, l.total);
+    cudaStream_t st = as_stream(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    // inputs: device memory is read in place, host memory copied in on the stream
+    const float *xd = x, *yd = y;
+    if (!device_reachable(x)) {
+        QKD_CUDA(cudaMemcpyAsync(ws + l.xs, x, (size_t)count * 4, cudaMemcpyHostToDevice, st));
+        xd = reinterpret_cast<const float *>(ws + l.xs);
+    }
+    if (!device_reachable(y)) {
+        QKD_CUDA(cudaMemcpyAsync(ws + l.ys, y, (size_t)count * 4, cudaMemcpyHostToDevice, st));
+        yd = reinterpret_cast<const float *>(ws + l.ys);
+    }
+    uint8_t *bob = reinterpret_cast<uint8_t *>(ws + l.bob), *alice = reinterpret_cast<uint8_t *>(ws + l.alice);
+    float *llr = reinterpret_cast<float *>(ws + l.llr);
+    uint32_t *bitsT = reinterpret_cast<uint32_t *>(ws + l.bitsT), *sbits = reinterpret_cast<uint32_t *>(ws + l.sbits);
+    uint8_t *pk = reinterpret_cast<uint8_t *>(ws + l.pk), *cv = reinterpret_cast<uint8_t *>(ws + l.cv);
+    int32_t *it = reinterpret_cast<int32_t *>(ws + l.it);
+    // Bob: quantiser and bit slices (Sec. III-B steps 1-2)
+    if ((s = qkdrec_quantise_slices(yd, count, m, lo, hi, label, nullptr, bob, stream)) != QKDREC_OK) return s;
+    const int64_t plane8 = count / 8;
+    if (bob_packed) {
+        const bool dev = device_reachable(bob_packed);
+        for (int32_t j = 0; j < m; ++j)
+            if ((s = qkdrec_pack_bits(bob + (size_t)j * count, count, dev ? bob_packed + j * plane8 : pk + j * plane8,
+                                      stream)) != QKDREC_OK)
+                return s;
+        if (!dev && (s = put(bob_packed, pk, (size_t)m * plane8, st)) != QKDREC_OK) return s;
+    }
+    for (int32_t p = 0; p < n_points; ++p) {
+        const qkdrec_point &pt = points[p];
+        const int32_t n = pt.n, F = (int32_t)(count / n);
+        const int64_t W = ceil_div(F, 32);
+        const bool dev_a = device_reachable(pt.alice_packed);
+        const bool dev_c = !pt.converged || device_reachable(pt.converged);
+        const bool dev_i = !pt.iters || device_reachable(pt.iters);
+        uint8_t *cv_out = pt.converged && dev_c ? pt.converged : cv;
+        int32_t *it_out = pt.iters && dev_i ? pt.iters : it;
+        for (int32_t j = 0; j < m; ++j) {
+            const qkdrec_code_t c = pt.codes[j];
+            uint8_t *aj = alice + (size_t)j * count;
+            if (!c) {
+                // disclosed slice (rate 0): Bob's bits are sent in the clear
+                QKD_CUDA(cudaMemcpyAsync(aj, bob + (size_t)j * count, (size_t)count, cudaMemcpyDeviceToDevice, st));
+                QKD_CUDA(cudaMemsetAsync(cv_out + (size_t)j * F, 1, (size_t)F, st));
+                QKD_CUDA(cudaMemsetAsync(it_out + (size_t)j * F, 0, (size_t)F * 4, st));
+                continue;
+            }
+            const CodeDev &d = c->d;
+            {
+                // Bob's syndromes of slice j, 32 frames to a word (Sec. II Step 5)
+                prof::Scope ps(prof::kSyndrome, st);
+                const int64_t tasks = W * (n / 16);
+                pack_frames_kernel<<<(unsigned)std::min<int64_t>(ceil_div(tasks * 32, 256), (int64_t)sm_count() * 32),
+                                     256, 0, st>>>(bob + (size_t)j * count, n, F, W, bitsT);
+                QKD_LAUNCHED("pack_frames_kernel");
+                dim3 g((unsigned)ceil_div(d.M, 256), (unsigned)std::min<int64_t>(W, 65535));
+                syndrome_packed_kernel<<<g, 256, 0, st>>>(d.rp, d.ci, bitsT, n, d.M, W, W, sbits,
+                                                          prof::counters(prof::kSyndrome));
+                QKD_LAUNCHED("syndrome_packed_kernel");
+            }
+            // Alice: soft information of slice j from x and her reconciled lower slices
+            if ((s = qkdrec_slice_llr(xd, count, m, j, lo, hi, sigma_n, label, j ? alice : nullptr, llr, stream)) !=
+                QKDREC_OK)
+                return s;
+            SyndIn si;
+            si.packed = sbits;
+            si.W = W;
+            if ((s = decode_batch_impl(c, llr, si, F, opts, aj, it_out + (size_t)j * F, cv_out + (size_t)j * F,
+                                       nullptr, ws + l.dec, l.dec_bytes, stream)) != QKDREC_OK)
+                return s;
+        }
+        for (int32_t j = 0; j < m; ++j)
+            if ((s = qkdrec_pack_bits(alice + (size_t)j * count, count,
+                                      dev_a ? pt.alice_packed + j * plane8 : pk + j * plane8, stream)) != QKDREC_OK)
+                return s;
+        if (!dev_a && (s = put(pt.alice_packed, pk, (size_t)m * plane8, st)) != QKDREC_OK) return s;
+        if (pt.converged && !dev_c && (s = put(pt.converged, cv, (size_t)m * F, st)) != QKDREC_OK) return s;
+        if (pt.iters && !dev_i && (s = put(pt.iters, it, (size_t)m * F * 4, st)) != QKDREC_OK) return s;
+    }
+    return QKDREC_OK;
+}
+
+}  // extern "C"
