@@ -21,6 +21,15 @@ extern "C" {
  */
 qkdrec_status qkdrec_selftest_phi(const float *x, int64_t count, float *out, void *stream);
 
+/*
+ * The same function as the two-frames-per-lane sum-product check kernel
+ * evaluates it (pairs of values in packed FP32x2 arithmetic):
+ * out[i] = phi(clamp(|x[i]|, 1e-30, 30)).
+ *   x, out  DEVICE float [count], 8-byte aligned; count even.
+ * Errors: QKDREC_ERR_ARG (count odd or < 0, NULL, misaligned).
+ */
+qkdrec_status qkdrec_selftest_phi_pair(const float *x, int64_t count, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,7 @@ EXPORTED = [
     "qkdrec_quantiser_range", "qkdrec_reconcile", "qkdrec_reconcile_workspace_size", "qkdrec_pack_bits",
     "qkdrec_unpack_bits",
 ]
-SELFTEST = ["qkdrec_selftest_phi"]
+SELFTEST = ["qkdrec_selftest_phi", "qkdrec_selftest_phi_pair"]
 
 
 class QkdrecError(RuntimeError):
@@ -136,6 +136,7 @@ def lib():
         "qkdrec_plan_autotune": (U, [P, P, ctypes.c_size_t, I32, P, P, P]),
         "qkdrec_profile_begin": (U, []),
         "qkdrec_selftest_phi": (U, [P, I64, P, P]),
+        "qkdrec_selftest_phi_pair": (U, [P, I64, P, P]),
         "qkdrec_profile_end": (U, [P, I32, P]),
         "qkdrec_last_error": (ctypes.c_char_p, []),
         "qkdrec_version": (ctypes.c_char_p, []),
@@ -725,4 +726,14 @@ def qkdrec_selftest_phi(x):
     xp = _dev(x, torch.float32, "x")
     out = torch.empty_like(x)
     _check(lib().qkdrec_selftest_phi(xp, x.numel(), ctypes.c_void_p(out.data_ptr()), _stream(x)))
+    return out
+
+
+def qkdrec_selftest_phi_pair(x):
+    """phi(clamp(|x|)) evaluated by the two-frames-per-lane sum-product kernel's function
+    (x: float32 CUDA tensor of even length)."""
+    torch = _torch()
+    xp = _dev(x, torch.float32, "x")
+    out = torch.empty_like(x)
+    _check(lib().qkdrec_selftest_phi_pair(xp, x.numel(), ctypes.c_void_p(out.data_ptr()), _stream(x)))
     return out

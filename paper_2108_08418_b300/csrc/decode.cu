@@ -260,6 +260,7 @@ __device__ __forceinline__ void publish_unsat(uint32_t bits, int64_t f0, int64_t
 // computes and stores the outgoing messages.  Otherwise pass 2 reads the
 // posteriors and old messages again.
 constexpr int kStash = 32;
+constexpr int kSp2Chunk = 2;     // edge loads in flight per lane in check_flood_sp2
 
 template <int ALGO, typename MsgT, int V, bool CACHED>
 __global__ void __launch_bounds__(kCheckWarps * 32, (ALGO == kSP && V == 1) ? 8 : (ALGO == kOMS && V == 4 ? 4 : 3))
@@ -403,6 +404,145 @@ check_flood_f(DecArgs a) {
     }
     // messages read + written and the posterior gathered, per active edge-frame
     prof_add(a.prof, units, units * (a.do_msgs ? 2 * sizeof(MsgT) + 4 : 4));
+}
+
+// ------------------------------ sum-product check kernel, two frames per lane
+// phi of two values at once: the polynomial and product steps in packed FP32x2
+// arithmetic (one instruction for both), the MUFU approximations per value.
+// The same identities as phi_fast, with the small-argument range folded into
+// the logarithmic one: below 0.1, 1 - e^-x is formed from its series
+// x (1 - x/2 + x^2/6 - x^3/24 + x^4/120) (relative truncation < 1.4e-8), so
+//   x >= 2 : phi = 2u (1 + u^2/3 + u^4/5 + u^6/7),  u = e^-x,
+//   x <  2 : phi = ln((1 + u) / (1 - u)).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 phi2(float2 x) {
+    const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+    const float2 t = __fmul2_rn(x, f2(-kLog2e));
+    const float2 u = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+    const float2 u2 = __fmul2_rn(u, u);
+    float2 p = __ffma2_rn(u2, f2(1.0f / 7.0f), f2(0.2f));
+    p = __ffma2_rn(u2, p, f2(1.0f / 3.0f));
+    p = __ffma2_rn(u2, p, f2(1.0f));
+    const float2 big = __fmul2_rn(__fadd2_rn(u, u), p);
+    float2 sr = __ffma2_rn(x, f2(1.0f / 120.0f), f2(-1.0f / 24.0f));
+    sr = __ffma2_rn(x, sr, f2(1.0f / 6.0f));
+    sr = __ffma2_rn(x, sr, f2(-0.5f));
+    sr = __ffma2_rn(x, sr, f2(1.0f));
+    const float2 dser = __fmul2_rn(x, sr);
+    const float2 dsub = __ffma2_rn(u, f2(-1.0f), f2(1.0f));
+    const float2 r = make_float2(rcp_approx(x.x < 0.1f ? dser.x : dsub.x), rcp_approx(x.y < 0.1f ? dser.y : dsub.y));
+    const float2 ar = __ffma2_rn(u, r, r);                       // (1 + u) / (1 - u)
+    const float2 mid = __fmul2_rn(make_float2(lg2_approx(ar.x), lg2_approx(ar.y)), f2(kLn2));
+    return make_float2(x.x >= 2.0f ? big.x : mid.x, x.y >= 2.0f ? big.y : mid.y);
+}
+__device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
+
+// The sum-product check update of check_flood_f<kSP, float, 1, true> on the
+// same 32-frame-block layout, with each lane holding two frames of a block:
+// half-warp h serves listed block 2 b + h, lane l of it frames 2l, 2l + 1, so a
+// warp moves one 8-byte value per lane per edge and shares the edge's column
+// index and address arithmetic between two frames.  Per check and frame, pass 1
+// keeps sum-except-largest and largest of phi(|q|) in the form
+//   acc0 += min(f, acc1),  acc1 = max(f, acc1)
+// (no argmax: for the largest edge acc0 + (acc1 - f) = acc0 exactly), and
+// stashes phi(|q|) carrying the sign of q in shared memory; the signs, the
+// hard decisions' parity and the syndrome are XORs of whole words.  Posteriors
+// are made +0.0 for -0.0 first (L + 0), so a sign bit is a hard decision and
+// q = L - m (never -0.0 then) carries sgn(0) = +1.
+template <int CH>
+__global__ void __launch_bounds__(kCheckWarps * 32, 5)
+check_flood_sp2(DecArgs a) {
+    extern __shared__ float2 stash2[];   // [kCheckWarps][dstash][32]
+    __shared__ uint32_t blkw[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = lane >> 4, hl = lane & 15;
+    const float *L = reinterpret_cast<const float *>(a.L);
+    float *msg = reinterpret_cast<float *>(a.msg);
+    constexpr int LG = 5;
+    float2 *my = stash2 + (warp * a.dstash) * 32 + lane;
+    unsigned long long units = 0;
+    const int32_t nblk = *a.blk_n;
+    const int64_t c0 = ((int64_t)blockIdx.x * kCheckWarps + warp) * kChecksPerWarp;
+    for (int32_t bp = blockIdx.y; 2 * bp < nblk; bp += gridDim.y) {
+        const int32_t bi = 2 * bp + half;
+        const int64_t fb = bi < nblk ? __ldg(a.blk + bi) : -1;
+        const int64_t f0 = (fb << LG) + 2 * hl;
+        uint32_t act = 0;
+        if (fb >= 0) {
+            const uint32_t w = *reinterpret_cast<const uint16_t *>(a.active + f0);
+            act = (w & 1u) | ((w >> 7) & 2u);
+        }
+        uint32_t unsat_bits = 0;
+        if (act) {
+            const int nact = __popc(act);
+            const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);
+            for (int it = 0; it < kChecksPerWarp; ++it) {
+                const int64_t c = c0 + it;
+                if (c >= a.M) break;
+                const int32_t beg = __ldg(a.rp + c), d = __ldg(a.rp + c + 1) - beg;
+                const uint32_t s = (__ldg(a.sbits + c * a.W + (f0 >> 5)) >> (f0 & 31)) & 3u;
+                uint32_t px = 0, py = 0, sx = 0, sy = 0;     // xor of L words, of q words
+                float2 acc0 = f2(0.0f), acc1 = f2(0.0f);
+                units += (unsigned long long)d * nact;
+                for (int k0 = 0; k0 < d; k0 += CH) {
+                    float2 Lv[CH], mo[CH];
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        const int32_t e = beg + min(k0 + j, d - 1);
+                        const int32_t col = __ldg(a.ci + e);
+                        Lv[j] = __ldg(reinterpret_cast<const float2 *>(L + bL + ((uint32_t)col << LG)));
+                        mo[j] = __ldcs(reinterpret_cast<const float2 *>(msg + bM + ((uint32_t)e << LG)));
+                    }
+#pragma unroll
+                    for (int j = 0; j < CH; ++j) {
+                        const int k = k0 + j;
+                        if (k >= d) break;
+                        const float2 Lc = __fadd2_rn(Lv[j], f2(0.0f));
+                        px ^= fbits(Lc.x);
+                        py ^= fbits(Lc.y);
+                        const float2 q = __ffma2_rn(mo[j], f2(-1.0f), Lc);
+                        sx ^= fbits(q.x);
+                        sy ^= fbits(q.y);
+                        const float2 aq = make_float2(fmaxf(fminf(fabsf(q.x), kAMax), kAMin),
+                                                      fmaxf(fminf(fabsf(q.y), kAMax), kAMin));
+                        const float2 f = phi2(aq);
+                        my[k * 32] = make_float2(__uint_as_float(fbits(f.x) | (fbits(q.x) & 0x80000000u)),
+                                                 __uint_as_float(fbits(f.y) | (fbits(q.y) & 0x80000000u)));
+                        acc0 = __fadd2_rn(acc0, make_float2(fminf(f.x, acc1.x), fminf(f.y, acc1.y)));
+                        acc1 = make_float2(fmaxf(f.x, acc1.x), fmaxf(f.y, acc1.y));
+                    }
+                }
+                unsat_bits |= (s ^ (px >> 31) ^ ((py >> 30) & 2u)) & act;
+                // syndrome xor the signs of all q, in the sign bit of each frame's word
+                const uint32_t nx = (s << 31) ^ sx, ny = ((s & 2u) << 30) ^ sy;
+                for (int k = 0; k < d; ++k) {
+                    const float2 fs = my[k * 32];
+                    const float2 f = make_float2(fabsf(fs.x), fabsf(fs.y));
+                    const float2 ex = __fadd2_rn(acc0, __ffma2_rn(f, f2(-1.0f), acc1));
+                    const float2 mg = phi2(make_float2(fminf(ex.x, kAMax), fminf(ex.y, kAMax)));
+                    const float2 mn = make_float2(__uint_as_float(fbits(mg.x) | ((fbits(fs.x) ^ nx) & 0x80000000u)),
+                                                  __uint_as_float(fbits(mg.y) | ((fbits(fs.y) ^ ny) & 0x80000000u)));
+                    __stcs(reinterpret_cast<float2 *>(msg + bM + ((uint32_t)(beg + k) << LG)), mn);
+                }
+            }
+        }
+        if (a.early_stop) {
+            // merge the stopping-test bits of each half-warp's block, then one
+            // global atomic per block
+            uint32_t v = unsat_bits << (2 * hl);
+            for (int o = 8; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+            if (threadIdx.x < 2) blkw[threadIdx.x] = 0;
+            __syncthreads();
+            if (hl == 0 && v) atomicOr(&blkw[half], v);
+            __syncthreads();
+            if (threadIdx.x < 2 && blkw[threadIdx.x]) {
+                const int32_t bj = 2 * bp + (int32_t)threadIdx.x;
+                atomicOr(&a.unsat_cur[__ldg(a.blk + bj)], blkw[threadIdx.x]);
+            }
+            __syncthreads();
+        }
+    }
+    prof_add(a.prof, units, units * 12);
 }
 
 // ----------------------------------------------------- integer check kernel
@@ -1318,7 +1458,21 @@ static void launch_check(DecArgs a, const CodeDev &d, int algo, int prec, cudaSt
         else check_flood_i<4, 0><<<g.grid, B, 0, st>>>(a);
     } else if (algo == QKDREC_SP_FLOOD) {
         if (prec == kF32) {
-            if (V == 1) check_flood_f<kSP, float, 1, true><<<g.grid, B, stash, st>>>(a);
+            if (V == 1 && a.do_msgs && g.fvw == 32) {
+                // two frames per lane, half-warps on two listed blocks
+                const size_t stash2 = (size_t)kCheckWarps * a.dstash * 32 * sizeof(float2);
+                static bool attr_set[64] = {false};   // per device
+                int dev = 0;
+                cudaGetDevice(&dev);
+                if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+                    cudaFuncSetAttribute(check_flood_sp2<kSp2Chunk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)kCheckWarps * kStash * 32 * sizeof(float2)));
+                    attr_set[dev] = true;
+                }
+                dim3 g2 = g.grid;
+                g2.y = (g2.y + 1) / 2;
+                check_flood_sp2<kSp2Chunk><<<g2, B, stash2, st>>>(a);
+            } else if (V == 1) check_flood_f<kSP, float, 1, true><<<g.grid, B, stash, st>>>(a);
             else check_flood_f<kSP, float, 4, false><<<g.grid, B, 0, st>>>(a);
         } else {
             if (V == 1) check_flood_f<kSP, __half, 1, true><<<g.grid, B, stash, st>>>(a);
@@ -1405,6 +1559,14 @@ __global__ void phi_selftest_kernel(const float *__restrict__ x, int64_t count, 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = phi_clamped(x[i]);
 }
+// phi2 on consecutive pairs, clamped as the two-frame kernel clamps |q|
+__global__ void phi_pair_selftest_kernel(const float *__restrict__ x, int64_t pairs, float *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = reinterpret_cast<const float2 *>(x)[i];
+        reinterpret_cast<float2 *>(out)[i] = phi2(make_float2(fmaxf(fminf(fabsf(v.x), kAMax), kAMin),
+                                                              fmaxf(fminf(fabsf(v.y), kAMax), kAMin)));
+    }
+}
 
 qkdrec_status decode_batch_impl(qkdrec_code_t code, const float *llr, const SyndIn &synd, int32_t F,
                                 const qkdrec_decode_opts *opts, uint8_t *bits_out, int32_t *iters_out,
@@ -1462,6 +1624,19 @@ qkdrec_status qkdrec_selftest_phi(const float *x, int64_t count, float *out, voi
     phi_selftest_kernel<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 4096), 256, 0, as_stream(stream)>>>(
         x, count, out);
     QKD_LAUNCHED("phi_selftest_kernel");
+    return QKDREC_OK;
+}
+
+qkdrec_status qkdrec_selftest_phi_pair(const float *x, int64_t count, float *out, void *stream) {
+    clear_error();
+    if (count < 0 || count % 2) QKD_FAIL(QKDREC_ERR_ARG, "count must be even and >= 0");
+    if (count == 0) return QKDREC_OK;
+    if (!x || !out) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(x) % 8 || reinterpret_cast<uintptr_t>(out) % 8)
+        QKD_FAIL(QKDREC_ERR_ARG, "x/out must be 8-byte aligned");
+    phi_pair_selftest_kernel<<<(unsigned)std::min<int64_t>(ceil_div(count / 2, 256), 4096), 256, 0,
+                               as_stream(stream)>>>(x, count / 2, out);
+    QKD_LAUNCHED("phi_pair_selftest_kernel");
     return QKDREC_OK;
 }
 

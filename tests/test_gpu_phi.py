@@ -28,6 +28,20 @@ def test_phi_relative_error():
     assert rel.max() < 4e-6
 
 
+def test_phi_pair_relative_error():
+    """The packed two-value form used by the two-frames-per-lane kernel: same bound."""
+    from paper_2108_08418_b300 import build
+    build.build()
+    x = np.concatenate([np.logspace(-30, np.log10(30.0), 200_000),
+                        np.linspace(0.0, 4.0, 100_000), np.linspace(0.09, 0.11, 10_000),
+                        np.array([0.0, 1e-38, 0.1, 2.0, 30.0, 31.0, 1e30, -2.5])]).astype(np.float32)
+    got = q.qkdrec_selftest_phi_pair(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    ref = phi64(np.abs(x.astype(np.float64)))
+    rel = np.abs(got - ref) / ref
+    print("max relative error of the pair phi:", rel.max())
+    assert rel.max() < 4e-6
+
+
 def test_phi_is_an_involution():
     x = np.logspace(-6, np.log10(25.0), 10_001).astype(np.float32)
     d = torch.from_numpy(x).cuda()
