@@ -260,7 +260,13 @@ __device__ __forceinline__ void publish_unsat(uint32_t bits, int64_t f0, int64_t
 // computes and stores the outgoing messages.  Otherwise pass 2 reads the
 // posteriors and old messages again.
 constexpr int kStash = 32;
-constexpr int kSp2Chunk = 2;     // edge loads in flight per lane in check_flood_sp2
+// check_flood_sp2: edges per load chunk, and the next chunk's loads issued
+// before the current chunk is processed.  Measured on the n = 2^16, 512-frame
+// case (B300, 5 iterations): 0.339 ms per launch with chunks of 2 and no
+// prefetch at 5 blocks per SM; 0.259 ms with chunks of 4 and prefetch at 4
+// blocks per SM (64 registers); chunks of 3 the same, 6 or 8 at 3 blocks slower.
+constexpr int kSp2Chunk = 4;
+constexpr bool kSp2Prefetch = true;
 
 template <int ALGO, typename MsgT, int V, bool CACHED>
 __global__ void __launch_bounds__(kCheckWarps * 32, (ALGO == kSP && V == 1) ? 8 : (ALGO == kOMS && V == 4 ? 4 : 3))
@@ -450,7 +456,7 @@ __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); 
 // are made +0.0 for -0.0 first (L + 0), so a sign bit is a hard decision and
 // q = L - m (never -0.0 then) carries sgn(0) = +1.
 template <int CH>
-__global__ void __launch_bounds__(kCheckWarps * 32, 5)
+__global__ void __launch_bounds__(kCheckWarps * 32, 4)
 check_flood_sp2(DecArgs a) {
     extern __shared__ float2 stash2[];   // [kCheckWarps][dstash][32]
     __shared__ uint32_t blkw[2];
@@ -484,8 +490,8 @@ check_flood_sp2(DecArgs a) {
                 uint32_t px = 0, py = 0, sx = 0, sy = 0;     // xor of L words, of q words
                 float2 acc0 = f2(0.0f), acc1 = f2(0.0f);
                 units += (unsigned long long)d * nact;
-                for (int k0 = 0; k0 < d; k0 += CH) {
-                    float2 Lv[CH], mo[CH];
+                float2 Lv[CH], mo[CH];
+                auto fetch = [&](int k0) {
 #pragma unroll
                     for (int j = 0; j < CH; ++j) {
                         const int32_t e = beg + min(k0 + j, d - 1);
@@ -493,14 +499,28 @@ check_flood_sp2(DecArgs a) {
                         Lv[j] = __ldg(reinterpret_cast<const float2 *>(L + bL + ((uint32_t)col << LG)));
                         mo[j] = __ldcs(reinterpret_cast<const float2 *>(msg + bM + ((uint32_t)e << LG)));
                     }
+                };
+                if (kSp2Prefetch) fetch(0);
+                for (int k0 = 0; k0 < d; k0 += CH) {
+                    float2 Lc2[CH], mc2[CH];
+                    if (kSp2Prefetch) {
+                        // the next chunk's loads go out before this chunk is processed
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) { Lc2[j] = Lv[j]; mc2[j] = mo[j]; }
+                        if (k0 + CH < d) fetch(k0 + CH);
+                    } else {
+                        fetch(k0);
+#pragma unroll
+                        for (int j = 0; j < CH; ++j) { Lc2[j] = Lv[j]; mc2[j] = mo[j]; }
+                    }
 #pragma unroll
                     for (int j = 0; j < CH; ++j) {
                         const int k = k0 + j;
                         if (k >= d) break;
-                        const float2 Lc = __fadd2_rn(Lv[j], f2(0.0f));
+                        const float2 Lc = __fadd2_rn(Lc2[j], f2(0.0f));
                         px ^= fbits(Lc.x);
                         py ^= fbits(Lc.y);
-                        const float2 q = __ffma2_rn(mo[j], f2(-1.0f), Lc);
+                        const float2 q = __ffma2_rn(mc2[j], f2(-1.0f), Lc);
                         sx ^= fbits(q.x);
                         sy ^= fbits(q.y);
                         const float2 aq = make_float2(fmaxf(fminf(fabsf(q.x), kAMax), kAMin),
@@ -939,22 +959,26 @@ __global__ void __launch_bounds__(256) var_flood_i8x16(DecArgs a) {
     prof_add(a.prof, units, bytes);
 }
 
-// FP16-message flooding, variable side, 8 frames per thread: thread (listed
-// frame block on y, (variable, group of 8 frames) on x).  The same sums, in
-// the same (ascending edge) order, as var_flood<kF16>.
-__global__ void __launch_bounds__(256) var_flood_f16x8(DecArgs a) {
-    constexpr int LG = lgfb_of<4>();                   // 128-frame blocks: 16 groups of 8
-    const int64_t items = (int64_t)a.n * 16;
+// Float-posterior flooding, variable side, 8 frames per thread: thread (listed
+// frame block on y, (variable, group of 8 frames) on x) on a layout of 2^LG-frame
+// blocks.  The same sums, in the same (ascending edge) order, as var_flood
+// (FP32 accumulation of FP32 or FP16 messages); the edge indices of a chunk of
+// four edges are loaded together, then their messages, so a variable of degree
+// 3 is one round trip of index loads and one of message loads.
+template <typename MsgT, int LG>
+__global__ void __launch_bounds__(256) var_flood_x8(DecArgs a) {
+    constexpr int G = (1 << LG) / 8;                   // groups of 8 frames per block
+    const int64_t items = (int64_t)a.n * G;
     float *L = reinterpret_cast<float *>(a.L);
     const float *llr = reinterpret_cast<const float *>(a.llr_i);
-    const __half *msg = reinterpret_cast<const __half *>(a.msg);
+    const MsgT *msg = reinterpret_cast<const MsgT *>(a.msg);
     unsigned long long units = 0, bytes = 0;
     const int32_t nblk = *a.blk_n;
     for (int32_t bi = blockIdx.y; bi < nblk; bi += gridDim.y) {
         const int64_t fb = __ldg(a.blk + bi);
         for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
              idx += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t v = idx >> 4, f0 = (fb << LG) + ((idx & 15) << 3);
+            const int64_t v = idx / G, f0 = (fb << LG) + ((idx % G) << 3);
             const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);
             if (v == 0 && (f0 & 31) == 0 && a.early_stop) a.unsat_next[f0 >> 5] = 0;   // next test starts clear
             const uint2 aw = *reinterpret_cast<const uint2 *>(a.active + f0);
@@ -975,7 +999,7 @@ __global__ void __launch_bounds__(256) var_flood_f16x8(DecArgs a) {
             const int64_t pv = bL + (v << LG);
             const unsigned nu = __popc(upd);
             units += nu;
-            bytes += (unsigned long long)nu * ((ve - vb) * 2 + 4 + 4);
+            bytes += (unsigned long long)nu * ((ve - vb) * sizeof(MsgT) + 4 + 4);
             float acc[8];
             {
                 const float4 c0 = __ldg(reinterpret_cast<const float4 *>(llr + pv));
@@ -983,24 +1007,34 @@ __global__ void __launch_bounds__(256) var_flood_f16x8(DecArgs a) {
                 acc[0] = c0.x; acc[1] = c0.y; acc[2] = c0.z; acc[3] = c0.w;
                 acc[4] = c1.x; acc[5] = c1.y; acc[6] = c1.z; acc[7] = c1.w;
             }
-            // edges in chunks of four: index loads, then message loads, issued together
             for (int32_t k0 = vb; k0 < ve; k0 += 4) {
                 int32_t e[4];
-                uint4 m[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) e[j] = __ldg(a.vedge + min(k0 + j, ve - 1));
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (k0 + j < ve) m[j] = __ldcs(reinterpret_cast<const uint4 *>(msg + bM + ((int64_t)e[j] << LG)));
+                float m[4][8];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (k0 + j >= ve) break;
-                    const uint32_t mw[4] = {m[j].x, m[j].y, m[j].z, m[j].w};
-                    for (int w = 0; w < 4; ++w) {
-                        const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&mw[w]));
-                        acc[2 * w] += h.x;
-                        acc[2 * w + 1] += h.y;
+                    const MsgT *mp = msg + bM + ((int64_t)e[j] << LG);
+                    if (sizeof(MsgT) == 2) {
+                        const uint4 h = __ldcs(reinterpret_cast<const uint4 *>(mp));
+                        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+                        for (int w = 0; w < 4; ++w) {
+                            const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(&hw[w]));
+                            m[j][2 * w] = t.x;
+                            m[j][2 * w + 1] = t.y;
+                        }
+                    } else {
+                        const float4 m0 = __ldcs(reinterpret_cast<const float4 *>(mp));
+                        const float4 m1 = __ldcs(reinterpret_cast<const float4 *>(mp) + 1);
+                        m[j][0] = m0.x; m[j][1] = m0.y; m[j][2] = m0.z; m[j][3] = m0.w;
+                        m[j][4] = m1.x; m[j][5] = m1.y; m[j][6] = m1.z; m[j][7] = m1.w;
                     }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (k0 + j >= ve) break;
+                    for (int i = 0; i < 8; ++i) acc[i] += m[j][i];
                 }
             }
             float4 *dst = reinterpret_cast<float4 *>(L + pv);
@@ -1506,8 +1540,9 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
     // integer form: (variable, 16 frames) on x, listed frame blocks on y; FP16
     // messages: (variable, 8 frames)
     const bool i16 = prec == kI8 && l.lgfb == lgfb_of<4>() && d.dv_max <= 1000;
-    const bool h8 = prec == kF16 && l.lgfb == lgfb_of<4>();
-    dim3 igrid((unsigned)std::min<int64_t>(ceil_div((int64_t)d.n * (h8 ? 16 : 8), 256), (int64_t)sm_count() * 64), 1);
+    const bool x8 = prec != kI8;     // 8 frames per thread, 32- or 128-frame blocks
+    const int groups = x8 ? (1 << l.lgfb) / 8 : 8;
+    dim3 igrid((unsigned)std::min<int64_t>(ceil_div((int64_t)d.n * groups, 256), (int64_t)sm_count() * 64), 1);
     igrid.y = (unsigned)std::max<int64_t>(1, std::min<int64_t>(l.Fp >> l.lgfb, (int64_t)sm_count() * 64 / igrid.x));
 
     auto check = [&](int t, int do_msgs) {
@@ -1532,10 +1567,14 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
             a.prof = prof::counters(kind);
             prof::Scope ps(kind, st);
             if (i16) var_flood_i8x16<<<igrid, 256, 0, st>>>(a);
-            else if (h8) var_flood_f16x8<<<igrid, 256, 0, st>>>(a);
             else if (prec == kI8) var_flood<kI8><<<vgrid, 256, 0, st>>>(a);
-            else if (prec == kF16) var_flood<kF16><<<vgrid, 256, 0, st>>>(a);
-            else var_flood<kF32><<<vgrid, 256, 0, st>>>(a);
+            else if (l.lgfb == lgfb_of<1>()) {
+                if (prec == kF16) var_flood_x8<__half, lgfb_of<1>()><<<igrid, 256, 0, st>>>(a);
+                else var_flood_x8<float, lgfb_of<1>()><<<igrid, 256, 0, st>>>(a);
+            } else {
+                if (prec == kF16) var_flood_x8<__half, lgfb_of<4>()><<<igrid, 256, 0, st>>>(a);
+                else var_flood_x8<float, lgfb_of<4>()><<<igrid, 256, 0, st>>>(a);
+            }
         }
         QKD_LAUNCHED("var_flood");
         if (o.early_stop) {
