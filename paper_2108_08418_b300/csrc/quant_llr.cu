@@ -53,10 +53,32 @@ struct __align__(8) LlrParams {
     double td[kMaxK + 1];    // the same thresholds in FP64
     float tf[kMaxK + 1];     // t_0 .. t_K as floats (t_0 = -inf, t_K = +inf)
     uint8_t k_of_label[kMaxK];
+    // the candidates of each lower-bit pattern `low` in increasing interval
+    // order, cand[low nc + i] (nc = K >> j), and bit j of each interval's label
+    uint8_t cand[kMaxK];
+    uint8_t bitj[kMaxK];
     float inv_sigma;
     double inv_sigma_d;
+    float ln_h;              // ln of the interval width in units of sigma_n
+    float ln_half_n;         // ln (nc / 2): candidates per set
     int32_t m, K, j;
 };
+
+// The derived tables of p from k_of_label, m, K, j, the quantiser step delta
+// and inv_sigma (host side; the per-frame kernel fills the same fields itself).
+static void llr_tables(LlrParams &p, double delta) {
+    const int nc = p.K >> p.j, lowmask = (1 << p.j) - 1;
+    int fill[kMaxK] = {0};
+    uint8_t lab_of_k[kMaxK];
+    for (int l = 0; l < p.K; ++l) lab_of_k[p.k_of_label[l]] = (uint8_t)l;
+    for (int k = 0; k < p.K; ++k) {
+        const int low = lab_of_k[k] & lowmask;
+        p.cand[low * nc + fill[low]++] = (uint8_t)k;
+        p.bitj[k] = (uint8_t)((lab_of_k[k] >> p.j) & 1);
+    }
+    p.ln_h = (float)log(delta * p.inv_sigma_d);
+    p.ln_half_n = (float)log(0.5 * nc);
+}
 
 constexpr float kSkipNats = 25.0f;   // terms below e^-25 of the set's nearest term are dropped
 constexpr float kSkipLinNats = 16.0f;  // same, in the linear-domain sums (<= 2^m e^-16 relative)
@@ -122,44 +144,64 @@ __device__ __forceinline__ double lp_interval64(const LlrParams &p, int k, doubl
     return logp64((p.td[k] - x) * p.inv_sigma_d, (p.td[k + 1] - x) * p.inv_sigma_d);
 }
 
+// Upper tail Q(|z|) = erfc(|z| / sqrt 2) / 2 at a standardised threshold.
+__device__ __forceinline__ float tail_q(float z) { return 0.5f * erfcf(fabsf(z) * 0.70710678118654752f); }
+// P(k | x) from the tails at its two bounds a < b (the same values p_lin32 forms):
+// beside x above, T(a) - T(b); below, T(b) - T(a); containing x, 1 - T(a) - T(b).
+__device__ __forceinline__ float p_from_tails(float a, float b, float Ta, float Tb) {
+    return a >= 0.0f ? Ta - Tb : (b <= 0.0f ? Tb - Ta : 1.0f - Ta - Tb);
+}
+
 // LLR of one sample (x, reconciled lower bits `low`) with the tables of p.
 __device__ __forceinline__ float llr_one(const LlrParams &p, float x, int low) {
     const int nc = p.K >> p.j;  // candidates consistent with the lower bits
-    const float lg_half_n = logf(0.5f * (float)nc);   // log |K_b|
+    const uint8_t *cl = p.cand + low * nc;
     // nearest candidate of each set
     float dmin[2] = {INFINITY, INFINITY};
     int kmin[2] = {0, 0};
-    for (int u = 0; u < nc; ++u) {
-        const int k = p.k_of_label[(u << p.j) | low];
+    for (int i = 0; i < nc; ++i) {
+        const int k = cl[i];
         const float d = interval_dist(p, k, x);
-        const int b = u & 1;
+        const int b = p.bitj[k];
         if (d < dmin[b]) { dmin[b] = d; kmin[b] = k; }
     }
+    // bounds on each set's total: above, |K_b| x the largest term's bound
+    // (Q(d) <= e^{-d^2/2} / 2 beside x, 1 inside); below, the nearest term alone,
+    // which holds a strip of width h at most d + h from x: P >= h phi(d + h)
+    const float h = __expf(p.ln_h);
+    const float ub0 = p.ln_half_n + (dmin[0] > 0.0f ? kLn05 - 0.5f * dmin[0] * dmin[0] : 0.0f);
+    const float ub1 = p.ln_half_n + (dmin[1] > 0.0f ? kLn05 - 0.5f * dmin[1] * dmin[1] : 0.0f);
+    const float lb0 = p.ln_h - 0.5f * (dmin[0] + h) * (dmin[0] + h) - 0.91893853f;
+    const float lb1 = p.ln_h - 0.5f * (dmin[1] + h) * (dmin[1] + h) - 0.91893853f;
+    // a set whose whole mass is provably more than the clip below the other's
+    // cannot move the clipped result
+    if (ub1 < lb0 - kLlrClip) return kLlrClip;
+    if (ub0 < lb1 - kLlrClip) return -kLlrClip;
     if (fmaxf(dmin[0], dmin[1]) <= kLinDist) {
-        // both nearest terms are ordinary floats: plain sums of P(k | x), terms
-        // below e^-16 of their set's nearest term dropped
-        const float pn0 = p_lin32((p.tf[kmin[0]] - x) * p.inv_sigma, (p.tf[kmin[0] + 1] - x) * p.inv_sigma);
-        const float pn1 = p_lin32((p.tf[kmin[1]] - x) * p.inv_sigma, (p.tf[kmin[1] + 1] - x) * p.inv_sigma);
-        const float cut0 = logf(pn0) - kSkipLinNats, cut1 = logf(pn1) - kSkipLinNats;
-        float s0 = pn0, s1 = pn1;
-        for (int u = 0; u < nc; ++u) {
-            const int k = p.k_of_label[(u << p.j) | low];
-            const int b = u & 1;
-            if (k == kmin[b]) continue;
-            const float d = interval_dist(p, k, x);
+        // both nearest terms are ordinary floats: plain sums of P(k | x) over the
+        // candidates in interval order, terms bounded below e^-16 of their set's
+        // lower bound dropped, each threshold's tail evaluated once
+        const float cut0 = lb0 - kSkipLinNats, cut1 = lb1 - kSkipLinNats;
+        float s0 = 0.0f, s1 = 0.0f, Tn = 0.0f;
+        int kn = -2;
+        for (int i = 0; i < nc; ++i) {
+            const int k = cl[i];
+            const int b = p.bitj[k];
+            const float a_ = (p.tf[k] - x) * p.inv_sigma, b_ = (p.tf[k + 1] - x) * p.inv_sigma;
+            const float d = a_ >= 0.0f ? a_ : (b_ <= 0.0f ? -b_ : 0.0f);
             const float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
             if (bound < (b ? cut1 : cut0)) continue;
-            const float t = p_lin32((p.tf[k] - x) * p.inv_sigma, (p.tf[k + 1] - x) * p.inv_sigma);
+            const float Ta = k == kn ? Tn : tail_q(a_);
+            const float Tb = tail_q(b_);
+            kn = k + 1;
+            Tn = Tb;
+            const float t = p_from_tails(a_, b_, Ta, Tb);
             if (b) s1 += t;
             else s0 += t;
         }
         return fminf(fmaxf(logf(s0) - logf(s1), -kLlrClip), kLlrClip);
     }
     const float lpn0 = lp_interval32(p, kmin[0], x), lpn1 = lp_interval32(p, kmin[1], x);
-    // a set whose whole mass is provably more than the clip below the other's
-    // nearest term cannot move the clipped result
-    const float ub0 = lg_half_n + (dmin[0] > 0.0f ? kLn05 - 0.5f * dmin[0] * dmin[0] : 0.0f);
-    const float ub1 = lg_half_n + (dmin[1] > 0.0f ? kLn05 - 0.5f * dmin[1] * dmin[1] : 0.0f);
     float llr;
     if (ub1 < lpn0 - kLlrClip) {
         llr = kLlrClip;
@@ -168,9 +210,9 @@ __device__ __forceinline__ float llr_one(const LlrParams &p, float x, int low) {
     } else if (fmaxf(lpn0, lpn1) >= -kFarNats) {
         // FP32: sums relative to each set's nearest term
         float s0 = 1.0f, s1 = 1.0f;
-        for (int u = 0; u < nc; ++u) {
-            const int k = p.k_of_label[(u << p.j) | low];
-            const int b = u & 1;
+        for (int i = 0; i < nc; ++i) {
+            const int k = cl[i];
+            const int b = p.bitj[k];
             if (k == kmin[b]) continue;
             const float d = interval_dist(p, k, x);
             const float bound = d > 0.0f ? kLn05 - 0.5f * d * d : 0.0f;
@@ -187,9 +229,9 @@ __device__ __forceinline__ float llr_one(const LlrParams &p, float x, int low) {
         const double xd = (double)x;
         const double r0 = lp_interval64(p, kmin[0], xd), r1 = lp_interval64(p, kmin[1], xd);
         double s0 = 1.0, s1 = 1.0;
-        for (int u = 0; u < nc; ++u) {
-            const int k = p.k_of_label[(u << p.j) | low];
-            const int b = u & 1;
+        for (int i = 0; i < nc; ++i) {
+            const int k = cl[i];
+            const int b = p.bitj[k];
             if (k == kmin[b]) continue;
             const float d = interval_dist(p, k, x);
             const float bound = kLn05 - 0.5f * d * d;
@@ -394,6 +436,18 @@ __global__ void slice_llr_frames_kernel(const float *__restrict__ xs, const int6
         sp.m = m;
         sp.K = K;
         sp.j = j;
+        sp.ln_h = (float)log(delta / sn);
+        sp.ln_half_n = logf(0.5f * (float)(K >> j));
+    }
+    if (threadIdx.x < K) {
+        // candidate lists in interval order: interval k's rank among the
+        // intervals sharing its lower label bits
+        const int k = threadIdx.x, lowmask = (1 << j) - 1, nc = K >> j;
+        const int lab = gray ? (k ^ (k >> 1)) : k, low = lab & lowmask;
+        int rank = 0;
+        for (int k2 = 0; k2 < k; ++k2) rank += ((gray ? (k2 ^ (k2 >> 1)) : k2) & lowmask) == low;
+        sp.cand[low * nc + rank] = (uint8_t)k;
+        sp.bitj[k] = (uint8_t)((lab >> j) & 1);
     }
     __syncthreads();
     unsigned long long units = 0;
@@ -475,6 +529,7 @@ qkdrec_status qkdrec_slice_llr(const float *x, int64_t count, int32_t m, int32_t
     for (int k = 0; k < p.K; ++k) p.k_of_label[label_of(k, label)] = (uint8_t)k;
     p.inv_sigma = (float)(1.0 / sigma_n);
     p.inv_sigma_d = 1.0 / sigma_n;
+    llr_tables(p, delta);
     const int block = 128;
     prof::Scope ps(prof::kSliceLlr, as_stream(stream));
     slice_llr_kernel<<<grid_for(count, block), block, 0, as_stream(stream)>>>(x, count, lower_bits, p, llr_out,
