@@ -928,9 +928,12 @@ def run_ours(args):
         bob_pk[snr] = torch.stack([q.qkdrec_pack_bits(bits[j]) for j in range(M_SLICES)])
         del bits
 
-    def frame_errors(snr, ln, j, packed):
+    def frame_bad(snr, ln, j, packed):
         n, F = 1 << ln, N_SAMPLES >> ln
-        return int((packed[(snr, ln)][j].view(F, n // 8) != bob_pk[snr][j].view(F, n // 8)).any(dim=1).sum())
+        return (packed[(snr, ln)][j].view(F, n // 8) != bob_pk[snr][j].view(F, n // 8)).any(dim=1)
+
+    def frame_errors(snr, ln, j, packed):
+        return int(frame_bad(snr, ln, j, packed).sum())
 
     good_bits, raw_bits, fer, mean_iters = 0, 0, {}, {}
     edge_updates = sum(v["units"] for k, v in stats.items() if k.startswith(("check_flood", "layer_oms"))) / args.steps
@@ -948,6 +951,22 @@ def run_ours(args):
                 its.append(round(float(iters[(snr, ln, j)].float().mean().item()), 2))
             fer[f"snr{int(snr)}_n2^{ln}"] = errs
             mean_iters[f"snr{int(snr)}_n2^{ln}"] = its
+    # the paper's reconciliation efficiency of each point's rates (Eq. beta, disclosed
+    # slices at rate 0), and the net key it leaves: (Pi(M(Y)) - m + sum R_j) bits per
+    # sample of every sub-block whose slices all reconciled, per second
+    beta_pt, net_bits = {}, 0.0
+    for snr in SNRS:
+        lo, hi = lo_hi[snr]
+        for ln in LOGNS:
+            n, F = 1 << ln, N_SAMPLES >> ln
+            rates = [rate_of[(snr, ln, j)] for j in range(M_SLICES)]
+            beta, H = q.qkdrec_reconciliation_efficiency(snr, M_SLICES, lo, hi, rates)
+            beta_pt[f"snr{int(snr)}_n2^{ln}"] = round(beta, 4)
+            bad = torch.zeros(F, dtype=torch.bool, device=dev)
+            for j in range(M_SLICES):
+                if rates[j] > 0:
+                    bad |= frame_bad(snr, ln, j, alice_pk)
+            net_bits += (H - M_SLICES + sum(rates)) * n * (F - int(bad.sum()))
     # how full the decoders' frame blocks stay: frame-iterations done over what
     # the blocks (32 frames, kept until their last frame stops) occupy
     occ_num = occ_den = 0.0
@@ -1029,6 +1048,14 @@ def run_ours(args):
                    "fer_per_slice": fer, "mean_iters_per_slice": mean_iters,
                    "fer_plain_sp_f32_per_slice": fer_plain,
                    "frame_block_occupancy": occ_num / occ_den if occ_den else None,
+                   "beta_per_point": beta_pt,
+                   "net_key_bits_per_s": net_bits * world / (ms_step / 1e3),
+                   "net_key_note": ("(Pi(M(Y)) - m + sum_j R_j) x samples of sub-blocks with every slice reconciled, "
+                                    "over the device step time (Eq. beta's numerator; before parameter estimation "
+                                    "and privacy amplification)"),
+                   "rate_tables_note": ("the back-off rates were calibrated with layered offset min-sum trials "
+                                        "(<= 50 iterations); the line decodes with the form named in 'algo'")
+                   if args.rate_rule == "backoff" else None,
                    "error_vs_oracle": err_oracle,
                    "code_residual_4cycles": residual, "setup_s": round(setup_s, 1),
                    "timing": ("step captured once as a CUDA graph and replayed; kernel figures from the same "

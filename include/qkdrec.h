@@ -574,6 +574,19 @@ qkdrec_status qkdrec_checks_for_rate(int32_t n, double rate, int32_t *m_checks);
  * QKDREC_ERR_ARG (NULL, snr or va not positive and finite).  HOST. */
 qkdrec_status qkdrec_quantiser_range(double snr, double va, double *lo, double *hi);
 
+/*
+ * Reconciliation efficiency of slice reconciliation with code rates R_j
+ * (Eq. beta):  beta = (Pi(M(Y)) - m + sum_j R_j) / I_AB,  where Pi(M(Y)) is the
+ * entropy in bits of Bob's quantised value (y ~ N(0, va + 1/snr), 2^m bins on
+ * [lo, hi] as qkdrec_quantise_slices) and I_AB = 1/2 log2(1 + va snr).  A
+ * disclosed slice has R_j = 0 (its bits are revealed).
+ *   rates    HOST double [m], each in [0, 1).
+ *   beta     out;  entropy  out (may be NULL): Pi(M(Y)) in bits per sample.
+ * Errors: QKDREC_ERR_ARG.  HOST.
+ */
+qkdrec_status qkdrec_reconciliation_efficiency(double snr, int32_t m_slices, double lo, double hi, double va,
+                                               const double *rates, double *beta, double *entropy);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *qkdrec_last_error(void);
 

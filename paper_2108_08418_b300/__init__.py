@@ -41,7 +41,7 @@ EXPORTED = [
     "qkdrec_code_set_qc", "qkdrec_qc_timeouts",
     "qkdrec_make_regular_code", "qkdrec_free", "qkdrec_code_rate", "qkdrec_checks_for_rate",
     "qkdrec_quantiser_range", "qkdrec_reconcile", "qkdrec_reconcile_workspace_size", "qkdrec_pack_bits",
-    "qkdrec_unpack_bits",
+    "qkdrec_unpack_bits", "qkdrec_reconciliation_efficiency",
 ]
 SELFTEST = ["qkdrec_selftest_phi", "qkdrec_selftest_phi_pair"]
 
@@ -120,6 +120,7 @@ def lib():
         "qkdrec_code_rate": (U, [D, D, I32, P]),
         "qkdrec_checks_for_rate": (U, [I32, D, P]),
         "qkdrec_quantiser_range": (U, [D, D, P, P]),
+        "qkdrec_reconciliation_efficiency": (U, [D, I32, D, D, D, P, P, P]),
         "qkdrec_decode_static_capacity": (ctypes.c_size_t, []),
         "qkdrec_decode_batch_static": (U, [P, P, P, I32, P, P, P, P, P, P]),
         "qkdrec_woms_workspace_size": (U, [P, I32, I32, I32, P]),
@@ -680,6 +681,17 @@ def qkdrec_code_rate(capacity: float, fraction: float = 0.95, denom: int = 64) -
 
 
 code_rate = qkdrec_code_rate
+
+
+def qkdrec_reconciliation_efficiency(snr: float, m_slices: int, lo: float, hi: float, rates, va: float = 1.0):
+    """(beta, Pi(M(Y))): Eq. beta for slice code rates `rates` (0 = disclosed)."""
+    r = np.ascontiguousarray(rates, dtype=np.float64)
+    if r.shape != (m_slices,):
+        raise ValueError("one rate per slice")
+    b, h = ctypes.c_double(), ctypes.c_double()
+    _check(lib().qkdrec_reconciliation_efficiency(float(snr), int(m_slices), float(lo), float(hi), float(va),
+                                                  r.ctypes.data, ctypes.byref(b), ctypes.byref(h)))
+    return b.value, h.value
 
 
 def qkdrec_checks_for_rate(n: int, rate: float) -> int:

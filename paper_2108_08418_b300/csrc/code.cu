@@ -289,6 +289,34 @@ qkdrec_status qkdrec_quantiser_range(double snr, double va, double *lo, double *
     return QKDREC_OK;
 }
 
+qkdrec_status qkdrec_reconciliation_efficiency(double snr, int32_t m, double lo, double hi, double va,
+                                               const double *rates, double *beta, double *entropy) {
+    clear_error();
+    if (!rates || !beta) QKD_FAIL(QKDREC_ERR_ARG, "rates/beta NULL");
+    if (!(snr > 0) || !(va > 0) || m < 1 || m > 16 || !(lo < hi))
+        QKD_FAIL(QKDREC_ERR_ARG, "bad arguments (snr=%g m=%d lo=%g hi=%g va=%g)", snr, m, lo, hi, va);
+    // Pi(M(Y)): entropy of Bob's quantised value, y ~ N(0, va + 1/snr), 2^m bins
+    const int K = 1 << m;
+    const double sy = sqrt(va + 1.0 / snr), r2 = 0.70710678118654752440;
+    auto cdf = [&](double t) { return isinf(t) ? (t > 0 ? 1.0 : 0.0) : 0.5 * erfc(-t / sy * r2); };
+    double H = 0.0, sum_r = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double a = k == 0 ? -INFINITY : lo + (hi - lo) * k / K;
+        const double b = k == K - 1 ? INFINITY : lo + (hi - lo) * (k + 1) / K;
+        // the smaller tail difference, so an outer bin keeps its relative precision
+        const double P = (a >= 0.0) ? 0.5 * (erfc(a / sy * r2) - erfc(b / sy * r2)) : cdf(b) - cdf(a);
+        if (P > 0) H -= P * log2(P);
+    }
+    for (int j = 0; j < m; ++j) {
+        if (!(rates[j] >= 0.0 && rates[j] < 1.0)) QKD_FAIL(QKDREC_ERR_ARG, "rate[%d]=%g outside [0, 1)", j, rates[j]);
+        sum_r += rates[j];
+    }
+    const double iab = 0.5 * log2(1.0 + va * snr);   // I(X;Y) of the Gaussian channel, bits per sample
+    *beta = (H - m + sum_r) / iab;
+    if (entropy) *entropy = H;
+    return QKDREC_OK;
+}
+
 qkdrec_status qkdrec_code_layers(qkdrec_code_t code, int32_t *layer_of_check) {
     clear_error();
     if (!code || !layer_of_check) QKD_FAIL(QKDREC_ERR_ARG, "NULL argument");

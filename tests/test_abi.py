@@ -148,3 +148,23 @@ def test_make_regular_code_argument_errors(L):
     L.qkdrec_free(ctypes.cast(rp, ctypes.c_void_p))
     L.qkdrec_free(ctypes.cast(ci, ctypes.c_void_p))
     L.qkdrec_free(None)
+
+
+def test_reconciliation_efficiency_matches_the_oracle(L):
+    """Eq. beta from the library against the oracle's quantiser entropy: with the
+    rates at the slice capacities the numerator is I(M(Y); X) (Eq. beta2 with the
+    Slepian-Wolf bound tight), so beta < 1; with every slice disclosed it is
+    (Pi(M(Y)) - m) / I_AB."""
+    import math
+    for snr, m in ((3.0, 5), (15.0, 5), (3.0, 4)):
+        lo, hi = oracle.quantiser_range(snr)
+        caps = [oracle.slice_capacity(snr, m, j) for j in range(m)]
+        beta, H = q.qkdrec_reconciliation_efficiency(snr, m, lo, hi, caps)
+        assert abs(H - oracle.label_entropy(snr, m)) < 1e-10
+        iab = 0.5 * math.log2(1 + snr)
+        assert abs(beta - (oracle.label_entropy(snr, m) - m + sum(caps)) / iab) < 1e-9
+        assert 0.9 < beta < 1.0
+        b0, _ = q.qkdrec_reconciliation_efficiency(snr, m, lo, hi, [0.0] * m)
+        assert abs(b0 - (H - m) / iab) < 1e-12
+    with pytest.raises(q.QkdrecError):
+        q.qkdrec_reconciliation_efficiency(3.0, 2, -1.0, 1.0, [0.5, 1.0])
