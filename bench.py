@@ -967,6 +967,25 @@ def run_ours(args):
                 if rates[j] > 0:
                     bad |= frame_bad(snr, ln, j, alice_pk)
             net_bits += (H - M_SLICES + sum(rates)) * n * (F - int(bad.sum()))
+    # Sec. IV-B's optimum sub-block length with this decoder's measured inputs:
+    # c_h (time per arithmetic operation, Eq. DeltaT) and D_j (mean iterations of
+    # each decoded slice of the largest sub-blocks at SNR 3; 3 edges per sample for
+    # the dv = 3 codes, 0 for a disclosed slice), at the paper's standard settings
+    nr_opt = None
+    if edge_updates:
+        c_h = (ms / args.steps / 1e3) / (7 * edge_updates)
+        ln_big = max(LOGNS)
+        g_j = [3.0 if rate_of[(3.0, ln_big, j)] > 0 else 0.0 for j in range(M_SLICES)]
+        d_j = [float(iters[(3.0, ln_big, j)].float().mean()) if g_j[j] else 0.0 for j in range(M_SLICES)]
+        nr_opt = {}
+        for form, name in ((0, "awgn_dispersion"), (1, "printed_dispersion")):
+            r = q.qkdrec_nr_optimise(g_j, d_j, c_h=c_h, dispersion_form=form)
+            nr_opt[name] = {"nr_opt": r["nr_opt"], "key_rate_bits_per_s": r["key_rate_opt"],
+                            "at_boundary": bool(r["at_boundary"])}
+        nr_opt["inputs"] = {"c_h_s": c_h, "D_j": [round(v, 2) for v in d_j], "edges_per_sample": g_j,
+                            "settings": "the paper's standard CV-QKD settings (N = 1e9, m = 5, eps = 2.5e-10, "
+                                        "V_A = 5, T = 0.9, xi_ch = 0.0186, xi_d = 0.0133)"}
+        nr_opt["paper"] = {"nr_opt": 3.6e7, "key_rate_bits_per_s": 4.3e5, "c_h_s": 3.2e-9, "hardware": "GTX 1060"}
     # how full the decoders' frame blocks stay: frame-iterations done over what
     # the blocks (32 frames, kept until their last frame stops) occupy
     occ_num = occ_den = 0.0
@@ -1049,6 +1068,7 @@ def run_ours(args):
                    "fer_plain_sp_f32_per_slice": fer_plain,
                    "frame_block_occupancy": occ_num / occ_den if occ_den else None,
                    "beta_per_point": beta_pt,
+                   "nr_optimum": nr_opt,
                    "net_key_bits_per_s": net_bits * world / (ms_step / 1e3),
                    "net_key_note": ("(Pi(M(Y)) - m + sum_j R_j) x samples of sub-blocks with every slice reconciled, "
                                     "over the device step time (Eq. beta's numerator; before parameter estimation "

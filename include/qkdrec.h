@@ -587,6 +587,67 @@ qkdrec_status qkdrec_quantiser_range(double snr, double va, double *lo, double *
 qkdrec_status qkdrec_reconciliation_efficiency(double snr, int32_t m_slices, double lo, double hi, double va,
                                                const double *rates, double *beta, double *entropy);
 
+/* ------------------------------------------- optimum sub-block length N_R */
+
+/*
+ * Parameters of the key-rate optimisation over the sub-block length
+ * (Sec. IV-B, Eqs. R_Finite, AEP, FiniteK, BPSRate, simplifiedOpt, diff_eq2;
+ * the appendix for S_BE).  The paper's standard settings: N = 1e9, m = 5,
+ * eps_EC = 2 eps_s = eps_PA = eps_PE = 2.5e-10, V_A = 5, T = 0.9,
+ * xi_ch = 0.0186, xi_d = 0.0133, eta_d = 1, c_h = 3.2e-9 s.
+ */
+typedef struct {
+    double n_signals;                 /* N, quantum signals of the block */
+    int32_t m_slices;                 /* m, 1..16 */
+    double eps_ec, eps_s, eps_pa, eps_pe;   /* failure probabilities, each in (0, 1/2) */
+    double va;                        /* modulation variance V_A */
+    double transmissivity;            /* T in (0, 1] */
+    double xi_ch, xi_d;               /* channel excess noise, detector noise */
+    double eta_d;                     /* detection efficiency in (0, 1] */
+    double n_estimation;              /* N_e signals for parameter estimation; <= 0: N / 2 */
+    double c_h;                       /* seconds per arithmetic operation of the decoder (Eq. DeltaT) */
+    const double *edges_per_sample;   /* HOST [m]: G_j / N_R of slice j's code (0: disclosed slice) */
+    const double *iterations;         /* HOST [m]: D_j, decoding iterations of slice j */
+    int32_t dispersion_form;          /* 0: A = gamma (gamma+2) / (2 (gamma+1)^2) (log2 e)^2, the
+                                         AWGN channel dispersion; 1: as printed, with (log2 eps_EC)^2 */
+    double nr_min;                    /* lower end of the N_R range; <= 0: 1e5 (Sec. IV-B) */
+} qkdrec_nr_params;
+
+typedef struct {
+    double snr;                       /* gamma = (V_A T / 2) / (1 + (xi_ch + xi_d) / 2)   (Eq. SNR) */
+    double i_ab;                      /* C(gamma) = 1/2 log2(1 + gamma), bits per sample */
+    double dispersion;                /* A */
+    double qinv_ec;                   /* Q^-1(eps_EC) */
+    double delta_aep;                 /* Delta_AEP (Eq. AEP) */
+    double s_be;                      /* S_BE: chi_BE at T^L, xi_ch^U (appendix) */
+    double t_low, xi_up;              /* the worst-case estimates T^L, xi_ch^U */
+    double b1, b2;                    /* B_1, B_2 of Eq. simplifiedOpt */
+    double nr_stationary;             /* root of dK'/dN_R = 0 in the range (0: none) */
+    double nr_opt;                    /* maximiser of K'_Finite over the range */
+    double key_rate_opt;              /* K'_Finite there, bits per second */
+    double d2_key_rate;               /* d^2 K'/dN_R^2 at nr_opt (< 0 at an interior maximum) */
+    int32_t at_boundary;              /* 1 if the maximum is at an end of the range */
+} qkdrec_nr_result;
+
+/*
+ * The N_R that maximises the finite-length key rate in bits per second,
+ *   K'(N_R) = (N C_Finite(N_R) - B_1) / (B_2 N_R),
+ *   C_Finite(N_R) = C(gamma) - (sqrt(N_R A) Q^-1(eps_EC) + 1/2 log2 N_R) / N_R,
+ *   B_1 = N S_BE + sqrt(N) Delta_AEP + 2 log2(1 / (2 eps_PA)),
+ *   B_2 = sum_j 7 (G_j / N_R) D_j c_h,
+ * over nr_min <= N_R <= N: the stationary point (bisection on ln N_R) or an
+ * end of the range, whichever gives the larger K'.  Readings where the paper's
+ * formulas are garbled: base-2 logarithms throughout; S_BE from the standard
+ * symplectic eigenvalues of reverse reconciliation with heterodyne detection
+ * (the squares the appendix drops restored, chi_ch in Psi_2, the detector
+ * term (2 - eta_d + 2 xi_d) / eta_d); T^L and xi_ch^U from t^ = sqrt(eta_d T),
+ * sigma^2 = T eta_d xi_ch + 1 + xi_d, tau = Q^-1(eps_PE / 2).  HOST only.
+ * Errors: QKDREC_ERR_ARG (parameters out of range, B_2 = 0, T^L <= 0).
+ */
+qkdrec_status qkdrec_nr_optimise(const qkdrec_nr_params *params, qkdrec_nr_result *out);
+/* K'_Finite(N_R) in bits per second for one N_R >= 1 (same parameters). */
+qkdrec_status qkdrec_nr_key_rate(const qkdrec_nr_params *params, double nr, double *key_rate);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *qkdrec_last_error(void);
 

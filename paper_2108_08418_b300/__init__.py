@@ -41,7 +41,7 @@ EXPORTED = [
     "qkdrec_code_set_qc", "qkdrec_qc_timeouts",
     "qkdrec_make_regular_code", "qkdrec_free", "qkdrec_code_rate", "qkdrec_checks_for_rate",
     "qkdrec_quantiser_range", "qkdrec_reconcile", "qkdrec_reconcile_workspace_size", "qkdrec_pack_bits",
-    "qkdrec_unpack_bits", "qkdrec_reconciliation_efficiency",
+    "qkdrec_unpack_bits", "qkdrec_reconciliation_efficiency", "qkdrec_nr_optimise", "qkdrec_nr_key_rate",
 ]
 SELFTEST = ["qkdrec_selftest_phi", "qkdrec_selftest_phi_pair"]
 
@@ -74,6 +74,21 @@ class TuningC(ctypes.Structure):
 class PointC(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("codes", ctypes.c_void_p), ("alice_packed", ctypes.c_void_p),
                 ("converged", ctypes.c_void_p), ("iters", ctypes.c_void_p)]
+
+
+class NrParamsC(ctypes.Structure):
+    _fields_ = [("n_signals", ctypes.c_double), ("m_slices", ctypes.c_int32), ("eps_ec", ctypes.c_double),
+                ("eps_s", ctypes.c_double), ("eps_pa", ctypes.c_double), ("eps_pe", ctypes.c_double),
+                ("va", ctypes.c_double), ("transmissivity", ctypes.c_double), ("xi_ch", ctypes.c_double),
+                ("xi_d", ctypes.c_double), ("eta_d", ctypes.c_double), ("n_estimation", ctypes.c_double),
+                ("c_h", ctypes.c_double), ("edges_per_sample", ctypes.c_void_p), ("iterations", ctypes.c_void_p),
+                ("dispersion_form", ctypes.c_int32), ("nr_min", ctypes.c_double)]
+
+
+class NrResultC(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("snr", "i_ab", "dispersion", "qinv_ec", "delta_aep", "s_be", "t_low",
+                                               "xi_up", "b1", "b2", "nr_stationary", "nr_opt", "key_rate_opt",
+                                               "d2_key_rate")] + [("at_boundary", ctypes.c_int32)]
 
 
 class DecodeOptsC(ctypes.Structure):
@@ -121,6 +136,8 @@ def lib():
         "qkdrec_checks_for_rate": (U, [I32, D, P]),
         "qkdrec_quantiser_range": (U, [D, D, P, P]),
         "qkdrec_reconciliation_efficiency": (U, [D, I32, D, D, D, P, P, P]),
+        "qkdrec_nr_optimise": (U, [P, P]),
+        "qkdrec_nr_key_rate": (U, [P, D, P]),
         "qkdrec_decode_static_capacity": (ctypes.c_size_t, []),
         "qkdrec_decode_batch_static": (U, [P, P, P, I32, P, P, P, P, P, P]),
         "qkdrec_woms_workspace_size": (U, [P, I32, I32, I32, P]),
@@ -692,6 +709,37 @@ def qkdrec_reconciliation_efficiency(snr: float, m_slices: int, lo: float, hi: f
     _check(lib().qkdrec_reconciliation_efficiency(float(snr), int(m_slices), float(lo), float(hi), float(va),
                                                   r.ctypes.data, ctypes.byref(b), ctypes.byref(h)))
     return b.value, h.value
+
+
+# the paper's standard CV-QKD settings (Sec. IV-B)
+NR_STANDARD = dict(n_signals=1e9, m_slices=5, eps_ec=2.5e-10, eps_s=1.25e-10, eps_pa=2.5e-10, eps_pe=2.5e-10,
+                   va=5.0, transmissivity=0.9, xi_ch=0.0186, xi_d=0.0133, eta_d=1.0, n_estimation=0.0,
+                   c_h=3.2e-9, dispersion_form=0, nr_min=1e5)
+
+
+def _nr_params(edges_per_sample, iterations, **kw):
+    p = {**NR_STANDARD, **kw}
+    g = np.ascontiguousarray(edges_per_sample, dtype=np.float64)
+    d = np.ascontiguousarray(iterations, dtype=np.float64)
+    if g.shape != (p["m_slices"],) or d.shape != (p["m_slices"],):
+        raise ValueError("one edges-per-sample and one iteration count per slice")
+    c = NrParamsC(**{k: v for k, v in p.items()}, edges_per_sample=g.ctypes.data, iterations=d.ctypes.data)
+    return c, (g, d)
+
+
+def qkdrec_nr_optimise(edges_per_sample, iterations, **kw) -> dict:
+    """Optimum sub-block length (include/qkdrec.h); keyword overrides of NR_STANDARD."""
+    c, keep = _nr_params(edges_per_sample, iterations, **kw)
+    r = NrResultC()
+    _check(lib().qkdrec_nr_optimise(ctypes.byref(c), ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in r._fields_}
+
+
+def qkdrec_nr_key_rate(nr: float, edges_per_sample, iterations, **kw) -> float:
+    c, keep = _nr_params(edges_per_sample, iterations, **kw)
+    v = ctypes.c_double()
+    _check(lib().qkdrec_nr_key_rate(ctypes.byref(c), float(nr), ctypes.byref(v)))
+    return v.value
 
 
 def qkdrec_checks_for_rate(n: int, rate: float) -> int:
