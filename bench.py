@@ -55,6 +55,24 @@ def sweep_workload(rate_rule):
                                                                       RATES_BACKOFF)
 
 
+# iterations after which the FP32 flooding decoders re-pack their decoding
+# frames (the library's fixed schedule)
+REPACK_AT = (16, 32, 64)
+
+
+def block_work(t, sched, B=32):
+    """Frame-iterations that 32-frame blocks occupy for frames taking t[f] check
+    passes, re-packed densely (in their order) after each iteration in sched."""
+    work, cur = 0, np.asarray(t)
+    for it in range(1, int(cur.max()) + 1 if cur.size else 1):
+        if it - 1 in sched:
+            cur = cur[cur >= it]
+        pad = (-cur.size) % B
+        tb = np.concatenate([cur, np.zeros(pad, dtype=cur.dtype)]).reshape(-1, B)
+        work += int((tb >= it).any(axis=1).sum()) * B
+    return work
+
+
 def code_seed(logn, j):
     return 2000 + 100 * logn + j
 
@@ -986,18 +1004,22 @@ def run_ours(args):
                             "settings": "the paper's standard CV-QKD settings (N = 1e9, m = 5, eps = 2.5e-10, "
                                         "V_A = 5, T = 0.9, xi_ch = 0.0186, xi_d = 0.0133)"}
         nr_opt["paper"] = {"nr_opt": 3.6e7, "key_rate_bits_per_s": 4.3e5, "c_h_s": 3.2e-9, "hardware": "GTX 1060"}
-    # how full the decoders' frame blocks stay: frame-iterations done over what
-    # the blocks (32 frames, kept until their last frame stops) occupy
-    occ_num = occ_den = 0.0
-    for (snr, ln, j), it in iters.items():
-        if rate_of[(snr, ln, j)] <= 0:
-            continue
-        e = codes[(ln, j, rate_of[(snr, ln, j)])].E
-        t = it.to(torch.float64) + 1.0
-        pad = (-t.numel()) % 32
-        tb = torch.cat([t, torch.zeros(pad, dtype=t.dtype, device=t.device)]).view(-1, 32)
-        occ_num += float(tb.sum()) * e
-        occ_den += float(tb.max(dim=1).values.sum()) * 32 * e
+    # how full the decoders' 32-frame blocks stay: frame-iterations done over the
+    # frame-iterations the blocks occupy (a block runs until its last frame stops),
+    # from the per-frame iteration counts; with the FP32 flooding decoders' re-packing
+    # of the decoding frames after iterations REPACK_AT, and without it
+    occ = {}
+    repacks = prec == "f32" and algo != "oms_layered"
+    for name, sched in (("with_repacking", REPACK_AT if repacks else ()), ("without_repacking", ())):
+        num = den = 0.0
+        for (snr, ln, j), it in iters.items():
+            if rate_of[(snr, ln, j)] <= 0:
+                continue
+            e = codes[(ln, j, rate_of[(snr, ln, j)])].E
+            t_f = it.cpu().numpy().astype(np.int64) + 1
+            num += float(t_f.sum()) * e
+            den += block_work(t_f, sched) * e
+        occ[name] = num / den if den else None
 
     # per-result error against the FP64 oracle on a sample of sub-blocks, and (for the
     # low-precision forms) the FER of the plain FP32 sum-product form on the same block
@@ -1066,7 +1088,7 @@ def run_ours(args):
                    "equivalent_c_h_s": (ms_step / 1e3) / (7 * edge_updates * world) if edge_updates else None,
                    "fer_per_slice": fer, "mean_iters_per_slice": mean_iters,
                    "fer_plain_sp_f32_per_slice": fer_plain,
-                   "frame_block_occupancy": occ_num / occ_den if occ_den else None,
+                   "frame_block_occupancy": occ,
                    "beta_per_point": beta_pt,
                    "nr_optimum": nr_opt,
                    "net_key_bits_per_s": net_bits * world / (ms_step / 1e3),

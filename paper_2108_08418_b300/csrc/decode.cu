@@ -1237,7 +1237,7 @@ __global__ void write_out(const void *Lp, int32_t F, int32_t n, int64_t Fp, int 
 struct Layout {
     int64_t Fp, FV, W;
     int lgfb;
-    size_t llr_i, L, msg, sbits, active, mask, unsat0, unsat1, iters, blk, blk_n, fmap, fcnt, total;
+    size_t llr_i, L, msg, sbits, active, mask, unsat0, unsat1, iters, blk, blk_n, fmap, fcnt, fsrc, total;
 };
 
 // register-cache size of the check kernels for a code: 8 or 32 edges, 0 = reload
@@ -1276,8 +1276,21 @@ static Layout make_layout(const CodeDev &d, int32_t F, int algo, int prec) {
     l.blk_n = take(4);
     l.fmap = take((size_t)l.Fp * 4);
     l.fcnt = take(4);
+    l.fsrc = take((size_t)l.Fp * 4);
     l.total = off;
     return l;
+}
+
+// Iterations after which a flooding FP32 pass with the stopping test re-packs
+// its still-decoding frames densely into the other half of its workspace (the
+// frame blocks then hold only decoding frames again).  A fixed schedule, so the
+// host always knows which half is live and the launches need no device
+// decision; chosen on the measured iteration counts of the block-size sweep,
+// where it lifts the decoding frames' share of the frame-block work from 0.75 to
+// 0.87 after paying for the moves.
+constexpr int kCompactAt[] = {16, 32, 64};
+static bool compacts(const qkdrec_decode_opts &o, int algo, int prec) {
+    return o.early_stop && algo != QKDREC_OMS_LAYERED && prec == kF32 && o.max_iter > kCompactAt[0];
 }
 
 static bool opts_ok(const qkdrec_decode_opts *o) {
@@ -1287,10 +1300,10 @@ static bool opts_ok(const qkdrec_decode_opts *o) {
 }
 
 static size_t workspace_for(const CodeDev &d, int32_t F, const qkdrec_decode_opts *o) {
-    size_t b = make_layout(d, F, o->algo, o->prec).total;
+    size_t b = make_layout(d, F, o->algo, o->prec).total * (compacts(*o, o->algo, o->prec) ? 2 : 1);
     if (o->fallback_f32 && o->prec != kF32) {
         const int algo = o->fallback_f32 == 2 ? QKDREC_SP_FLOOD : o->algo;
-        size_t b32 = make_layout(d, F, algo, kF32).total;
+        size_t b32 = make_layout(d, F, algo, kF32).total * (compacts(*o, algo, kF32) ? 2 : 1);
         if (b32 > b) b = b32;
     }
     return b;
@@ -1357,6 +1370,78 @@ static qkdrec_status rebuild_blocks(const Layout &l, char *ws, cudaStream_t st) 
     return QKDREC_OK;
 }
 
+// The per-frame arrays of DecArgs and Prepared in the workspace half at ws.
+static void bind(DecArgs &a, Prepared &pr, char *ws, const Layout &l) {
+    a.sbits = reinterpret_cast<const uint32_t *>(ws + l.sbits);
+    a.active = reinterpret_cast<uint8_t *>(ws + l.active);
+    a.iters_i = reinterpret_cast<int32_t *>(ws + l.iters);
+    a.L = ws + l.L;
+    a.msg = ws + l.msg;
+    a.llr_i = ws + l.llr_i;
+    a.blk = reinterpret_cast<const int32_t *>(ws + l.blk);
+    a.blk_n = reinterpret_cast<const int32_t *>(ws + l.blk_n);
+    pr.unsat[0] = reinterpret_cast<uint32_t *>(ws + l.unsat0);
+    pr.unsat[1] = reinterpret_cast<uint32_t *>(ws + l.unsat1);
+    pr.mask = reinterpret_cast<uint8_t *>(ws + l.mask);
+}
+
+// ------------------------------------------------------ frame re-packing
+// rmask = frames of this half that have stopped (their outputs are final)
+__global__ void retired_mask(int64_t Fp, const uint8_t *__restrict__ mask, const uint8_t *__restrict__ active,
+                             uint8_t *__restrict__ rmask) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < Fp; f += (int64_t)gridDim.x * blockDim.x)
+        rmask[f] = mask[f] && !active[f];
+}
+// positions of the decoding frames, packed to fsrc[0 .. *cnt) (*cnt cleared
+// before); a warp's frames keep their order, so consecutive new positions mostly
+// come from one old frame block
+__global__ void list_active(int64_t Fp, const uint8_t *__restrict__ active, int32_t *fsrc, int32_t *cnt) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = f < Fp && active[f];
+    const uint32_t m = __ballot_sync(0xffffffffu, on);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (on) fsrc[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)f;
+}
+// new position p holds old position fsrc[p]: its frame is fmap_old[fsrc[p]]
+__global__ void remap_frames(const int32_t *__restrict__ fsrc, const int32_t *__restrict__ cnt,
+                             const int32_t *__restrict__ fmap_old, int32_t *__restrict__ fmap_new) {
+    const int64_t c = *cnt;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < c; p += (int64_t)gridDim.x * blockDim.x)
+        fmap_new[p] = fmap_old ? fmap_old[fsrc[p]] : fsrc[p];
+}
+// 32-bit values of every item (variable or edge) of the re-packed frames:
+// one warp per (32 new positions, item), writes coalesced
+__global__ void gather_frames32(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t items,
+                                int lgfb, const int32_t *__restrict__ fsrc, const int32_t *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = *cnt, words = (c + 31) >> 5, tasks = words * items;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tasks; t += wstride) {
+        const int64_t w = t / items, item = t - w * items, p = (w << 5) + lane;
+        uint32_t v = 0;
+        if (p < c) v = src[fpos(item, items, __ldg(fsrc + p), lgfb)];
+        dst[fpos(item, items, p, lgfb)] = v;
+    }
+}
+// per-frame state of the new half: positions < *cnt decoding
+__global__ void init_repacked(int64_t Fp, int64_t W, const int32_t *__restrict__ cnt, uint8_t *active,
+                              uint8_t *mask, int32_t *iters_i, uint32_t *unsat0, uint32_t *unsat1) {
+    const int64_t c = *cnt;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < Fp; f += (int64_t)gridDim.x * blockDim.x) {
+        active[f] = f < c;
+        mask[f] = f < c;
+        iters_i[f] = 0;
+        if (f < W) {
+            unsat0[f] = 0;
+            unsat1[f] = 0;
+        }
+    }
+}
+
 // Shared set-up of one decode pass: per-frame state, interleaved LLRs and
 // posteriors, packed syndromes, zero messages.
 // compact: decode the frames with conv_prev[f] == 0 packed to the front (a
@@ -1368,12 +1453,7 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const SyndIn &s
     a.ci = d.ci;
     a.vptr = d.vptr;
     a.vedge = d.vedge;
-    a.sbits = reinterpret_cast<const uint32_t *>(ws + l.sbits);
-    a.active = reinterpret_cast<uint8_t *>(ws + l.active);
-    a.iters_i = reinterpret_cast<int32_t *>(ws + l.iters);
-    a.L = ws + l.L;
-    a.msg = ws + l.msg;
-    a.llr_i = ws + l.llr_i;
+    bind(a, pr, ws, l);
     a.Fp = l.Fp;
     a.FV = l.FV;
     a.E = d.E;
@@ -1388,13 +1468,8 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const SyndIn &s
     a.early_stop = o.early_stop ? 1 : 0;
     a.beta = o.offset;
     a.prof = nullptr;
-    pr.unsat[0] = reinterpret_cast<uint32_t *>(ws + l.unsat0);
-    pr.unsat[1] = reinterpret_cast<uint32_t *>(ws + l.unsat1);
-    pr.mask = reinterpret_cast<uint8_t *>(ws + l.mask);
     a.unsat_cur = pr.unsat[0];
     a.unsat_next = pr.unsat[1];
-    a.blk = reinterpret_cast<const int32_t *>(ws + l.blk);
-    a.blk_n = reinterpret_cast<const int32_t *>(ws + l.blk_n);
     int32_t *fmap = compact ? reinterpret_cast<int32_t *>(ws + l.fmap) : nullptr;
     int32_t *fcnt = compact ? reinterpret_cast<int32_t *>(ws + l.fcnt) : nullptr;
     if (compact) {
@@ -1446,11 +1521,9 @@ static qkdrec_status prepare(const CodeDev &d, const float *llr, const SyndIn &s
 // Shared tail: iteration counts / converged flags, then bits and posteriors
 // back to the frame-major output layout.
 static qkdrec_status finish(const CodeDev &d, int32_t F, int T, int prec, const qkdrec_decode_opts &o,
-                            const uint8_t *conv_prev, bool compact, char *ws, const Layout &l, const Prepared &pr,
-                            const DecArgs &a, int final_buf, uint8_t *bits_out, int32_t *iters_out,
-                            uint8_t *conv_out, float *post_out, cudaStream_t st) {
-    const int32_t *fmap = compact ? reinterpret_cast<const int32_t *>(ws + l.fmap) : nullptr;
-    const int32_t *fcnt = compact ? reinterpret_cast<const int32_t *>(ws + l.fcnt) : nullptr;
+                            const uint8_t *conv_prev, const int32_t *fmap, const int32_t *fcnt, char *ws,
+                            const Layout &l, const Prepared &pr, const DecArgs &a, int final_buf, uint8_t *bits_out,
+                            int32_t *iters_out, uint8_t *conv_out, float *post_out, cudaStream_t st) {
     {
         prof::Scope ps(prof::kFinish, st);
         finalize<<<(unsigned)ceil_div(F, 256), 256, 0, st>>>(F, T, conv_prev ? 1 : 0, pr.mask, a.active,
@@ -1535,6 +1608,11 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
     Prepared pr;
     qkdrec_status s = prepare(d, llr, synd, F, o, prec, conv_prev, compact, ws, l, st, a, pr);
     if (s != QKDREC_OK) return s;
+    // the live workspace half and its frame placement (NULL: position = frame)
+    char *cur = ws;
+    const int32_t *fmap_cur = compact ? reinterpret_cast<const int32_t *>(ws + l.fmap) : nullptr;
+    const int32_t *fcnt_cur = compact ? reinterpret_cast<const int32_t *>(ws + l.fcnt) : nullptr;
+    const bool repack = compacts(o, o.algo, prec);
     const int64_t vitems = (int64_t)d.n * l.FV;
     const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(vitems, 256), (int64_t)sm_count() * 64);
     // integer form: (variable, 16 frames) on x, listed frame blocks on y; FP16
@@ -1580,7 +1658,49 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
         if (o.early_stop) {
             // frames retired by this variable pass leave the list
             prof::Scope ps(prof::kFinish, st);
-            if ((s = rebuild_blocks(l, ws, st)) != QKDREC_OK) return s;
+            if ((s = rebuild_blocks(l, cur, st)) != QKDREC_OK) return s;
+        }
+        if (repack && t < o.max_iter && std::find(std::begin(kCompactAt), std::end(kCompactAt), t) != std::end(kCompactAt)) {
+            // the frames that stopped leave with their final outputs; the decoding
+            // ones move, state and all, to the front of the other half
+            prof::Scope ps(prof::kRepack, st);
+            char *nxt = cur == ws ? ws + l.total : ws;
+            uint8_t *rmask = reinterpret_cast<uint8_t *>(nxt + l.mask);
+            const unsigned gF = (unsigned)std::min<int64_t>(ceil_div(l.Fp, 256), (int64_t)sm_count() * 32);
+            retired_mask<<<gF, 256, 0, st>>>(l.Fp, pr.mask, a.active, rmask);
+            finalize<<<(unsigned)ceil_div(F, 256), 256, 0, st>>>(F, t, conv_prev ? 1 : 0, rmask, a.active, a.iters_i,
+                                                                 pr.unsat[0], iters_out, conv_out, fmap_cur);
+            {
+                dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
+                write_out<kF32><<<grd, blk, 0, st>>>(a.L, F, d.n, l.Fp, l.lgfb, o.llr_step, rmask, bits_out, post_out,
+                                                     fmap_cur, fcnt_cur);
+            }
+            int32_t *fsrc = reinterpret_cast<int32_t *>(nxt + l.fsrc), *fcnt_n = reinterpret_cast<int32_t *>(nxt + l.fcnt);
+            int32_t *fmap_n = reinterpret_cast<int32_t *>(nxt + l.fmap);
+            QKD_CUDA(cudaMemsetAsync(fcnt_n, 0, sizeof(int32_t), st));
+            list_active<<<(unsigned)ceil_div(l.Fp, 256), 256, 0, st>>>(l.Fp, a.active, fsrc, fcnt_n);
+            remap_frames<<<gF, 256, 0, st>>>(fsrc, fcnt_n, fmap_cur, fmap_n);
+            const unsigned gG = (unsigned)sm_count() * 16;
+            gather_frames32<<<gG, 256, 0, st>>>(reinterpret_cast<const uint32_t *>(a.llr_i),
+                                                reinterpret_cast<uint32_t *>(nxt + l.llr_i), d.n, l.lgfb, fsrc, fcnt_n);
+            gather_frames32<<<gG, 256, 0, st>>>(reinterpret_cast<const uint32_t *>(a.L),
+                                                reinterpret_cast<uint32_t *>(nxt + l.L), d.n, l.lgfb, fsrc, fcnt_n);
+            gather_frames32<<<gG, 256, 0, st>>>(reinterpret_cast<const uint32_t *>(a.msg),
+                                                reinterpret_cast<uint32_t *>(nxt + l.msg), d.E, l.lgfb, fsrc, fcnt_n);
+            {
+                dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)std::min<int64_t>(l.W, 65535));
+                prep_synd_packed<<<grd, 256, 0, st>>>(a.sbits, l.W, F, d.M, l.W,
+                                                      reinterpret_cast<uint32_t *>(nxt + l.sbits), fsrc, fcnt_n);
+            }
+            Prepared pn;
+            bind(a, pn, nxt, l);
+            init_repacked<<<gF, 256, 0, st>>>(l.Fp, l.W, fcnt_n, a.active, pn.mask, a.iters_i, pn.unsat[0], pn.unsat[1]);
+            QKD_LAUNCHED("frame re-packing");
+            pr = pn;
+            cur = nxt;
+            fmap_cur = fmap_n;
+            fcnt_cur = fcnt_n;
+            if ((s = rebuild_blocks(l, cur, st)) != QKDREC_OK) return s;
         }
     }
     // stopping test on the final posteriors (parity buffer (T+1)&1 is clear)
@@ -1588,8 +1708,8 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
     a.early_stop = 1;
     check(T + 1, 0);
     QKD_LAUNCHED("check_flood(parity)");
-    return finish(d, F, T, prec, o, conv_prev, compact, ws, l, pr, a, (T + 1) & 1, bits_out, iters_out, conv_out,
-                  post_out, st);
+    return finish(d, F, T, prec, o, conv_prev, fmap_cur, fcnt_cur, cur, l, pr, a, (T + 1) & 1, bits_out, iters_out,
+                  conv_out, post_out, st);
 }
 
 #include "decode_layered.cuh"

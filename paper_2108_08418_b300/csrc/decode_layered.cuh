@@ -374,6 +374,7 @@ qkdrec_status run_layered(const CodeDev &d, const float *llr, const SyndIn &synd
     // final stopping test on the last posteriors: parity buffer (T+1)&1 is clear
     parity(T + 1);
     QKD_LAUNCHED("parity");
-    return finish(d, F, T, prec, o, conv_prev, compact, ws, l, pr, a, (T + 1) & 1, bits_out, iters_out, conv_out,
-                  post_out, st);
+    return finish(d, F, T, prec, o, conv_prev, compact ? reinterpret_cast<const int32_t *>(ws + l.fmap) : nullptr,
+                  compact ? reinterpret_cast<const int32_t *>(ws + l.fcnt) : nullptr, ws, l, pr, a, (T + 1) & 1,
+                  bits_out, iters_out, conv_out, post_out, st);
 }

@@ -11,7 +11,7 @@ static const char *kNames[kNumKinds] = {
     "check_flood_sp_f32", "check_flood_sp_f16", "check_flood_oms_f32", "check_flood_oms_f16",
     "check_flood_oms_i8", "parity_f32", "parity_i8", "var_flood_f32", "var_flood_f16", "var_flood_i8",
     "layer_oms_f32", "layer_oms_f16", "layer_oms_i8", "slice_llr", "quantise", "syndrome",
-    "prep", "finish", "woms_check_fwd", "woms_check_bwd", "woms_var", "plan_layered", "layer_qc_tma", "pack"};
+    "prep", "finish", "woms_check_fwd", "woms_check_bwd", "woms_var", "plan_layered", "layer_qc_tma", "pack", "repack"};
 
 struct Rec {
     int kind;

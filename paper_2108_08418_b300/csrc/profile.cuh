@@ -13,7 +13,7 @@ enum Kind {
     kLayerF32, kLayerF16, kLayerI8,
     kSliceLlr, kQuantise, kSyndrome,
     kPrep, kFinish,
-    kWomsFwd, kWomsBwd, kWomsVar, kPlan, kLayerQc, kPack,
+    kWomsFwd, kWomsBwd, kWomsVar, kPlan, kLayerQc, kPack, kRepack,
     kNumKinds
 };
 

@@ -67,3 +67,13 @@ def test_sweep_workload_names_its_rate_rule():
     assert "back-off rates" in bench.sweep_workload("backoff")
     assert "codes at 0.95 x slice capacity" not in bench.sweep_workload("backoff")
     assert "codes at 0.95 x slice capacity" in bench.sweep_workload("capacity")
+
+
+def test_block_work_model():
+    import numpy as np
+    t = np.array([1, 2, 3, 40, 5] * 10)            # 50 frames: two 32-frame blocks
+    assert bench.block_work(t, ()) == 32 * 40 + 32 * 40
+    # re-packed after iteration 16: one frame of the 10 with 40 passes per block
+    # row ... all ten long frames share one block from pass 17 on
+    assert bench.block_work(t, (16,)) == 32 * 16 * 2 + 32 * (40 - 16)
+    assert bench.block_work(np.array([3] * 64), (1, 2)) == 64 * 3
