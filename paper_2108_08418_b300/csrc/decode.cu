@@ -1281,7 +1281,7 @@ static Layout make_layout(const CodeDev &d, int32_t F, int algo, int prec) {
     return l;
 }
 
-// Iterations after which a flooding FP32 pass with the stopping test re-packs
+// Iterations after which a flooding pass with the stopping test re-packs
 // its still-decoding frames densely into the other half of its workspace (the
 // frame blocks then hold only decoding frames again).  A fixed schedule, so the
 // host always knows which half is live and the launches need no device
@@ -1290,7 +1290,8 @@ static Layout make_layout(const CodeDev &d, int32_t F, int algo, int prec) {
 // 0.87 after paying for the moves.
 constexpr int kCompactAt[] = {16, 32, 64};
 static bool compacts(const qkdrec_decode_opts &o, int algo, int prec) {
-    return o.early_stop && algo != QKDREC_OMS_LAYERED && prec == kF32 && o.max_iter > kCompactAt[0];
+    (void)prec;
+    return o.early_stop && algo != QKDREC_OMS_LAYERED && o.max_iter > kCompactAt[0];
 }
 
 static bool opts_ok(const qkdrec_decode_opts *o) {
@@ -1413,16 +1414,17 @@ __global__ void remap_frames(const int32_t *__restrict__ fsrc, const int32_t *__
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < c; p += (int64_t)gridDim.x * blockDim.x)
         fmap_new[p] = fmap_old ? fmap_old[fsrc[p]] : fsrc[p];
 }
-// 32-bit values of every item (variable or edge) of the re-packed frames:
-// one warp per (32 new positions, item), writes coalesced
-__global__ void gather_frames32(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, int64_t items,
-                                int lgfb, const int32_t *__restrict__ fsrc, const int32_t *__restrict__ cnt) {
+// The values (32-, 16- or 8-bit) of every item (variable or edge) of the
+// re-packed frames: one warp per (32 new positions, item), writes coalesced
+template <typename T>
+__global__ void gather_frames(const T *__restrict__ src, T *__restrict__ dst, int64_t items, int lgfb,
+                              const int32_t *__restrict__ fsrc, const int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t c = *cnt, words = (c + 31) >> 5, tasks = words * items;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tasks; t += wstride) {
         const int64_t w = t / items, item = t - w * items, p = (w << 5) + lane;
-        uint32_t v = 0;
+        T v = 0;
         if (p < c) v = src[fpos(item, items, __ldg(fsrc + p), lgfb)];
         dst[fpos(item, items, p, lgfb)] = v;
     }
@@ -1672,8 +1674,12 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
                                                                  pr.unsat[0], iters_out, conv_out, fmap_cur);
             {
                 dim3 blk(32, 8), grd((unsigned)ceil_div(d.n, 32), (unsigned)std::min<int64_t>(ceil_div(l.Fp, 32), 65535));
-                write_out<kF32><<<grd, blk, 0, st>>>(a.L, F, d.n, l.Fp, l.lgfb, o.llr_step, rmask, bits_out, post_out,
-                                                     fmap_cur, fcnt_cur);
+                if (prec == kI8)
+                    write_out<kI8><<<grd, blk, 0, st>>>(a.L, F, d.n, l.Fp, l.lgfb, o.llr_step, rmask, bits_out,
+                                                        post_out, fmap_cur, fcnt_cur);
+                else
+                    write_out<kF32><<<grd, blk, 0, st>>>(a.L, F, d.n, l.Fp, l.lgfb, o.llr_step, rmask, bits_out,
+                                                         post_out, fmap_cur, fcnt_cur);
             }
             int32_t *fsrc = reinterpret_cast<int32_t *>(nxt + l.fsrc), *fcnt_n = reinterpret_cast<int32_t *>(nxt + l.fcnt);
             int32_t *fmap_n = reinterpret_cast<int32_t *>(nxt + l.fmap);
@@ -1681,12 +1687,24 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
             list_active<<<(unsigned)ceil_div(l.Fp, 256), 256, 0, st>>>(l.Fp, a.active, fsrc, fcnt_n);
             remap_frames<<<gF, 256, 0, st>>>(fsrc, fcnt_n, fmap_cur, fmap_n);
             const unsigned gG = (unsigned)sm_count() * 16;
-            gather_frames32<<<gG, 256, 0, st>>>(reinterpret_cast<const uint32_t *>(a.llr_i),
-                                                reinterpret_cast<uint32_t *>(nxt + l.llr_i), d.n, l.lgfb, fsrc, fcnt_n);
-            gather_frames32<<<gG, 256, 0, st>>>(reinterpret_cast<const uint32_t *>(a.L),
-                                                reinterpret_cast<uint32_t *>(nxt + l.L), d.n, l.lgfb, fsrc, fcnt_n);
-            gather_frames32<<<gG, 256, 0, st>>>(reinterpret_cast<const uint32_t *>(a.msg),
-                                                reinterpret_cast<uint32_t *>(nxt + l.msg), d.E, l.lgfb, fsrc, fcnt_n);
+            // element sizes of the layout: channel values, posteriors, messages
+            auto gather = [&](size_t off, int64_t items, int bytes) {
+                if (bytes == 4)
+                    gather_frames<uint32_t><<<gG, 256, 0, st>>>(reinterpret_cast<const uint32_t *>(cur + off),
+                                                                reinterpret_cast<uint32_t *>(nxt + off), items,
+                                                                l.lgfb, fsrc, fcnt_n);
+                else if (bytes == 2)
+                    gather_frames<uint16_t><<<gG, 256, 0, st>>>(reinterpret_cast<const uint16_t *>(cur + off),
+                                                                reinterpret_cast<uint16_t *>(nxt + off), items,
+                                                                l.lgfb, fsrc, fcnt_n);
+                else
+                    gather_frames<uint8_t><<<gG, 256, 0, st>>>(reinterpret_cast<const uint8_t *>(cur + off),
+                                                               reinterpret_cast<uint8_t *>(nxt + off), items, l.lgfb,
+                                                               fsrc, fcnt_n);
+            };
+            gather(l.llr_i, d.n, prec == kI8 ? 1 : 4);
+            gather(l.L, d.n, prec == kI8 ? 2 : 4);
+            gather(l.msg, d.E, prec == kF32 ? 4 : (prec == kF16 ? 2 : 1));
             {
                 dim3 grd((unsigned)ceil_div(d.M, 8 * 64), (unsigned)std::min<int64_t>(l.W, 65535));
                 prep_synd_packed<<<grd, 256, 0, st>>>(a.sbits, l.W, F, d.M, l.W,

@@ -1,6 +1,7 @@
-"""Re-packing of the still-decoding frames during a flooding FP32 decode.
+"""Re-packing of the still-decoding frames during a flooding decode.
 
-After iterations 16, 32 and 64 the frames that have not stopped move, with
+After iterations 16, 32 and 64 (flooding schedule, every message precision)
+the frames that have not stopped move, with
 their messages, posteriors, channel values and syndrome bits, to the front of
 the other half of the workspace, and the stopped ones leave with their final
 outputs.  Every frame is decoded on its own, so where it sits must not change
@@ -31,14 +32,15 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("algo", ["sp_flood", "oms_flood"])
-def test_repacking_leaves_every_frame_unchanged(algo):
+@pytest.mark.parametrize("algo,prec", [("sp_flood", "f32"), ("oms_flood", "f32"), ("oms_flood", "f16"),
+                                       ("oms_flood", "i8"), ("sp_flood", "f16")])
+def test_repacking_leaves_every_frame_unchanged(algo, prec):
     n, F = 1024, 333
     rp, ci, _ = code(700, n, 0.5)
     b, llr = bpsk_frames(701, F, n, 0.9)          # near the threshold: 1 to 100 iterations
     c = q.Code(n, rp, ci)
     s = oracle.syndrome(rp, ci, b)
-    opts = q.DecodeOpts(algo=algo, max_iter=100)
+    opts = q.DecodeOpts(algo=algo, prec=prec, max_iter=100)
     res = []
     for perm in (np.arange(F), np.arange(F)[::-1], np.random.default_rng(2).permutation(F)):
         out = q.qkdrec_decode_batch(c, dev(llr[perm]), dev(s[perm]), opts, want_post=True)
