@@ -394,17 +394,21 @@ typedef struct {
  *                   pairs returns QKDREC_ERR_UNSUPPORTED)
  *   ctas_per_tile   1, 2, 4 or 8: CTAs of a thread-block cluster sharing one
  *                   tile (they split each layer's checks and meet at the
- *                   cluster barrier after every layer) */
+ *                   cluster barrier after every layer)
+ *   tiles_per_item  1, 2 or 4: tiles of one group a team decodes together,
+ *                   layer by layer, so one barrier interval holds that many
+ *                   tiles' checks of the layer */
 typedef struct {
     int32_t frames_per_tile;
     int32_t threads_per_cta;
     int32_t stage_depth;
     int32_t ctas_per_tile;
+    int32_t tiles_per_item;
 } qkdrec_tuning;
 
 typedef struct qkdrec_plan_s *qkdrec_plan_t;
 
-/* Defaults: 32 frames per tile, 512 threads, depth 8, 4 CTAs per tile. */
+/* Defaults: 32 frames per tile, 512 threads, depth 8, 4 CTAs per tile, 1 tile per item. */
 void qkdrec_tuning_default(qkdrec_tuning *tuning);
 
 /*

@@ -45,8 +45,10 @@ struct PlanGroup {
 };
 
 struct PlanItem {
-    int32_t g, tile;
+    int32_t g, tile, ntiles;   // tiles tile .. tile + ntiles - 1 of group g, decoded together
 };
+
+constexpr int kPlanMaxTiles = 4;   // tiles of one work item
 
 struct PlanArgs {
     const PlanGroup *groups;
@@ -75,8 +77,12 @@ struct PlanCount {
     unsigned long long units = 0, units_first = 0, punits = 0;
 };
 
-// Decode one work item with a team of tcs CTAs (trank = this CTA's place in the
-// team; unsat_dst = the team leader's shared stopping-test word).
+// Decode one work item -- K tiles of one group -- with a team of tcs CTAs
+// (trank = this CTA's place in the team; unsat_dst = the team leader's shared
+// stopping-test words, one per tile).  The K tiles run their layers in step:
+// between two barriers every warp handles its checks of the layer for each
+// tile in turn, so a layer with few checks still gives the team K times the
+// work per barrier.  Each tile's arithmetic is that of a one-tile item.
 template <int CH>
 __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, int trank, uint32_t *unsat_dst,
                                           uint32_t *s_unsat, float *qst, PlanCount &cnt) {
@@ -89,118 +95,141 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
     uint32_t units = 0, units_first = 0, punits = 0;   // this item's share (added to cnt at the end)
     const PlanItem itm = a.items[item];
     const PlanGroup &G = a.groups[itm.g];
-    const int n = G.n, M = G.M;
-    const int f0 = itm.tile * FT, nf = min(FT, G.F - f0);
-    char *tb = a.ws + G.ws_off + (int64_t)itm.tile * G.tile_bytes;
-    float *L = reinterpret_cast<float *>(tb);
-    float *msg = reinterpret_cast<float *>(tb + align_up((size_t)n * FT * 4, 256));
-    uint32_t *sw = reinterpret_cast<uint32_t *>(tb + align_up((size_t)n * FT * 4, 256) +
-                                                align_up((size_t)G.E * FT * 4, 256));
-    // ---- load the tile: L[v][i] = llr[f0 + i][v] through a per-warp transpose
+    const int n = G.n, M = G.M, K = itm.ntiles;
+    int f0[kPlanMaxTiles], nf[kPlanMaxTiles];
+    float *Lt[kPlanMaxTiles], *mt[kPlanMaxTiles];
+    uint32_t *swt[kPlanMaxTiles], active[kPlanMaxTiles];   // active: same value in every thread
+#pragma unroll
+    for (int k = 0; k < kPlanMaxTiles; ++k) {
+        const int tile = itm.tile + min(k, K - 1);
+        f0[k] = tile * FT;
+        nf[k] = k < K ? min(FT, G.F - f0[k]) : 0;
+        char *tb = a.ws + G.ws_off + (int64_t)tile * G.tile_bytes;
+        Lt[k] = reinterpret_cast<float *>(tb);
+        mt[k] = reinterpret_cast<float *>(tb + align_up((size_t)n * FT * 4, 256));
+        swt[k] = reinterpret_cast<uint32_t *>(tb + align_up((size_t)n * FT * 4, 256) + align_up((size_t)G.E * FT * 4, 256));
+        active[k] = nf[k] == 32 ? 0xffffffffu : ((1u << nf[k]) - 1u);
+    }
+    // ---- load the tiles: L[v][i] = llr[f0 + i][v] through a per-warp transpose
     // (swizzled columns, conflict-free), padding frames get a confident 0
-    for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
-        const int64_t v = v0 + lane;
-        for (int i = 0; i < FT; ++i)
-            tr[i * 32 + (lane ^ i)] = (i < nf && v < n) ? __ldg(G.llr + (int64_t)(f0 + i) * n + v) : kLlrClip;
-        __syncwarp();
-        for (int idx = lane; idx < 32 * FT; idx += 32) {
-            const int j = idx / FT, fi = idx - j * FT;
-            if (v0 + j < n) __stcg(L + (v0 + j) * FT + fi, tr[fi * 32 + (j ^ fi)]);
-        }
-        __syncwarp();
-    }
-    for (int64_t c = gt; c < M; c += TT) {
-        uint32_t w = 0;
-#pragma unroll 8
-        for (int i = 0; i < nf; ++i) w |= (uint32_t)(__ldg(G.synd + (int64_t)(f0 + i) * M + c) & 1) << i;
-        __stcg(sw + c, w);
-    }
-    uint32_t active = nf == 32 ? 0xffffffffu : ((1u << nf) - 1u);   // same value in every thread
-    plan_sync(tcs);
-    // ---- stopping test of the tile's current posteriors: frames failing a
-    // check are OR-ed into the leader's word
-    auto parity = [&]() {
-        uint32_t bad = 0;
-        if (fl < nf && ((active >> fl) & 1u)) {
-            for (int c = gw * slots + slot; c < M; c += TW * slots) {
-                uint32_t par = (__ldcg(sw + c) >> fl) & 1u;
-                const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
-                // CH gathers in flight (indices past the last edge clamped to it)
-                for (int k0 = 0; k0 < d; k0 += CH) {
-                    float Lv[CH];
-#pragma unroll
-                    for (int j = 0; j < CH; ++j)
-                        Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + beg + min(k0 + j, d - 1)) * FT + fl));
-#pragma unroll
-                    for (int j = 0; j < CH; ++j)
-                        if (k0 + j < d) par ^= (uint32_t)(Lv[j] < 0.0f);
-                }
-                bad |= par << fl;
-                punits += d;
+    for (int k = 0; k < K; ++k) {
+        float *L = Lt[k];
+        for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
+            const int64_t v = v0 + lane;
+            for (int i = 0; i < FT; ++i)
+                tr[i * 32 + (lane ^ i)] = (i < nf[k] && v < n) ? __ldg(G.llr + (int64_t)(f0[k] + i) * n + v) : kLlrClip;
+            __syncwarp();
+            for (int idx = lane; idx < 32 * FT; idx += 32) {
+                const int j = idx / FT, fi = idx - j * FT;
+                if (v0 + j < n) __stcg(L + (v0 + j) * FT + fi, tr[fi * 32 + (j ^ fi)]);
             }
+            __syncwarp();
         }
-        bad = __reduce_or_sync(0xffffffffu, bad);
-        if (lane == 0 && bad) atomicOr(unsat_dst, bad);
+        for (int64_t c = gt; c < M; c += TT) {
+            uint32_t w = 0;
+#pragma unroll 8
+            for (int i = 0; i < nf[k]; ++i) w |= (uint32_t)(__ldg(G.synd + (int64_t)(f0[k] + i) * M + c) & 1) << i;
+            __stcg(swt[k] + c, w);
+        }
+    }
+    plan_sync(tcs);
+    // ---- stopping test of the tiles' current posteriors: frames failing a
+    // check are OR-ed into the leader's word of their tile
+    auto parity = [&]() {
+        for (int k = 0; k < K; ++k) {
+            uint32_t bad = 0;
+            if (fl < nf[k] && ((active[k] >> fl) & 1u)) {
+                const float *L = Lt[k];
+                for (int c = gw * slots + slot; c < M; c += TW * slots) {
+                    uint32_t par = (__ldcg(swt[k] + c) >> fl) & 1u;
+                    const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
+                    // CH gathers in flight (indices past the last edge clamped to it)
+                    for (int k0 = 0; k0 < d; k0 += CH) {
+                        float Lv[CH];
+#pragma unroll
+                        for (int j = 0; j < CH; ++j)
+                            Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + beg + min(k0 + j, d - 1)) * FT + fl));
+#pragma unroll
+                        for (int j = 0; j < CH; ++j)
+                            if (k0 + j < d) par ^= (uint32_t)(Lv[j] < 0.0f);
+                    }
+                    bad |= par << fl;
+                    punits += d;
+                }
+            }
+            bad = __reduce_or_sync(0xffffffffu, bad);
+            if (lane == 0 && bad) atomicOr(unsat_dst + k, bad);
+        }
     };
     // retire the frames whose test passed (iterations executed: t)
     auto retire = [&](int t) {
         plan_sync(tcs);
-        const uint32_t u = *reinterpret_cast<volatile uint32_t *>(unsat_dst);
-        const uint32_t done = active & ~u;
-        if (trank == 0 && tid < nf && ((done >> tid) & 1u)) G.iters[f0 + tid] = t;
-        active &= u;
-        plan_sync(tcs);   // every CTA has read the word before it is cleared
-        if (trank == 0 && tid == 0) *s_unsat = 0;
+        for (int k = 0; k < K; ++k) {
+            const uint32_t u = reinterpret_cast<volatile uint32_t *>(unsat_dst)[k];
+            const uint32_t done = active[k] & ~u;
+            if (trank == 0 && tid < nf[k] && ((done >> tid) & 1u)) G.iters[f0[k] + tid] = t;
+            active[k] &= u;
+        }
+        plan_sync(tcs);   // every CTA has read the words before they are cleared
+        if (trank == 0 && tid < K) s_unsat[tid] = 0;
+    };
+    auto any_active = [&]() {
+        uint32_t x = 0;
+        for (int k = 0; k < K; ++k) x |= active[k];
+        return x != 0;
     };
     if (a.early_stop) {
         parity();
         retire(0);
     }
-    for (int t = 1; t <= a.max_iter && active; ++t) {
+    for (int t = 1; t <= a.max_iter && any_active(); ++t) {
         const bool first = t == 1;
         for (int ly = 0; ly < G.n_layers; ++ly) {
             const int32_t lb = __ldg(G.lptr + ly), le = __ldg(G.lptr + ly + 1);
-            const bool live = fl < nf && ((active >> fl) & 1u);
-            for (int32_t kk = lb + gw * slots + slot; live && kk < le; kk += TW * slots) {
+            for (int32_t kk = lb + gw * slots + slot; kk < le; kk += TW * slots) {
                 const int32_t c = __ldg(G.lchk + kk);
                 const int32_t beg = __ldg(G.rp + c), d = __ldg(G.rp + c + 1) - beg;
-                uint32_t neg = (__ldcg(sw + c) >> fl) & 1u;
-                float mn1 = INFINITY, mn2 = INFINITY;
-                int32_t arg = -1;
-                units += d;
-                if (first) units_first += d;
-                // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
-                for (int k0 = 0; k0 < d; k0 += CH) {
-                    float Lv[CH], mo[CH];
+                for (int k = 0; k < K; ++k) {
+                    if (!(fl < nf[k] && ((active[k] >> fl) & 1u))) continue;
+                    float *L = Lt[k], *msg = mt[k];
+                    uint32_t neg = (__ldcg(swt[k] + c) >> fl) & 1u;
+                    float mn1 = INFINITY, mn2 = INFINITY;
+                    int32_t arg = -1;
+                    units += d;
+                    if (first) units_first += d;
+                    // pass 1: q = L - m on every edge (CH loads in flight, indices clamped)
+                    for (int k0 = 0; k0 < d; k0 += CH) {
+                        float Lv[CH], mo[CH];
 #pragma unroll
-                    for (int j = 0; j < CH; ++j) {
-                        const int32_t e = beg + min(k0 + j, d - 1);
-                        Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl));
-                        mo[j] = first ? 0.0f : __ldcs(msg + ((uint32_t)e * FT + fl));
-                    }
+                        for (int j = 0; j < CH; ++j) {
+                            const int32_t e = beg + min(k0 + j, d - 1);
+                            Lv[j] = __ldcg(L + ((uint32_t)__ldg(G.ci + e) * FT + fl));
+                            mo[j] = first ? 0.0f : __ldcs(msg + ((uint32_t)e * FT + fl));
+                        }
 #pragma unroll
-                    for (int j = 0; j < CH; ++j) {
-                        const int k = k0 + j;
-                        if (k >= d) break;
-                        const float q = Lv[j] - mo[j];
-                        if (k < kStash) my[k * 32] = q;
-                        neg ^= (uint32_t)(q < 0.0f);
-                        const float m = fabsf(q);
-                        if (m < mn1) { mn2 = mn1; mn1 = m; arg = k; }
-                        else if (m < mn2) mn2 = m;
+                        for (int j = 0; j < CH; ++j) {
+                            const int kq = k0 + j;
+                            if (kq >= d) break;
+                            const float q = Lv[j] - mo[j];
+                            if (kq < kStash) my[kq * 32] = q;
+                            neg ^= (uint32_t)(q < 0.0f);
+                            const float m = fabsf(q);
+                            if (m < mn1) { mn2 = mn1; mn1 = m; arg = kq; }
+                            else if (m < mn2) mn2 = m;
+                        }
                     }
-                }
-                // pass 2: new messages and posteriors L = q + m
-                for (int k = 0; k < d; ++k) {
-                    const int32_t e = beg + k;
-                    float *Lp = L + ((uint32_t)__ldg(G.ci + e) * FT + fl);
-                    float *mp = msg + ((uint32_t)e * FT + fl);
-                    // edges beyond the stash: L and m of this edge are still unchanged
-                    const float q = k < kStash ? my[k * 32] : __ldcg(Lp) - (first ? 0.0f : __ldcs(mp));
-                    const float mag = fmaxf(((k == arg) ? mn2 : mn1) - a.beta, 0.0f);
-                    const float mn = ((neg ^ (uint32_t)(q < 0.0f)) & 1u) ? -mag : mag;
-                    __stcs(mp, mn);
-                    __stcg(Lp, q + mn);
+                    // pass 2: new messages and posteriors L = q + m
+                    for (int kq = 0; kq < d; ++kq) {
+                        const int32_t e = beg + kq;
+                        float *Lp = L + ((uint32_t)__ldg(G.ci + e) * FT + fl);
+                        float *mp = msg + ((uint32_t)e * FT + fl);
+                        // edges beyond the stash: L and m of this edge are still unchanged
+                        const float q = kq < kStash ? my[kq * 32] : __ldcg(Lp) - (first ? 0.0f : __ldcs(mp));
+                        const float mag = fmaxf(((kq == arg) ? mn2 : mn1) - a.beta, 0.0f);
+                        const float mn = ((neg ^ (uint32_t)(q < 0.0f)) & 1u) ? -mag : mag;
+                        __stcs(mp, mn);
+                        __stcg(Lp, q + mn);
+                    }
                 }
             }
             plan_sync(tcs);
@@ -215,22 +244,25 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
         retire(0);
     }
     // ---- outputs: frames still active never satisfied the syndrome
-    if (trank == 0 && tid < nf) {
-        const bool act = (active >> tid) & 1u;
-        G.conv[f0 + tid] = act ? 0 : 1;
-        if (act) G.iters[f0 + tid] = a.max_iter;
-    }
-    for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
-        for (int idx = lane; idx < 32 * FT; idx += 32) {
-            const int j = idx / FT, fi = idx - j * FT;
-            tr[fi * 32 + (j ^ fi)] = v0 + j < n ? __ldcg(L + (v0 + j) * FT + fi) : 0.0f;
+    for (int k = 0; k < K; ++k) {
+        if (trank == 0 && tid < nf[k]) {
+            const bool act = (active[k] >> tid) & 1u;
+            G.conv[f0[k] + tid] = act ? 0 : 1;
+            if (act) G.iters[f0[k] + tid] = a.max_iter;
         }
-        __syncwarp();
-        const int64_t v = v0 + lane;
-        if (v < n)
-            for (int i = 0; i < nf; ++i)
-                G.bits[(int64_t)(f0 + i) * n + v] = tr[i * 32 + (lane ^ i)] < 0.0f ? 1 : 0;
-        __syncwarp();
+        const float *L = Lt[k];
+        for (int64_t v0 = (int64_t)gw * 32; v0 < n; v0 += (int64_t)TW * 32) {
+            for (int idx = lane; idx < 32 * FT; idx += 32) {
+                const int j = idx / FT, fi = idx - j * FT;
+                tr[fi * 32 + (j ^ fi)] = v0 + j < n ? __ldcg(L + (v0 + j) * FT + fi) : 0.0f;
+            }
+            __syncwarp();
+            const int64_t v = v0 + lane;
+            if (v < n)
+                for (int i = 0; i < nf[k]; ++i)
+                    G.bits[(int64_t)(f0[k] + i) * n + v] = tr[i * 32 + (lane ^ i)] < 0.0f ? 1 : 0;
+            __syncwarp();
+        }
     }
     cnt.units += units;
     cnt.units_first += units_first;
@@ -244,14 +276,14 @@ __global__ void __launch_bounds__(NT, 1)
 plan_layered_kernel(PlanArgs a) {
     extern __shared__ float qst[];  // [warps][kStash][32]: q stash; 32 x 32 transposes
     __shared__ int s_item;
-    __shared__ uint32_t s_unsat;
+    __shared__ uint32_t s_unsat[kPlanMaxTiles];
     const int tid = threadIdx.x;
     const int CS = a.CS;
     const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
     volatile int *item_src = CS > 1 ? cg::this_cluster().map_shared_rank(&s_item, 0) : &s_item;
-    uint32_t *unsat_dst = CS > 1 ? cg::this_cluster().map_shared_rank(&s_unsat, 0) : &s_unsat;
+    uint32_t *unsat_dst = CS > 1 ? cg::this_cluster().map_shared_rank(s_unsat, 0) : s_unsat;
     PlanCount cnt;
-    if (tid == 0) s_unsat = 0;
+    if (tid < kPlanMaxTiles) s_unsat[tid] = 0;
     for (;;) {
         if (rank == 0 && tid == 0) s_item = atomicAdd(a.head, 1);
         plan_sync(CS);
@@ -260,7 +292,7 @@ plan_layered_kernel(PlanArgs a) {
             plan_sync(CS);   // no CTA leaves while another may still read the leader's word
             break;
         }
-        plan_item<CH>(a, item, CS, rank, unsat_dst, &s_unsat, qst, cnt);
+        plan_item<CH>(a, item, CS, rank, unsat_dst, s_unsat, qst, cnt);
         plan_sync(CS);   // the tile is finished in every CTA before the leader takes the next
     }
     // per edge-frame update: posterior and message read and written (16 B; the
@@ -293,6 +325,7 @@ static const int kPlanThreads[] = {256, 512, 1024};
 static const int kPlanDepth[] = {4, 8, 16};
 static int plan_max_threads(int depth) { return depth == 4 ? 1024 : (depth == 8 ? 512 : 256); }
 static const int kPlanCS[] = {1, 2, 4, 8};
+static const int kPlanTiles[] = {1, 2, 4};
 
 template <size_t N>
 static bool in_set(int v, const int (&set)[N]) {
@@ -303,7 +336,8 @@ static bool in_set(int v, const int (&set)[N]) {
 
 static bool tuning_ok(const qkdrec_tuning &t) {
     return in_set(t.frames_per_tile, kPlanFT) && in_set(t.threads_per_cta, kPlanThreads) &&
-           in_set(t.stage_depth, kPlanDepth) && in_set(t.ctas_per_tile, kPlanCS);
+           in_set(t.stage_depth, kPlanDepth) && in_set(t.ctas_per_tile, kPlanCS) &&
+           in_set(t.tiles_per_item, kPlanTiles);
 }
 
 static size_t plan_ws_bytes(const std::vector<qkdrec_group> &gs, int FT) {
@@ -344,9 +378,11 @@ static qkdrec_status plan_build(qkdrec_plan_s &p) {
         G.F = g.frames;
         G.dc_max = d.dc_max;
         const int tiles = (int)ceil_div(g.frames, FT);
-        for (int t = 0; t < tiles; ++t) {
-            const double c = (double)d.E * (double)std::min(FT, g.frames - t * FT);
-            items.push_back(PlanItem{(int32_t)i, t});
+        const int K = p.tuning.tiles_per_item;
+        for (int t = 0; t < tiles; t += K) {
+            const int nk = std::min(K, tiles - t);
+            const double c = (double)d.E * (double)std::min(FT * nk, g.frames - t * FT);
+            items.push_back(PlanItem{(int32_t)i, t, nk});
             cost.push_back(c + 1e-3 * (double)d.n_layers);
         }
         off += (int64_t)tiles * G.tile_bytes;
@@ -450,6 +486,7 @@ void qkdrec_tuning_default(qkdrec_tuning *t) {
     t->threads_per_cta = 512;
     t->stage_depth = 8;
     t->ctas_per_tile = 4;
+    t->tiles_per_item = 1;
 }
 
 qkdrec_status qkdrec_plan_create(const qkdrec_group *groups, int32_t n_groups, const qkdrec_decode_opts *opts,
@@ -559,17 +596,21 @@ qkdrec_status qkdrec_plan_autotune(qkdrec_plan_t p, void *workspace, size_t work
     };
     qkdrec_status s = QKDREC_OK;
     for (int ft : kPlanFT) {
-        p->tuning.frames_per_tile = ft;
-        if ((s = plan_build(*p)) != QKDREC_OK) break;
-        for (int cs : kPlanCS)
-            for (int th : kPlanThreads)
-                for (int dep : kPlanDepth) {
-                    if (s != QKDREC_OK) continue;
-                    p->tuning.ctas_per_tile = cs;
-                    p->tuning.threads_per_cta = th;
-                    p->tuning.stage_depth = dep;
-                    if (trial() < 0) s = QKDREC_ERR_CUDA;
-                }
+        for (int nk : kPlanTiles) {
+            p->tuning.frames_per_tile = ft;
+            p->tuning.tiles_per_item = nk;
+            if ((s = plan_build(*p)) != QKDREC_OK) break;
+            for (int cs : kPlanCS)
+                for (int th : kPlanThreads)
+                    for (int dep : kPlanDepth) {
+                        if (s != QKDREC_OK) continue;
+                        p->tuning.ctas_per_tile = cs;
+                        p->tuning.threads_per_cta = th;
+                        p->tuning.stage_depth = dep;
+                        if (trial() < 0) s = QKDREC_ERR_CUDA;
+                    }
+            if (s != QKDREC_OK) break;
+        }
         if (s != QKDREC_OK) break;
     }
     cudaEventDestroy(e0);

@@ -94,7 +94,11 @@ TUNINGS = [None,
            dict(frames_per_tile=16, threads_per_cta=512, stage_depth=4, ctas_per_tile=2),
            dict(frames_per_tile=32, threads_per_cta=1024, stage_depth=4, ctas_per_tile=8),
            dict(frames_per_tile=32, threads_per_cta=256, stage_depth=16, ctas_per_tile=1),
-           dict(frames_per_tile=8, threads_per_cta=512, stage_depth=8, ctas_per_tile=4)]
+           dict(frames_per_tile=8, threads_per_cta=512, stage_depth=8, ctas_per_tile=4),
+           # several tiles of a group decoded together, layer by layer (ragged last item)
+           dict(frames_per_tile=8, threads_per_cta=256, stage_depth=4, ctas_per_tile=2, tiles_per_item=2),
+           dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=4, ctas_per_tile=8, tiles_per_item=4),
+           dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=1, tiles_per_item=4)]
 
 
 def make_groups(spec, seed=800):
@@ -219,6 +223,7 @@ def test_plan_autotune_picks_a_supported_tuning_and_keeps_results():
     assert best["threads_per_cta"] in (256, 512, 1024)
     assert best["stage_depth"] in (4, 8, 16)
     assert best["ctas_per_tile"] in (1, 2, 4, 8)
+    assert best["tiles_per_item"] in (1, 2, 4)
     assert ms > 0 and plan.tuning() == best
     plan.launch(ws)
     torch.cuda.synchronize()
@@ -237,6 +242,8 @@ def test_plan_rejects_unsupported_options_and_small_workspace():
         q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(frames_per_tile=4))
     with pytest.raises(RuntimeError):
         q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(ctas_per_tile=3))
+    with pytest.raises(RuntimeError):
+        q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(tiles_per_item=3))
     deep = q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(stage_depth=16, threads_per_cta=512))
     with pytest.raises(RuntimeError):          # depth 16 runs at most 256 threads per CTA
         deep.launch(deep.workspace())
