@@ -1307,6 +1307,7 @@ CASES = {
     "decode_oms_f32": dict(logn=16, frames=512, rate=0.84375, algo="oms_flood", prec="f32", iters=5),
     "decode_layered_f32": dict(logn=16, frames=512, rate=0.84375, algo="oms_layered", prec="f32", iters=5),
     "decode_oms_i8": dict(logn=16, frames=512, rate=0.84375, algo="oms_flood", prec="i8", iters=5),
+    "decode_oms_f16": dict(logn=16, frames=512, rate=0.84375, algo="oms_flood", prec="f16", iters=5),
     # the plan decoder on a small uneven batch: 96 frames of n = 2^16, 192 of 2^14, 384 of 2^12
     # (rate 0.84375; ~0.9 GB on the device)
     # layered min-sum of a quasi-cyclic code (Z = 2^13, 3 x 8 base matrix: n = 2^16, rate 0.625),
