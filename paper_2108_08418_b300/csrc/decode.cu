@@ -1640,7 +1640,9 @@ static qkdrec_status run_flood(const CodeDev &d, const float *llr, const SyndIn 
     char *cur = ws;
     const int32_t *fmap_cur = compact ? reinterpret_cast<const int32_t *>(ws + l.fmap) : nullptr;
     const int32_t *fcnt_cur = compact ? reinterpret_cast<const int32_t *>(ws + l.fcnt) : nullptr;
-    const bool repack = compacts(o, o.algo, prec);
+    // a re-decode pass holds only frames a first pass could not solve, which
+    // mostly run every iteration: re-packing them would move them for nothing
+    const bool repack = compacts(o, o.algo, prec) && !compact;
     const int64_t vitems = (int64_t)d.n * l.FV;
     const unsigned vgrid = (unsigned)std::min<int64_t>(ceil_div(vitems, 256), (int64_t)sm_count() * 64);
     // integer form: (variable, 16 frames) on x, listed frame blocks on y; FP16
