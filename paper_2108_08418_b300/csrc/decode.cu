@@ -1330,7 +1330,7 @@ static size_t workspace_for(const CodeDev &d, int32_t F, const qkdrec_decode_opt
     size_t b = make_layout(d, F, o->algo, o->prec).total * (compacts(*o, o->algo, o->prec) ? 2 : 1);
     if (o->fallback_f32 && o->prec != kF32) {
         const int algo = o->fallback_f32 == 2 ? QKDREC_SP_FLOOD : o->algo;
-        size_t b32 = make_layout(d, F, algo, kF32).total * (compacts(*o, algo, kF32) ? 2 : 1);
+        size_t b32 = make_layout(d, F, algo, kF32).total;   // the re-decode pass does not re-pack
         if (b32 > b) b = b32;
     }
     return b;
