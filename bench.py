@@ -1311,6 +1311,8 @@ CASES = {
     # the slice LLR kernel on 2^24 samples of the sweep's data (SNR 3, slice 2, Bob's
     # lower slices): the small case for ncu
     "slice_llr": dict(llr=(3.0, 2), count=1 << 24),
+    # the same kernel on the top slice at SNR 15 (two candidates per sample)
+    "slice_llr_j4": dict(llr=(15.0, 4), count=1 << 24),
     # one slice decode of the sweep at n = 2^16 and 512 frames (edge messages 400 MB,
     # larger than L2; ~1 GB on the device): the small case for ncu --set full
     "decode_sp_f32": dict(logn=16, frames=512, rate=0.84375, algo="sp_flood", prec="f32", iters=5),

@@ -30,6 +30,16 @@ qkdrec_status qkdrec_selftest_phi(const float *x, int64_t count, float *out, voi
  */
 qkdrec_status qkdrec_selftest_phi_pair(const float *x, int64_t count, float *out, void *stream);
 
+/*
+ * out[i] = Q(|z[i]|), the Gaussian upper tail P(N(0,1) > |z|), as the slice LLR
+ * kernel evaluates it at a standardised interval bound (Sec. III-B step 4:
+ * P(k | x) is the Gaussian mass of interval k), pairs of values in packed
+ * FP32x2 arithmetic.
+ *   z, out  DEVICE float [count], 8-byte aligned; count even.
+ * Errors: QKDREC_ERR_ARG (count odd or < 0, NULL, misaligned).
+ */
+qkdrec_status qkdrec_selftest_gauss_tail(const float *z, int64_t count, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

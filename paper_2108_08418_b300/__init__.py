@@ -43,7 +43,7 @@ EXPORTED = [
     "qkdrec_quantiser_range", "qkdrec_reconcile", "qkdrec_reconcile_workspace_size", "qkdrec_pack_bits",
     "qkdrec_unpack_bits", "qkdrec_reconciliation_efficiency", "qkdrec_nr_optimise", "qkdrec_nr_key_rate",
 ]
-SELFTEST = ["qkdrec_selftest_phi", "qkdrec_selftest_phi_pair"]
+SELFTEST = ["qkdrec_selftest_phi", "qkdrec_selftest_phi_pair", "qkdrec_selftest_gauss_tail"]
 
 
 class QkdrecError(RuntimeError):
@@ -156,6 +156,7 @@ def lib():
         "qkdrec_profile_begin": (U, []),
         "qkdrec_selftest_phi": (U, [P, I64, P, P]),
         "qkdrec_selftest_phi_pair": (U, [P, I64, P, P]),
+        "qkdrec_selftest_gauss_tail": (U, [P, I64, P, P]),
         "qkdrec_profile_end": (U, [P, I32, P]),
         "qkdrec_last_error": (ctypes.c_char_p, []),
         "qkdrec_version": (ctypes.c_char_p, []),
@@ -797,4 +798,14 @@ def qkdrec_selftest_phi_pair(x):
     xp = _dev(x, torch.float32, "x")
     out = torch.empty_like(x)
     _check(lib().qkdrec_selftest_phi_pair(xp, x.numel(), ctypes.c_void_p(out.data_ptr()), _stream(x)))
+    return out
+
+
+def qkdrec_selftest_gauss_tail(z):
+    """Q(|z|) = P(N(0,1) > |z|) as the slice LLR kernel evaluates it (z: float32 CUDA
+    tensor of even length)."""
+    torch = _torch()
+    zp = _dev(z, torch.float32, "z")
+    out = torch.empty_like(z)
+    _check(lib().qkdrec_selftest_gauss_tail(zp, z.numel(), ctypes.c_void_p(out.data_ptr()), _stream(z)))
     return out

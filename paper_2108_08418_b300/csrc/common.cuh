@@ -49,6 +49,24 @@ constexpr float kAMax = 30.0f;
 constexpr int kQMax = 31;
 constexpr int kPMax = 32767;
 
+// The MUFU approximations (PTX ex2/lg2/rcp .approx.ftz): about 2 ulp relative.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 // Parity-check matrix with device copies (one per slice; shared by all frames).
 struct CodeDev {
     int32_t n = 0, M = 0;

@@ -170,21 +170,6 @@ template <> __device__ __forceinline__ uint32_t active_bits<4>(const uint8_t *p)
 //   0.03 <= x < 2   : phi = log2((1 + u)/(1 - u)) ln 2, 1 - u >= 0.0296;
 //   x < 0.03        : coth(y) y = 1 + y^2/3 - y^4/45 + ..., so with y = x/2
 //                     phi = ln(2/x) + x^2/12 - 7 x^4/1440 + O(x^6).
-__device__ __forceinline__ float ex2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-    float r;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 __device__ __forceinline__ float phi_fast(float x) {
     const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
     const float u = ex2_approx(-x * kLog2e);
@@ -436,7 +421,6 @@ check_flood_f(DecArgs a) {
 // x (1 - x/2 + x^2/6 - x^3/24 + x^4/120) (relative truncation < 1.4e-8), so
 //   x >= 2 : phi = 2u (1 + u^2/3 + u^4/5 + u^6/7),  u = e^-x,
 //   x <  2 : phi = ln((1 + u) / (1 - u)).
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 phi2(float2 x) {
     const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
     const float2 t = __fmul2_rn(x, f2(-kLog2e));

@@ -67,7 +67,7 @@ def test_quantiser_empty_and_ragged():
 
 # ------------------------------------------------------------------ slice LLR
 @pytest.mark.parametrize("snr,m,label", [(3.0, 4, "gray"), (15.0, 5, "gray"), (3.0, 5, "binary"),
-                                         (2.0, 6, "gray")])
+                                         (2.0, 6, "gray"), (30.0, 8, "gray"), (8.0, 7, "binary")])
 def test_slice_llr_vs_oracle(snr, m, label):
     lo, hi = oracle.quantiser_range(snr)
     sn = snr ** -0.5
