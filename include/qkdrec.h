@@ -186,12 +186,21 @@ qkdrec_status qkdrec_quantise_slices(const float *y, int64_t count, int32_t m_sl
  *             reconciled lower bits of sample i },
  *   P(k | x) = Phi((t_{k+1} - x)/sigma_n) - Phi((t_k - x)/sigma_n), t_0 = -inf,
  *   t_{2^m} = +inf, the thresholds of qkdrec_quantise_slices.
- * The result is clipped to [-30, 30].  Interval probabilities are evaluated
- * in FP32 in the log domain (Gaussian tails through the scaled complementary
- * error function, so no tail underflows); when every candidate of both sets
- * lies in the far tail (nearest term below e^-50) the two set sums are formed
- * in FP64.  Terms below e^-25 of their set's nearest term, and a set that
- * cannot move the clipped result, are skipped.
+ * The result is clipped to [-30, 30].  Three evaluation paths, chosen per
+ * sample from each set's nearest candidate (distance d in units of sigma_n):
+ *  - saturation: bounds on the two set masses (above: |K_b| times the nearest
+ *    term's Gaussian bound; below: a strip of the interval's width at d + width)
+ *    show one set more than e^30 below the other -> +-30, no tail evaluated;
+ *  - linear FP32 (both nearest candidates within 9 sigma, the common case):
+ *    P(k | x) as differences of Gaussian upper tails Q, each from a fitted
+ *    Mills ratio (about 1.2e-6 relative), over every candidate or over the
+ *    window of candidates whose bound is within e^-16 of its set's lower
+ *    bound; L = ln(S0 / S1);
+ *  - log domain (a nearest candidate beyond 9 sigma, e.g. wrong lower bits):
+ *    each set summed relative to its nearest term in FP32 through the scaled
+ *    complementary error function, terms below e^-25 of it skipped, and in
+ *    FP64 when both sets lie below e^-50.
+ * The result is within 1e-4 max(|L|, 1) of the exact value.
  *   x           DEVICE float [count]       Alice's quadratures.
  *   lower_bits  DEVICE uint8 [j][count]    reconciled slices 0..j-1 (NULL iff j = 0).
  *   llr_out     DEVICE float [count].
