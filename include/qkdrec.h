@@ -396,28 +396,41 @@ typedef struct {
 } qkdrec_group;
 
 /* Launch shape of a plan; the autotuner searches all combinations.
- *   frames_per_tile 8, 16 or 32: frames decoded together (lanes per check)
+ *   frames_per_tile 8, 16 or 32: frames decoded together
+ *   frames_per_lane 1, 2 or 4, with frames_per_tile / frames_per_lane >= 8:
+ *                   frames one lane updates together (2- or 4-wide loads);
+ *                   a check of a tile is served by frames_per_tile /
+ *                   frames_per_lane lanes
  *   threads_per_cta 256, 512 or 1024
  *   stage_depth     4, 8 or 16: edge loads in flight per lane; with at most
- *                   1024, 512 or 256 threads per CTA (a launch outside these
- *                   pairs returns QKDREC_ERR_UNSUPPORTED)
+ *                   1024, 512 or 256 threads per CTA at one frame per lane,
+ *                   512 or 256 (depth 4 or 8) at two or four (a launch
+ *                   outside these pairs returns QKDREC_ERR_UNSUPPORTED)
  *   ctas_per_tile   1, 2, 4 or 8: CTAs of a thread-block cluster sharing one
  *                   tile (they split each layer's checks and meet at the
  *                   cluster barrier after every layer)
  *   tiles_per_item  1, 2 or 4: tiles of one group a team decodes together,
  *                   layer by layer, so one barrier interval holds that many
- *                   tiles' checks of the layer */
+ *                   tiles' checks of the layer
+ *   sparse_frames   0 .. 32: once at most this many frames of a work item are
+ *                   still decoding, each lane serves one (check, frame) pair
+ *                   (0: never); the tail of a batch -- frames that need many
+ *                   iterations -- then spreads every layer over all lanes
+ * Every tuning gives the same bits, iteration counts and flags. */
 typedef struct {
     int32_t frames_per_tile;
     int32_t threads_per_cta;
     int32_t stage_depth;
     int32_t ctas_per_tile;
     int32_t tiles_per_item;
+    int32_t frames_per_lane;
+    int32_t sparse_frames;
 } qkdrec_tuning;
 
 typedef struct qkdrec_plan_s *qkdrec_plan_t;
 
-/* Defaults: 32 frames per tile, 512 threads, depth 8, 4 CTAs per tile, 1 tile per item. */
+/* Defaults: 32 frames per tile, 512 threads, depth 8, 4 CTAs per tile, 1 tile per item,
+ * 1 frame per lane, sparse mode from 4 decoding frames. */
 void qkdrec_tuning_default(qkdrec_tuning *tuning);
 
 /*
@@ -445,9 +458,10 @@ qkdrec_status qkdrec_plan_workspace_size(qkdrec_plan_t plan, size_t *bytes);
 qkdrec_status qkdrec_plan_launch(qkdrec_plan_t plan, void *workspace, size_t workspace_bytes, void *stream);
 qkdrec_status qkdrec_plan_get_tuning(qkdrec_plan_t plan, qkdrec_tuning *out);
 /*
- * Autotuner: times every tuning on this plan's batch (iterations capped at
- * max_iter if > 0), keeps the fastest in the plan and returns it (best_ms =
- * its time).  Synchronous; runs real decodes (the outputs are overwritten).
+ * Autotuner: times every launch shape on this plan's batch (iterations capped
+ * at max_iter if > 0), then at the fastest shape the sparse-mode thresholds
+ * 0, 1, 2, 4, 8; keeps the fastest tuning in the plan and returns it (best_ms = its time).
+ * Synchronous; runs real decodes (the outputs are overwritten).
  */
 qkdrec_status qkdrec_plan_autotune(qkdrec_plan_t plan, void *workspace, size_t workspace_bytes,
                                    int32_t max_iter, void *stream, qkdrec_tuning *best_out, float *best_ms);

@@ -66,7 +66,8 @@ class GroupC(ctypes.Structure):
 class TuningC(ctypes.Structure):
     _fields_ = [("frames_per_tile", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("stage_depth", ctypes.c_int32), ("ctas_per_tile", ctypes.c_int32),
-                ("tiles_per_item", ctypes.c_int32)]
+                ("tiles_per_item", ctypes.c_int32), ("frames_per_lane", ctypes.c_int32),
+                ("sparse_frames", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -98,7 +98,23 @@ TUNINGS = [None,
            # several tiles of a group decoded together, layer by layer (ragged last item)
            dict(frames_per_tile=8, threads_per_cta=256, stage_depth=4, ctas_per_tile=2, tiles_per_item=2),
            dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=4, ctas_per_tile=8, tiles_per_item=4),
-           dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=1, tiles_per_item=4)]
+           dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=1, tiles_per_item=4),
+           # two or four frames per lane (2- and 4-wide accesses; frames retiring inside a lane)
+           dict(frames_per_tile=16, threads_per_cta=256, stage_depth=8, ctas_per_tile=2, frames_per_lane=2),
+           dict(frames_per_tile=32, threads_per_cta=512, stage_depth=4, ctas_per_tile=1, frames_per_lane=4),
+           dict(frames_per_tile=32, threads_per_cta=256, stage_depth=8, ctas_per_tile=8, frames_per_lane=4,
+                tiles_per_item=2),
+           dict(frames_per_tile=32, threads_per_cta=512, stage_depth=4, ctas_per_tile=4, frames_per_lane=2),
+           # sparse mode (one (check, frame) pair per lane) never, from the first iteration, or late
+           dict(frames_per_tile=8, threads_per_cta=256, stage_depth=4, ctas_per_tile=1, sparse_frames=0),
+           dict(frames_per_tile=32, threads_per_cta=512, stage_depth=4, ctas_per_tile=2, frames_per_lane=4,
+                tiles_per_item=4, sparse_frames=0),
+           dict(frames_per_tile=32, threads_per_cta=256, stage_depth=8, ctas_per_tile=4, frames_per_lane=4,
+                tiles_per_item=2, sparse_frames=8),
+           dict(frames_per_tile=16, threads_per_cta=1024, stage_depth=4, ctas_per_tile=8, tiles_per_item=4,
+                sparse_frames=16),
+           dict(frames_per_tile=32, threads_per_cta=512, stage_depth=4, ctas_per_tile=8, frames_per_lane=4,
+                tiles_per_item=2, sparse_frames=4)]
 
 
 def make_groups(spec, seed=800):
@@ -224,6 +240,8 @@ def test_plan_autotune_picks_a_supported_tuning_and_keeps_results():
     assert best["stage_depth"] in (4, 8, 16)
     assert best["ctas_per_tile"] in (1, 2, 4, 8)
     assert best["tiles_per_item"] in (1, 2, 4)
+    assert best["frames_per_lane"] in (1, 2, 4) and best["frames_per_tile"] // best["frames_per_lane"] >= 8
+    assert best["sparse_frames"] in (0, 1, 2, 4, 8)
     assert ms > 0 and plan.tuning() == best
     plan.launch(ws)
     torch.cuda.synchronize()
@@ -244,6 +262,16 @@ def test_plan_rejects_unsupported_options_and_small_workspace():
         q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(ctas_per_tile=3))
     with pytest.raises(RuntimeError):
         q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(tiles_per_item=3))
+    with pytest.raises(RuntimeError):          # fewer than 8 lanes per check
+        q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(frames_per_tile=8, frames_per_lane=2))
+    with pytest.raises(RuntimeError):
+        q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(frames_per_lane=3))
+    with pytest.raises(RuntimeError):
+        q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(sparse_frames=33))
+    wide = q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(frames_per_lane=4, threads_per_cta=1024,
+                                                                 stage_depth=4))
+    with pytest.raises(RuntimeError):          # four frames per lane run at most 512 threads per CTA
+        wide.launch(wide.workspace())
     deep = q.Plan(groups, q.DecodeOpts(algo="oms_layered"), dict(stage_depth=16, threads_per_cta=512))
     with pytest.raises(RuntimeError):          # depth 16 runs at most 256 threads per CTA
         deep.launch(deep.workspace())
