@@ -1332,6 +1332,10 @@ CASES = {
                              tuning=dict(frames_per_tile=8, threads_per_cta=1024, stage_depth=4, ctas_per_tile=1)),
     "plan_layered_ft32": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
                               tuning=dict(frames_per_tile=32, threads_per_cta=512, stage_depth=8, ctas_per_tile=8)),
+    # the shape the autotuner picks on the uneven batch: 4 frames per lane, 2 tiles per item
+    "plan_layered_v4": dict(groups=((16, 96), (14, 192), (12, 384)), rate=0.84375, iters=5,
+                            tuning=dict(frames_per_tile=32, threads_per_cta=512, stage_depth=4, ctas_per_tile=8,
+                                        tiles_per_item=2, frames_per_lane=4, sparse_frames=4)),
 }
 
 
