@@ -320,9 +320,14 @@ typedef struct {
 } qkdrec_point;
 
 /* DEVICE workspace bytes qkdrec_reconcile needs for these arguments (the
- * sizes of the codes, the frame counts and the decoder options). */
+ * sizes of the codes, the frame counts and the decoder options) with every
+ * partition in flight at once (at most 8); the _limited form sizes it for at
+ * most max_in_flight (>= 1) partitions in flight, 1 = one after another. */
 qkdrec_status qkdrec_reconcile_workspace_size(int64_t count, int32_t m_slices, const qkdrec_decode_opts *opts,
                                               const qkdrec_point *points, int32_t n_points, size_t *bytes);
+qkdrec_status qkdrec_reconcile_workspace_size_limited(int64_t count, int32_t m_slices, const qkdrec_decode_opts *opts,
+                                                      const qkdrec_point *points, int32_t n_points,
+                                                      int32_t max_in_flight, size_t *bytes);
 
 /*
  * Reverse slice reconciliation of one block of count quadrature pairs, end to
@@ -340,8 +345,19 @@ qkdrec_status qkdrec_reconcile_workspace_size(int64_t count, int32_t m_slices, c
  *               workspace on the stream (pinned memory lets the copy overlap).
  *   bob_packed  out [m_slices][count / 8] (may be NULL, HOST or DEVICE): Bob's
  *               slices, packed like alice_packed, for checking the result.
- *   workspace   DEVICE, >= qkdrec_reconcile_workspace_size bytes, 256-byte
- *               aligned, clobbered.  Nothing is allocated.
+ *   workspace   DEVICE, 256-byte aligned, clobbered: at least
+ *               qkdrec_reconcile_workspace_size_limited(..., 1) bytes.  The
+ *               partitions are decoded concurrently, as many at once as the
+ *               workspace holds slots for (qkdrec_reconcile_workspace_size:
+ *               all of them, up to 8), each on one of this device's side
+ *               streams, forked from `stream` after Bob's slices and joined
+ *               back before the call's work ends; with one slot everything
+ *               runs on `stream` in order.  Nothing is allocated (the side
+ *               streams and their events are created once per device, at the
+ *               first call that runs partitions concurrently, which should
+ *               come before any stream capture; calls that run partitions
+ *               concurrently share them, so two such calls must not be issued
+ *               at the same time from different host threads).
  * Asynchronous on `stream`; all argument checks happen before anything is
  * enqueued.  Errors: QKDREC_ERR_ARG (sizes, NULLs, a code whose length is not
  * its partition's n, workspace too small), the errors of the calls above.

@@ -40,7 +40,8 @@ EXPORTED = [
     "qkdrec_plan_get_tuning", "qkdrec_plan_autotune", "qkdrec_slice_llr_soft", "qkdrec_bits_to_llr",
     "qkdrec_code_set_qc", "qkdrec_qc_timeouts",
     "qkdrec_make_regular_code", "qkdrec_free", "qkdrec_code_rate", "qkdrec_checks_for_rate",
-    "qkdrec_quantiser_range", "qkdrec_reconcile", "qkdrec_reconcile_workspace_size", "qkdrec_pack_bits",
+    "qkdrec_quantiser_range", "qkdrec_reconcile", "qkdrec_reconcile_workspace_size",
+    "qkdrec_reconcile_workspace_size_limited", "qkdrec_pack_bits",
     "qkdrec_unpack_bits", "qkdrec_reconciliation_efficiency", "qkdrec_nr_optimise", "qkdrec_nr_key_rate",
 ]
 SELFTEST = ["qkdrec_selftest_phi", "qkdrec_selftest_phi_pair", "qkdrec_selftest_gauss_tail"]
@@ -131,6 +132,7 @@ def lib():
         "qkdrec_make_regular_code": (U, [U64, I32, I32, I32, P, P, P]),
         "qkdrec_free": (None, [P]),
         "qkdrec_reconcile_workspace_size": (U, [I64, I32, P, P, I32, P]),
+        "qkdrec_reconcile_workspace_size_limited": (U, [I64, I32, P, P, I32, I32, P]),
         "qkdrec_reconcile": (U, [P, P, I64, I32, D, D, D, U, P, P, I32, P, P, ctypes.c_size_t, P]),
         "qkdrec_pack_bits": (U, [P, I64, P, P]),
         "qkdrec_unpack_bits": (U, [P, I64, P, P]),
@@ -470,6 +472,17 @@ def qkdrec_reconcile_workspace_size(count: int, m_slices: int, opts: DecodeOpts,
     b = ctypes.c_size_t()
     _check(lib().qkdrec_reconcile_workspace_size(int(count), int(m_slices), ctypes.byref(o), pts.arr, len(points),
                                                  ctypes.byref(b)))
+    return b.value
+
+
+def qkdrec_reconcile_workspace_size_limited(count: int, m_slices: int, opts: DecodeOpts, points,
+                                            max_in_flight: int) -> int:
+    """Workspace bytes for at most max_in_flight partitions decoding at once (1: in order)."""
+    o = opts.c()
+    pts = _Points(points, m_slices)
+    b = ctypes.c_size_t()
+    _check(lib().qkdrec_reconcile_workspace_size_limited(int(count), int(m_slices), ctypes.byref(o), pts.arr,
+                                                         len(points), int(max_in_flight), ctypes.byref(b)))
     return b.value
 
 

@@ -2,9 +2,10 @@
 
 It must equal the same reconciliation done step by step with the single-step
 calls (quantiser, byte syndromes, slice LLRs, batch decoder) bit for bit, with
-its packed syndromes and packed outputs, for host and device buffers alike;
-and its reconciled slices must agree with the FP64 oracle's reconciliation of
-the same block where both decoders converge.
+its packed syndromes and packed outputs, for host and device buffers alike,
+with its partitions decoded one after another or concurrently (also inside a
+captured graph); and its reconciled slices must agree with the FP64 oracle's
+reconciliation of the same block where both decoders converge.
 """
 import numpy as np
 import pytest
@@ -130,6 +131,59 @@ def test_reconcile_with_host_buffers_equals_device_buffers():
     for r in res[1:]:
         for k in r:
             assert torch.equal(r[k], res[0][k]), k
+
+
+def test_reconcile_partitions_in_flight_give_identical_results():
+    """Three partitions decoded one after another, two at a time (a side stream
+    takes the third after the first) and all at once, and the concurrent form
+    captured in a CUDA graph and replayed: the same outputs bit for bit."""
+    count = 1 << 15
+    xh, yh = block(count, seed=905)
+    x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+    lo, hi = q.qkdrec_quantiser_range(SNR)
+    opts = q.DecodeOpts(algo="sp_flood", max_iter=30)
+    parts = [(512, [0.0, 0.125, 0.75, 0.5]), (1024, [0.0, 0.0, 0.75, 0.5]), (2048, [0.0, 0.125, 0.75, 0.5])]
+    codes = [codes_for(n, rates, 4000 + 100 * i)[0] for i, (n, rates) in enumerate(parts)]
+
+    def points(host_last=False):
+        out = []
+        for i, (n, _) in enumerate(parts):
+            F = count // n
+            host = host_last and i == len(parts) - 1
+            mk = (lambda shape, dt: torch.zeros(shape, dtype=dt).pin_memory()) if host else \
+                (lambda shape, dt: torch.zeros(shape, dtype=dt, device="cuda"))
+            out.append(dict(n=n, codes=codes[i], alice_packed=mk((M, count // 8), torch.uint8),
+                            converged=mk((M, F), torch.uint8), iters=mk((M, F), torch.int32)))
+        return out
+
+    def grab(pts):
+        return [{k: p[k].cpu().clone() for k in ("alice_packed", "converged", "iters")} for p in pts]
+
+    res = []
+    for k in (1, 2, 3):
+        pts = points(host_last=(k == 2))
+        ws = torch.empty(q.qkdrec_reconcile_workspace_size_limited(count, M, opts, pts, k), dtype=torch.uint8,
+                         device="cuda")
+        q.qkdrec_reconcile(x, y, M, lo, hi, SNR ** -0.5, opts, pts, workspace=ws)
+        torch.cuda.synchronize()
+        res.append(grab(pts))
+    assert q.qkdrec_reconcile_workspace_size(count, M, opts, points()) == ws.numel()
+    # the concurrent form inside a captured graph, replayed on a fresh output set
+    pts = points()
+    ws = torch.empty(q.qkdrec_reconcile_workspace_size(count, M, opts, pts), dtype=torch.uint8, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        q.qkdrec_reconcile(x, y, M, lo, hi, SNR ** -0.5, opts, pts, workspace=ws)
+    for p in pts:
+        for key in ("alice_packed", "converged", "iters"):
+            p[key].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    res.append(grab(pts))
+    for r in res[1:]:
+        for a, b in zip(r, res[0]):
+            for key in a:
+                assert torch.equal(a[key], b[key]), key
 
 
 def test_reconcile_agrees_with_the_oracle():
