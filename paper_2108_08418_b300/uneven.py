@@ -123,20 +123,32 @@ class UnevenBatch:
                       for gs in self.groups for g in gs] or [1])
         self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
         self.graph = None
+        self._side = torch.cuda.Stream(dev)
+        self._synd_done = [torch.cuda.Event() for _ in range(self.m)]
 
     # ------------------------------------------------------------------ run
     def step(self):
-        """Enqueue one reconciliation of the batch in `x`, `y` on the current stream."""
+        """Enqueue one reconciliation of the batch in `x`, `y` on the current stream.
+
+        Bob's syndromes depend only on his slices, so they run on a side stream
+        (forked after the quantiser, joined before the step ends) while Alice
+        decodes: the decode of slice j waits only for the syndromes of slice j."""
+        torch = _torch()
+        main = torch.cuda.current_stream(self.device)
         qkdrec_quantise_slices_frames(self.y, self.d_off, self.d_ranges, self.m, self.label, want_idx=False,
                                       bits_out=self.bob)
-        for j in range(self.m):
-            for g in self.groups[j]:
-                nf, n = g["f1"] - g["f0"], g["code"].n
-                qkdrec_syndrome(g["code"], self.bob[j, g["a"]:g["b"]].view(nf, n), out=g["synd"])
+        self._side.wait_stream(main)
+        with torch.cuda.stream(self._side):
+            for j in range(self.m):
+                for g in self.groups[j]:
+                    nf, n = g["f1"] - g["f0"], g["code"].n
+                    qkdrec_syndrome(g["code"], self.bob[j, g["a"]:g["b"]].view(nf, n), out=g["synd"])
+                self._synd_done[j].record(self._side)
         for j in range(self.m):
             for f, g in self.llr_runs[j]:
                 qkdrec_slice_llr_frames(self.x, self.d_off[f:g + 1], self.d_params[f:g], self.m, j,
                                         self.alice[:j] if j else None, self.label, out=self.llr)
+            main.wait_event(self._synd_done[j])
             if self.group_opts is not None:
                 for g in self.groups[j]:
                     qkdrec_decode_batch(g["code"], g["llr"], g["synd"], self.group_opts, workspace=self.ws,
