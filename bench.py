@@ -247,7 +247,8 @@ UNEVEN_WORKLOAD = ("uneven batch: 4096 frames, n in {4096, 16384, 65536}, SNR un
                    "capacity at the bin's lowest SNR, minus 3/64 while > 1 of 32 trial frames fail; below 0.10: "
                    "disclosed; table in uneven_rates.json), dv=3 codes per (n, rate), layered offset min-sum FP32 "
                    "(offset 0.5), "
-                   "<= 50 iterations, early stop, whole step replayed as one CUDA graph")
+                   "<= 50 iterations, early stop, the frames in two parts decoded on two streams, whole step "
+                   "replayed as one CUDA graph")
 
 
 def _capacity_row(snr):
@@ -505,7 +506,7 @@ def run_uneven(args):
     # per-kernel durations: the same step run eagerly with the profiling hooks
     q.qkdrec_profile_begin()
     for _ in range(args.steps):
-        ub.step()
+        ub.step(overlap=False)
     barrier()
     stats = q.qkdrec_profile_end()
 
@@ -554,13 +555,16 @@ def run_uneven(args):
                        f"FP32 sum-product flooding, <= {MAX_ITER} iterations, one batch-decoder call per group"),
                    "frames": int(n.size), "samples": int(n.sum()),
                    "groups_per_slice": [len(g) for g in ub.groups], "algo": algo, "prec": "f32",
-                   "max_iter": max_iter, "tuning_per_slice": [t[0] for t in tunings],
+                   "max_iter": max_iter, "tuning_per_part_and_slice": [t[0] for t in tunings],
                    "rate_rule": args.rate_rule,
                    "l2": "inputs larger than L2 (x, y 470 MB each; plan workspace "
                          f"{ub.ws.numel() / 2**30:.2f} GiB)",
                    "raw_decoded_bits_per_s": raw_bits / (ms_step / 1e3), "fer_per_slice": fer,
                    "mean_iters_per_slice": mean_iters, "code_residual_4cycles": residual,
-                   "kernel_times": "per-kernel figures from the same step run eagerly with the profiling hooks",
+                   "kernel_times": "per-kernel figures from the same step run eagerly with the profiling hooks, its "
+                                   "parts and syndromes in order on one stream",
+                   "dominant_kernel_gbs_over_step": (roof["achieved"] * roof["avg_launch_ms"] * roof["launches"]
+                                                     / args.steps / ms_step if roof else None),
                    "setup_s": round(setup_s, 1)},
         "roofline": roof,
         "kernels": kernels,

@@ -12,7 +12,10 @@ slice whose rate is 0 is disclosed).  One step of the batch:
          already reconciled slices 0..j-1 (Sec. III-B, multi-stage decoding),
          then ONE persistent plan launch decoding every frame of slice j
          (layered offset min-sum, per-frame stopping test), then the
-         disclosed frames of slice j copied in the clear.
+         disclosed frames of slice j copied in the clear -- for each of the
+         batch's `parts` parts (the frames of each length split between them,
+         every slice of a frame in the same part) on its own stream, so the
+         parts' launches overlap.
 
 Groups of a slice's plan are runs of consecutive frames sharing (n, rate):
 order the frames by (n, SNR) so that the runs are long.  All buffers are
@@ -40,13 +43,15 @@ class UnevenBatch:
     (n, rate) -> Code for every decoded (n_f, rates[j][f]) pair.
 
     decoder: None (default) decodes each slice with one persistent plan launch
-    (layered offset min-sum, `max_iter`, `offset`); a DecodeOpts instead runs
-    the plain batch decoder on every group of the slice in turn with those
-    options (the same step otherwise, also capturable)."""
+    per part (layered offset min-sum, `max_iter`, `offset`); a DecodeOpts
+    instead runs the plain batch decoder on every group of the slice in turn
+    with those options (the same step otherwise, also capturable).
+    parts: the batch's frames are split into this many parts, each decoded on
+    its own stream (results do not depend on it)."""
 
     def __init__(self, lengths, snrs, rates, codes, m_slices: int = 5, label: str = "gray",
                  max_iter: int = 50, offset: float = 0.5, tuning: dict | None = None, device="cuda",
-                 va: float = 1.0, decoder: DecodeOpts | None = None):
+                 va: float = 1.0, decoder: DecodeOpts | None = None, parts: int = 2):
         torch = _torch()
         self.lengths = np.asarray(lengths, dtype=np.int64)
         self.snrs = np.asarray(snrs, dtype=np.float64)
@@ -75,107 +80,153 @@ class UnevenBatch:
         self.opts = DecodeOpts(algo="oms_layered", prec="f32", max_iter=max_iter, offset=offset, early_stop=True)
         self.group_opts = decoder
         self.codes = codes
-        # per slice: groups (runs of frames with one code) and disclosed sample ranges
-        self.groups, self.disclosed, self.synd, self.plans, self.llr_runs = [], [], [], [], []
+        # Frames are cut into `parts` parts -- the frames of each length split
+        # into consecutive pieces, one per part, the same for every slice (a
+        # frame's slices all decode in its part, each after its lower slices):
+        # the parts are independent reconciliations, decoded on their own
+        # streams, so one part's slice launch fills the SMs another part's
+        # launch frees at its end.  Per part and slice: groups (runs of frames
+        # with one code), disclosed sample ranges, the frame runs that need
+        # slice-j LLRs.
+        self.parts = max(1, int(parts))
+        part_of = np.zeros(F, dtype=np.int64)
+        f = 0
+        while f < F:                        # runs of frames with one length
+            g = f + 1
+            while g < F and self.lengths[g] == self.lengths[f]:
+                g += 1
+            part_of[f:g] = (np.arange(g - f) * self.parts) // (g - f)
+            f = g
+        self.part_of = part_of
+        self.groups = [[] for _ in range(self.m)]
+        self.disclosed = [[] for _ in range(self.m)]
+        self.synd = []
+        self._parts = [dict(groups=[[] for _ in range(self.m)], disclosed=[[] for _ in range(self.m)],
+                            llr_runs=[[] for _ in range(self.m)], plans=[]) for _ in range(self.parts)]
         for j in range(self.m):
-            runs, opened = [], []
+            pieces = []                     # (part, first frame, end frame, code or None)
             f = 0
             while f < F:
-                key = (int(self.lengths[f]), float(self.rates[j, f]))
+                key = (int(self.lengths[f]), float(self.rates[j, f]), int(part_of[f]))
                 g = f + 1
-                while g < F and (int(self.lengths[g]), float(self.rates[j, g])) == key:
+                while g < F and (int(self.lengths[g]), float(self.rates[j, g]), int(part_of[g])) == key:
                     g += 1
-                if key[1] <= 0:
-                    opened.append((int(off[f]), int(off[g])))
-                else:
-                    if key not in codes:
-                        raise KeyError(f"no code for (n, rate) = {key}")
-                    runs.append((f, g, codes[key]))
+                if key[1] > 0 and key[:2] not in codes:
+                    raise KeyError(f"no code for (n, rate) = {key[:2]}")
+                pieces.append((key[2], f, g, codes[key[:2]] if key[1] > 0 else None))
                 f = g
-            total = sum((g - f) * c.M for f, g, c in runs)
+            total = sum((g - f) * c.M for _, f, g, c in pieces if c is not None)
             synd = torch.zeros(max(total, 1), dtype=torch.uint8, device=dev)
-            groups, so = [], 0
-            for f, g, c in runs:
-                nf = g - f
+            so = 0
+            for h, f, g, c in pieces:
+                P = self._parts[h]
                 a, b = int(off[f]), int(off[g])
-                groups.append(dict(code=c, f0=f, f1=g, a=a, b=b,
-                                   llr=self.llr[a:b].view(nf, c.n), bits=self.alice[j, a:b].view(nf, c.n),
-                                   synd=synd[so:so + nf * c.M].view(nf, c.M),
-                                   iters=self.iters[j, f:g], conv=self.conv[j, f:g]))
+                if c is None:
+                    self.disclosed[j].append((a, b))
+                    P["disclosed"][j].append((a, b))
+                    continue
+                nf = g - f
+                gd = dict(code=c, f0=f, f1=g, a=a, b=b,
+                          llr=self.llr[a:b].view(nf, c.n), bits=self.alice[j, a:b].view(nf, c.n),
+                          synd=synd[so:so + nf * c.M].view(nf, c.M),
+                          iters=self.iters[j, f:g], conv=self.conv[j, f:g])
                 so += nf * c.M
-            self.groups.append(groups)
-            # runs of consecutive decoded frames: the only frames that need slice-j LLRs
-            runs_j = []
-            for f, g, _ in runs:
+                self.groups[j].append(gd)
+                P["groups"][j].append(gd)
+                runs_j = P["llr_runs"][j]            # frames of this part that need slice-j LLRs
                 if runs_j and runs_j[-1][1] == f:
                     runs_j[-1][1] = g
                 else:
                     runs_j.append([f, g])
-            self.llr_runs.append(runs_j)
-            self.disclosed.append(opened)
             self.synd.append(synd)
+        self.plans = []
+        sizes = []
+        for P in self._parts:
             if decoder is None:
-                self.plans.append(Plan(groups, self.opts, tuning))
-        if decoder is None:
-            ws = max(p.workspace_size() for p in self.plans)
-        else:
-            ws = max([qkdrec_decode_workspace_size(g["code"], g["f1"] - g["f0"], decoder)
-                      for gs in self.groups for g in gs] or [1])
-        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+                P["plans"] = [Plan(P["groups"][j], self.opts, tuning) for j in range(self.m)]
+                self.plans += P["plans"]
+                sizes.append(max(p.workspace_size() for p in P["plans"]))
+            else:
+                sizes.append(max([qkdrec_decode_workspace_size(g["code"], g["f1"] - g["f0"], decoder)
+                                  for gs in P["groups"] for g in gs] or [1]))
+        # one workspace, a 256-byte-aligned piece per part
+        offs = np.concatenate([[0], np.cumsum([(sz + 255) // 256 * 256 for sz in sizes])])
+        self.ws = torch.empty(max(int(offs[-1]), 256), dtype=torch.uint8, device=dev)
+        self._ws = [self.ws[int(offs[h]):int(offs[h]) + sizes[h]] for h in range(self.parts)]
         self.graph = None
         self._side = torch.cuda.Stream(dev)
+        self._pstreams = [torch.cuda.Stream(dev) for _ in range(self.parts - 1)]
         self._synd_done = [torch.cuda.Event() for _ in range(self.m)]
 
     # ------------------------------------------------------------------ run
-    def step(self):
+    def step(self, overlap: bool = True):
         """Enqueue one reconciliation of the batch in `x`, `y` on the current stream.
 
         Bob's syndromes depend only on his slices, so they run on a side stream
-        (forked after the quantiser, joined before the step ends) while Alice
-        decodes: the decode of slice j waits only for the syndromes of slice j."""
+        (forked after the quantiser) while Alice decodes; each part of the batch
+        runs its slices in order on its own stream (the first on the current
+        one), its decode of slice j waiting only for the syndromes of slice j;
+        every stream is joined back before the step ends.  overlap=False runs
+        the same work in order on the current stream alone (for timing each
+        kernel by itself)."""
         torch = _torch()
         main = torch.cuda.current_stream(self.device)
         qkdrec_quantise_slices_frames(self.y, self.d_off, self.d_ranges, self.m, self.label, want_idx=False,
                                       bits_out=self.bob)
-        self._side.wait_stream(main)
-        with torch.cuda.stream(self._side):
+        side = self._side if overlap else main
+        pstreams = self._pstreams if overlap else [main] * len(self._pstreams)
+        side.wait_stream(main)
+        for st in pstreams:
+            st.wait_stream(main)
+        with torch.cuda.stream(side):
             for j in range(self.m):
                 for g in self.groups[j]:
                     nf, n = g["f1"] - g["f0"], g["code"].n
                     qkdrec_syndrome(g["code"], self.bob[j, g["a"]:g["b"]].view(nf, n), out=g["synd"])
-                self._synd_done[j].record(self._side)
-        for j in range(self.m):
-            for f, g in self.llr_runs[j]:
-                qkdrec_slice_llr_frames(self.x, self.d_off[f:g + 1], self.d_params[f:g], self.m, j,
-                                        self.alice[:j] if j else None, self.label, out=self.llr)
-            main.wait_event(self._synd_done[j])
-            if self.group_opts is not None:
-                for g in self.groups[j]:
-                    qkdrec_decode_batch(g["code"], g["llr"], g["synd"], self.group_opts, workspace=self.ws,
-                                        out=dict(bits=g["bits"], iters=g["iters"], converged=g["conv"]))
-            elif self.groups[j]:
-                self.plans[j].launch(self.ws)
-            for a, b in self.disclosed[j]:
-                self.alice[j, a:b].copy_(self.bob[j, a:b])
+                self._synd_done[j].record(side)
+        for h, P in enumerate(self._parts):
+            st = main if h == 0 else pstreams[h - 1]
+            with torch.cuda.stream(st):
+                for j in range(self.m):
+                    self._llr(P, j)
+                    st.wait_event(self._synd_done[j])
+                    if self.group_opts is not None:
+                        for g in P["groups"][j]:
+                            qkdrec_decode_batch(g["code"], g["llr"], g["synd"], self.group_opts,
+                                                workspace=self._ws[h],
+                                                out=dict(bits=g["bits"], iters=g["iters"], converged=g["conv"]))
+                    elif P["groups"][j]:
+                        P["plans"][j].launch(self._ws[h])
+                    for a, b in P["disclosed"][j]:
+                        self.alice[j, a:b].copy_(self.bob[j, a:b])
+        for st in pstreams:
+            main.wait_stream(st)
+        main.wait_stream(side)
+
+    def _llr(self, P, j):
+        """Slice-j LLRs of the frames of part P that decode slice j."""
+        for f, g in P["llr_runs"][j]:
+            qkdrec_slice_llr_frames(self.x, self.d_off[f:g + 1], self.d_params[f:g], self.m, j,
+                                    self.alice[:j] if j else None, self.label, out=self.llr)
 
     def autotune(self, max_iter: int = 10):
-        """Pick each slice plan's fastest tuning on the batch now in x, y (synchronous)."""
+        """Pick each plan's fastest tuning (per part and slice, part-major) on the
+        batch now in x, y (synchronous)."""
         torch = _torch()
         out = []
         if self.group_opts is not None:
             return [(None, 0.0)] * self.m
         self.step()
         torch.cuda.synchronize(self.device)
-        for j, p in enumerate(self.plans):
-            # the plan of slice j decodes the LLRs of slice j: recompute them first
-            for f, g in self.llr_runs[j]:
-                qkdrec_slice_llr_frames(self.x, self.d_off[f:g + 1], self.d_params[f:g], self.m, j,
-                                        self.alice[:j] if j else None, self.label, out=self.llr)
-            if not self.groups[j]:
-                out.append((None, 0.0))
-                continue
-            out.append(p.autotune(self.ws, max_iter))
-            p.launch(self.ws)
+        for h, P in enumerate(self._parts):
+            for j, p in enumerate(P["plans"]):
+                # the plan decodes the LLRs of slice j: recompute them first
+                self._llr(P, j)
+                if not P["groups"][j]:
+                    out.append((None, 0.0))
+                    continue
+                out.append(p.autotune(self._ws[h], max_iter))
+                p.launch(self._ws[h])
         torch.cuda.synchronize(self.device)
         self.graph = None
         return out

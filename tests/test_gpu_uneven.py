@@ -5,7 +5,8 @@ SNRs, per-frame slice rates) as one CUDA graph.
   counts, flags) equal those of the same reconciliation done frame group by
   frame group through the single-code entry points (quantiser, syndrome,
   slice LLR, batch decoder with layered offset min-sum).
-* Graph replay with new inputs written in place equals an eager step.
+* Graph replay with new inputs written in place equals an eager step, with
+  the batch's frames in one to three parts decoded on their own streams.
 * Against the FP64 oracle: for sampled frames the oracle reconciles the frame
   on its own (quantiser, syndromes, LLRs from its own lower slices, layered
   offset min-sum); both sides agree on every slice where both converge.
@@ -93,9 +94,14 @@ def per_group_reference(ub, x, y):
     return bob, alice, iters, conv
 
 
-def test_uneven_graph_equals_per_group_calls_and_replays():
+@pytest.mark.parametrize("parts", [1, 2, 3])
+def test_uneven_graph_equals_per_group_calls_and_replays(parts):
+    """The batch in 1-3 parts on their own streams (a frame's slices all in one
+    part): graph replays, and the same step run in order on one stream, equal
+    the per-group calls."""
     n, snr, rates, codes, csr, x, y = make_batch(41, 48)
-    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=40)
+    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=40, parts=parts)
+    assert len(set(ub.part_of.tolist())) == parts
     assert sum(len(g) for g in ub.groups) > M_SLICES           # several groups per slice
     assert any(ub.disclosed[j] for j in range(M_SLICES))       # some disclosed slices
     ub.x.copy_(torch.from_numpy(x))
@@ -118,6 +124,10 @@ def test_uneven_graph_equals_per_group_calls_and_replays():
     ub.replay()
     torch.cuda.synchronize()
     bob2, alice2, iters2, conv2 = per_group_reference(ub, x2, y2)
+    assert torch.equal(ub.alice, alice2) and torch.equal(ub.iters, iters2) and torch.equal(ub.conv, conv2)
+    ub.alice.zero_()
+    ub.step(overlap=False)
+    torch.cuda.synchronize()
     assert torch.equal(ub.alice, alice2) and torch.equal(ub.iters, iters2) and torch.equal(ub.conv, conv2)
     ub.destroy()
 
