@@ -247,7 +247,7 @@ UNEVEN_WORKLOAD = ("uneven batch: 4096 frames, n in {4096, 16384, 65536}, SNR un
                    "capacity at the bin's lowest SNR, minus 3/64 while > 1 of 32 trial frames fail; below 0.10: "
                    "disclosed; table in uneven_rates.json), dv=3 codes per (n, rate), layered offset min-sum FP32 "
                    "(offset 0.5), "
-                   "<= 50 iterations, early stop, the frames in two parts decoded on two streams, whole step "
+                   "<= 50 iterations, early stop, the frames in parts decoded on their own streams, whole step "
                    "replayed as one CUDA graph")
 
 
@@ -466,7 +466,8 @@ def run_uneven(args):
     x, y = synth.gaussian_frames(seed, n, snr)
     hx, hy = torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory()
     decoder = q.DecodeOpts(algo="sp_flood", prec="f32", max_iter=MAX_ITER, early_stop=True) if plain else None
-    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=UNEVEN_MAX_ITER, device=dev, decoder=decoder)
+    ub = UnevenBatch(n, snr, rates, codes, M_SLICES, max_iter=UNEVEN_MAX_ITER, device=dev, decoder=decoder,
+                     parts=args.uneven_parts)
     ub.x.copy_(hx)
     ub.y.copy_(hy)
     tunings = ub.autotune(max_iter=10)
@@ -554,7 +555,7 @@ def run_uneven(args):
                        "layered offset min-sum FP32 (offset 0.5), <= 50 iterations",
                        f"FP32 sum-product flooding, <= {MAX_ITER} iterations, one batch-decoder call per group"),
                    "frames": int(n.size), "samples": int(n.sum()),
-                   "groups_per_slice": [len(g) for g in ub.groups], "algo": algo, "prec": "f32",
+                   "groups_per_slice": [len(g) for g in ub.groups], "parts": ub.parts, "algo": algo, "prec": "f32",
                    "max_iter": max_iter, "tuning_per_part_and_slice": [t[0] for t in tunings],
                    "rate_rule": args.rate_rule,
                    "l2": "inputs larger than L2 (x, y 470 MB each; plan workspace "
@@ -1476,6 +1477,8 @@ def main():
                     help="sweep workload: decoder form (default FP32 sum-product; others re-decode failures in FP32)")
     ap.add_argument("--soft-chain", action="store_true",
                     help="sweep: slice LLRs from the lower slices' decoder posteriors (soft) instead of their bits")
+    ap.add_argument("--uneven-parts", type=int, default=2,
+                    help="uneven workload: parts of the batch decoded on their own streams")
     ap.add_argument("--uneven-decoder", choices=["plan", "sp_f32"], default="plan",
                     help="uneven workload: one persistent layered min-sum plan launch per slice (default) or the "
                          "plain FP32 sum-product batch decoder on every group")
