@@ -22,7 +22,7 @@
 // line.  Per tile the workspace holds L [n][FT] and m [E][FT] (frame fastest)
 // and the tile's syndrome bits, one word per check.  Messages are not cleared:
 // the first iteration reads m = 0 without loading it.  The q values of the
-// first kStash / V edges of a check wait in shared memory between the two
+// first min(SF / V, 32) edges of a check wait in shared memory between the two
 // passes; the rest are recomputed from L and m, which no other check of the
 // layer touches.  Posteriors go through L2 only (ld/st .cg), so what one SM of
 // the cluster wrote is what the others read; messages stream with the
@@ -54,7 +54,9 @@ constexpr int kPlanMaxTiles = 4;   // tiles of one work item
 constexpr int kPlanMaxSparse = 32; // sparse mode serves at most this many frames of an item
 
 // dynamic shared memory per warp: the q stash / transpose area
-constexpr size_t kPlanWarpSmem = (size_t)kStash * 32 * sizeof(float);
+// floats of q stash per lane for a launch variant of at most NT threads: the
+// stash is NT * SF * 4 = 128 KB per CTA in every variant (one CTA per SM)
+__host__ __device__ constexpr int plan_stash_floats(int NT) { return NT >= 1024 ? 32 : (NT >= 512 ? 64 : 128); }
 
 struct PlanArgs {
     const PlanGroup *groups;
@@ -159,11 +161,12 @@ template <int V> __device__ __forceinline__ VF<V> pl_ld_sh(const float *p) {
 //   pass 2: m' = sign * max(min_{other edges} |q| - beta, 0), L = q + m'.
 // Edges beyond the stash get q again from L and m, which no other check of
 // the layer touches.  The first iteration reads no message (m = 0).
-template <int V, int CH>
+template <int V, int CH, int SF>
 __device__ __forceinline__ void plan_check(const int32_t *__restrict__ ci, int32_t beg, int32_t d, bool first,
                                            float *L, float *msg, int FT, uint32_t neg, uint32_t live, float *st,
                                            float beta, uint32_t *hd, int f_lo) {
-    constexpr int SV = kStash / V;
+    // stashed edges: SF / V, at most 32 (their old signs are bits of one word per frame)
+    constexpr int SV = SF / V < 32 ? SF / V : 32;
     float mn1[V], mn2[V];
     int32_t arg[V];
     uint32_t ob[V];   // sign of the old posterior of each stashed edge (bit kq)
@@ -397,7 +400,7 @@ struct PlanCount {
 // one (check, decoding frame) pair with V * CH loads in flight, so a layer's
 // checks spread over 32 / A times as many lanes and a layer costs about one
 // check's chain of loads.  Every frame's arithmetic is the same in both modes.
-template <int CH, int V, int SE>
+template <int CH, int V, int SE, int SF>
 __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, int trank, uint32_t *unsat_dst,
                                           uint32_t *s_unsat, float *qst, uint8_t *s_pair, PlanCount &cnt) {
     constexpr uint32_t vmask = (1u << V) - 1u;
@@ -408,7 +411,7 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
     // with few checks still spreads over every SM of the team
     const int gw = warp * tcs + trank, TW = tcs * nwarps;
     const int64_t gt = (int64_t)trank * blockDim.x + tid, TT = (int64_t)tcs * blockDim.x;
-    float *tr = qst + (warp * kStash) * 32;          // this warp's 32 x 32 floats
+    float *tr = qst + (warp * SF) * 32;              // this warp's 32 x SF floats (32 x 32 for transposes)
     uint32_t units = 0, units_first = 0, pwords = 0;   // this item's share (added to cnt at the end)
     const PlanItem itm = a.items[item];
     const PlanGroup &G = a.groups[itm.g];
@@ -557,7 +560,7 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
                     for (int k = 0; k < K; ++k) {
                         const uint32_t la = (active[k] >> f_lo) & vmask;   // this lane's frames still decoding
                         if (!la) continue;
-                        plan_check<V, CH>(G.ci, beg, d, first, Lt[k] + f_lo, mt[k] + f_lo, FT,
+                        plan_check<V, CH, SF>(G.ci, beg, d, first, Lt[k] + f_lo, mt[k] + f_lo, FT,
                                           (__ldcg(swt[k] + c) >> f_lo) & vmask, la, tr + lane * V, a.beta, hdt[k],
                                           f_lo);
                         const uint32_t na = (uint32_t)__popc(la);
@@ -617,8 +620,7 @@ __device__ __forceinline__ void plan_item(const PlanArgs &a, int item, int tcs, 
 template <int CH, int NT, int V>
 __global__ void __launch_bounds__(NT, 1)
 plan_layered_kernel(PlanArgs a) {
-    // [warps][kStash][32] floats: q stash, 32 x 32 transposes; then
-    // [warps][kPlanMaxSlots][kPlanCi] staged column indices
+    // [warps][SF][32] floats: q stash and 32 x 32 transposes
     extern __shared__ __align__(16) float qst[];
     __shared__ int s_item;
     __shared__ uint32_t s_unsat[kPlanMaxTiles];
@@ -638,7 +640,7 @@ plan_layered_kernel(PlanArgs a) {
             plan_sync(CS);   // no CTA leaves while another may still read the leader's word
             break;
         }
-        plan_item<CH, V, (NT >= 512 ? 4 : 8)>(a, item, CS, rank, unsat_dst, s_unsat, qst, s_pair, cnt);
+        plan_item<CH, V, (NT >= 512 ? 4 : 8), plan_stash_floats(NT)>(a, item, CS, rank, unsat_dst, s_unsat, qst, s_pair, cnt);
         plan_sync(CS);   // the tile is finished in every CTA before the leader takes the next
     }
     // per edge-frame update: posterior and message read and written (16 B; the
@@ -764,12 +766,12 @@ static qkdrec_status plan_build(qkdrec_plan_s &p) {
 
 template <int CH, int NT, int V>
 static qkdrec_status plan_launch_ch(const PlanArgs &a, int threads, int CS, int n_items, cudaStream_t st) {
-    // up to 32 warps x 5 KB: above the default 48 KB of dynamic shared memory
+    // 128 KB of stash: above the default 48 KB of dynamic shared memory
     static bool attr_set = false;
-    const size_t stash = (size_t)(threads / 32) * kPlanWarpSmem;
+    const size_t stash = (size_t)threads * plan_stash_floats(NT) * sizeof(float);
     if (!attr_set) {
         QKD_CUDA(cudaFuncSetAttribute(plan_layered_kernel<CH, NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((size_t)(NT / 32) * kPlanWarpSmem)));
+                                      (int)((size_t)NT * plan_stash_floats(NT) * sizeof(float))));
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
