@@ -12,19 +12,23 @@
 // iteration) finishes up to 8 times sooner.  The cluster runs the whole layered
 // offset min-sum decode of its tile: all layers of all iterations, the
 // stopping test after every iteration (per-CTA partial results OR-ed into the
-// leader's shared word), frames retiring one by one, the tile leaving early
+// leader's shared words, one per tile), frames retiring one by one, the tile leaving early
 // once all its frames are done.
 //
 // Lane layout: a lane updates V consecutive frames (V = 1, 2 or 4) and FT / V
 // lanes serve one check, lane = slot * (FT / V) + frame / V, so a warp serves
 // 32 V / FT checks at a time; with FT / V = 8 lanes of 4 frames (or 32 lanes of
 // one) every posterior gather and message access of a check is one 128-byte
-// line.  Per tile the workspace holds L [n][FT] and m [E][FT] (frame fastest)
-// and the tile's syndrome bits, one word per check.  Messages are not cleared:
-// the first iteration reads m = 0 without loading it.  The q values of the
-// first min(SF / V, 32) edges of a check wait in shared memory between the two
-// passes; the rest are recomputed from L and m, which no other check of the
-// layer touches.  Posteriors go through L2 only (ld/st .cg), so what one SM of
+// line.  Per tile the workspace holds L [n][FT] and m [E][FT] (frame fastest),
+// the tile's syndrome bits (one word per check) and its hard decisions (one
+// word per variable, bit f = L[v][f] < 0, flipped by an atomic XOR whenever an
+// update changes a posterior's sign, so the stopping test XORs words instead of
+// gathering posteriors).  Messages are not cleared: the first iteration reads
+// m = 0 without loading it.  The q values of the first min(SF / V, 32) edges
+// of a check (SF: floats of stash per lane) wait in shared memory between the
+// two passes; the rest are recomputed from L and m, which no other check of
+// the layer touches.  Once at most `sparse` frames of an item are decoding,
+// the item switches to a mode with 8 lanes per (check, frame) (plan_item).  Posteriors go through L2 only (ld/st .cg), so what one SM of
 // the cluster wrote is what the others read; messages stream with the
 // evict-first hint (each check, hence each message, is always handled by the
 // same warp of the same CTA), so L2 keeps the tiles' posteriors, which the
