@@ -250,8 +250,10 @@ constexpr int kStash = 32;
 // case (B300, 5 iterations): 0.339 ms per launch with chunks of 2 and no
 // prefetch at 5 blocks per SM; 0.259 ms with chunks of 4 and prefetch at 4
 // blocks per SM (64 registers); chunks of 3 the same, 6 or 8 at 3 blocks slower.
+// The first chunk of a warp's next check is fetched during the last chunk of
+// the current one: check time +4.5 % throughput at check degree 4, +1.5 % at
+// degree 19 (same case), 703.6 -> 682.6 ms per sweep step.
 constexpr int kSp2Chunk = 4;
-constexpr bool kSp2Prefetch = true;
 // The same for the flooding min-sum check kernels.  Measured on the same case
 // (n = 2^16, 512 frames, 5 iterations): 6-bit integers on 16-bit lanes 0.130 ->
 // 0.104 ms per launch with the prefetch; float and FP16 messages (four frames
@@ -482,37 +484,46 @@ check_flood_sp2(DecArgs a) {
         if (act) {
             const int nact = __popc(act);
             const int64_t bL = fpos(0, a.n, f0, LG), bM = fpos(0, a.E, f0, LG);
+            // the next chunk's loads go out before a chunk is processed; after a
+            // check's last chunk, the first chunk of this warp's next check (its
+            // edges and messages are disjoint from this check's, the posteriors
+            // read-only here), so a check of a few edges still overlaps its
+            // gather with the previous check's work
+            float2 Lv[CH], mo[CH];
+            auto fetch = [&](int32_t fbeg, int32_t fd, int k0) {
+#pragma unroll
+                for (int j = 0; j < CH; ++j) {
+                    const int32_t e = fbeg + min(k0 + j, fd - 1);
+                    const int32_t col = __ldg(a.ci + e);
+                    Lv[j] = __ldg(reinterpret_cast<const float2 *>(L + bL + ((uint32_t)col << LG)));
+                    mo[j] = __ldcs(reinterpret_cast<const float2 *>(msg + bM + ((uint32_t)e << LG)));
+                }
+            };
+            int32_t nbeg = 0, nd = 0;
+            if (c0 < a.M) {
+                nbeg = __ldg(a.rp + c0);
+                nd = __ldg(a.rp + c0 + 1) - nbeg;
+                if (nd > 0) fetch(nbeg, nd, 0);
+            }
             for (int it = 0; it < kChecksPerWarp; ++it) {
                 const int64_t c = c0 + it;
                 if (c >= a.M) break;
-                const int32_t beg = __ldg(a.rp + c), d = __ldg(a.rp + c + 1) - beg;
+                const int32_t beg = nbeg, d = nd;
+                const bool more = it + 1 < kChecksPerWarp && c + 1 < a.M;
+                if (more) {
+                    nbeg = __ldg(a.rp + c + 1);
+                    nd = __ldg(a.rp + c + 2) - nbeg;
+                }
                 const uint32_t s = (__ldg(a.sbits + c * a.W + (f0 >> 5)) >> (f0 & 31)) & 3u;
                 uint32_t px = 0, py = 0, sx = 0, sy = 0;     // xor of L words, of q words
                 float2 acc0 = f2(0.0f), acc1 = f2(0.0f);
                 units += (unsigned long long)d * nact;
-                float2 Lv[CH], mo[CH];
-                auto fetch = [&](int k0) {
-#pragma unroll
-                    for (int j = 0; j < CH; ++j) {
-                        const int32_t e = beg + min(k0 + j, d - 1);
-                        const int32_t col = __ldg(a.ci + e);
-                        Lv[j] = __ldg(reinterpret_cast<const float2 *>(L + bL + ((uint32_t)col << LG)));
-                        mo[j] = __ldcs(reinterpret_cast<const float2 *>(msg + bM + ((uint32_t)e << LG)));
-                    }
-                };
-                if (kSp2Prefetch) fetch(0);
                 for (int k0 = 0; k0 < d; k0 += CH) {
                     float2 Lc2[CH], mc2[CH];
-                    if (kSp2Prefetch) {
-                        // the next chunk's loads go out before this chunk is processed
 #pragma unroll
-                        for (int j = 0; j < CH; ++j) { Lc2[j] = Lv[j]; mc2[j] = mo[j]; }
-                        if (k0 + CH < d) fetch(k0 + CH);
-                    } else {
-                        fetch(k0);
-#pragma unroll
-                        for (int j = 0; j < CH; ++j) { Lc2[j] = Lv[j]; mc2[j] = mo[j]; }
-                    }
+                    for (int j = 0; j < CH; ++j) { Lc2[j] = Lv[j]; mc2[j] = mo[j]; }
+                    if (k0 + CH < d) fetch(beg, d, k0 + CH);
+                    else if (more && nd > 0) fetch(nbeg, nd, 0);
 #pragma unroll
                     for (int j = 0; j < CH; ++j) {
                         const int k = k0 + j;
