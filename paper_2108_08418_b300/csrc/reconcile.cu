@@ -99,12 +99,26 @@ static qkdrec_status side_pool(SidePool **out) {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     SidePool &sp = g_pool[dev];
     if (!sp.ok) {
-        QKD_CUDA(cudaEventCreateWithFlags(&sp.fork, cudaEventDisableTiming));
-        for (int k = 0; k < kRecSlots; ++k) {
-            QKD_CUDA(cudaStreamCreateWithFlags(&sp.st[k], cudaStreamNonBlocking));
-            QKD_CUDA(cudaEventCreateWithFlags(&sp.join[k], cudaEventDisableTiming));
+        // all or nothing: a failed creation releases what was made
+        SidePool np;
+        int ns = 0, ne = 0;
+        bool fork = false;
+        cudaError_t e = cudaEventCreateWithFlags(&np.fork, cudaEventDisableTiming);
+        fork = e == cudaSuccess;
+        for (int k = 0; k < kRecSlots && e == cudaSuccess; ++k) {
+            if ((e = cudaStreamCreateWithFlags(&np.st[k], cudaStreamNonBlocking)) != cudaSuccess) break;
+            ++ns;
+            if ((e = cudaEventCreateWithFlags(&np.join[k], cudaEventDisableTiming)) != cudaSuccess) break;
+            ++ne;
         }
-        sp.ok = true;
+        if (e != cudaSuccess) {
+            for (int k = 0; k < ns; ++k) cudaStreamDestroy(np.st[k]);
+            for (int k = 0; k < ne; ++k) cudaEventDestroy(np.join[k]);
+            if (fork) cudaEventDestroy(np.fork);
+            QKD_FAIL(QKDREC_ERR_CUDA, "side streams for concurrent partitions: %s", cudaGetErrorString(e));
+        }
+        np.ok = true;
+        sp = np;
     }
     *out = &sp;
     return QKDREC_OK;
