@@ -37,6 +37,24 @@ def _torch():
     return torch
 
 
+def frame_parts(lengths, parts: int):
+    """Part of each frame: every run of consecutive frames with one length is cut
+    into `parts` consecutive pieces of near-equal size (sizes differ by at most
+    one frame), piece h going to part h; a run of fewer than `parts` frames
+    puts its frames in distinct parts."""
+    lengths = np.asarray(lengths)
+    F = lengths.size
+    out = np.zeros(F, dtype=np.int64)
+    f = 0
+    while f < F:
+        g = f + 1
+        while g < F and lengths[g] == lengths[f]:
+            g += 1
+        out[f:g] = (np.arange(g - f) * int(parts)) // (g - f)
+        f = g
+    return out
+
+
 class UnevenBatch:
     """lengths int [F] (samples per frame, in sample order); snrs float [F];
     rates float [m][F] (0 = the slice of that frame is disclosed); codes: dict
@@ -89,15 +107,7 @@ class UnevenBatch:
         # with one code), disclosed sample ranges, the frame runs that need
         # slice-j LLRs.
         self.parts = max(1, int(parts))
-        part_of = np.zeros(F, dtype=np.int64)
-        f = 0
-        while f < F:                        # runs of frames with one length
-            g = f + 1
-            while g < F and self.lengths[g] == self.lengths[f]:
-                g += 1
-            part_of[f:g] = (np.arange(g - f) * self.parts) // (g - f)
-            f = g
-        self.part_of = part_of
+        part_of = self.part_of = frame_parts(self.lengths, self.parts)
         self.groups = [[] for _ in range(self.m)]
         self.disclosed = [[] for _ in range(self.m)]
         self.synd = []
