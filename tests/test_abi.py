@@ -168,3 +168,23 @@ def test_reconciliation_efficiency_matches_the_oracle(L):
         assert abs(b0 - (H - m) / iab) < 1e-12
     with pytest.raises(q.QkdrecError):
         q.qkdrec_reconciliation_efficiency(3.0, 2, -1.0, 1.0, [0.5, 1.0])
+
+
+def test_reconcile_workspace_grows_by_one_slot_per_partition_in_flight(L):
+    """Host-side sizing of the whole-block call (no device work: every slice of
+    these partitions is disclosed, so no code is needed): a shared part plus one
+    equal slot per partition in flight, capped at the number of partitions;
+    max_in_flight < 1 is refused."""
+    torch = pytest.importorskip("torch")
+    count, m = 1 << 12, 3
+    opts = q.DecodeOpts()
+    pts = [dict(n=n, codes=[None] * m, alice_packed=torch.zeros((m, count // 8), dtype=torch.uint8))
+           for n in (256, 512, 1024)]
+    s = [q.qkdrec_reconcile_workspace_size_limited(count, m, opts, pts, k) for k in (1, 2, 3, 10)]
+    slot = s[1] - s[0]
+    assert slot > 0 and s[2] - s[1] == slot and s[3] == s[2]
+    assert q.qkdrec_reconcile_workspace_size(count, m, opts, pts) == s[2]
+    assert s[0] - slot >= count * 8        # the shared part holds x and y staging
+    with pytest.raises(q.QkdrecError) as e:
+        q.qkdrec_reconcile_workspace_size_limited(count, m, opts, pts, 0)
+    assert e.value.status == q.ERR_ARG
